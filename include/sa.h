@@ -1,0 +1,279 @@
+/*
+ * sa.h -- C ABI of libsa: Sinkhorn diagonal-scaling preprocessing for the optimal
+ * assignment problem on one GB300 GPU (sm_103a).
+ *
+ * Method: Sharify, Gaubert, Grigori, "Solution of the optimal assignment problem by
+ * diagonal scaling algorithms", arXiv:1104.3830.  Given an n x n non-negative matrix A,
+ * find a permutation sigma maximising prod_i a_{i sigma(i)} (Sec. 2.2).  The library
+ * scales the Hadamard power A^(p) = (a_ij^p) to the bistochastic matrix X(p) of maximal
+ * entropy (Eq. pentropyopt, Thm. prop-borweinlewisnussbaum) with the log-domain Sinkhorn
+ * iteration (Sec. 4.1.2) under an increasing p schedule, deletes the entries with
+ * x_ij(p) < t (Eq. matrixred), compacts the survivors into CSR, solves that reduced
+ * instance exactly and proves the result optimal for A by LP duality.
+ *
+ * Conventions used by every entry point.
+ *  - Weights are integers w_ij >= 0 with a_ij = w_ij; w = 0 marks a forbidden entry
+ *    (b_ij = log a_ij = -inf, Eq. pentropyopt).  int16 weights must be <= 32767.
+ *  - Matrices are row-major on the device with a leading dimension ld >= n (elements).
+ *    The fused kernels need ld * sizeof(weight) to be a multiple of 16 bytes and the base
+ *    16-byte aligned; other layouts run on the plain kernels.
+ *  - Potentials are FP64 natural-log vectors u (rows) and v (columns) with
+ *        x_ij(p) = exp(p * log w_ij - u_i - v_j),
+ *    i.e. u_i = -log (D_r)_ii and v_j = -log (D_c)_jj for X(p) = D_r A^(p) D_c; in the
+ *    paper's log coordinates (Sec. 4.1.2) u = -p * ubar and v = -p * vbar.  (u + c, v - c)
+ *    describe the same X (P gauge), so compare X or u_i + v_j, never raw u or v.
+ *  - All device work of a context runs in order on the context's CUDA stream.  Calls
+ *    that return host results synchronise that stream before returning.
+ *  - Errors are returned as sa_status codes; nothing crosses the ABI as an exception.
+ *    sa_last_error() gives a message for the calling thread's last failure.
+ *  - Pointers named d_* are device pointers; all others are host pointers.  Unless a
+ *    comment says otherwise the caller owns every buffer it passes.
+ */
+#ifndef SA_H
+#define SA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SA_OK = 0,
+    SA_PENDING = 1,               /* sa_poll: the request is not finished yet */
+    SA_E_INVALID = -1,            /* bad argument (null pointer, n <= 0, bad schedule, ...) */
+    SA_E_NOMEM = -2,              /* device or host allocation failed */
+    SA_E_CUDA = -3,               /* a CUDA call failed; sa_last_error has the CUDA message */
+    SA_E_NOT_CONVERGED = -4,      /* some p step hit max_sweeps_per_p before tol */
+    SA_E_NO_PERFECT_MATCHING = -5,/* the allowed entries contain no permutation */
+    SA_E_NONFINITE = -6,          /* a row or column lost all mass (no support, Sec. 2.1) */
+    SA_E_BUDGET = -7,             /* request larger than the server's memory budget */
+    SA_E_TIMEOUT = -8,            /* a bounded device wait gave up (kernel returned early) */
+    SA_E_UNSUPPORTED = -9         /* valid request this build cannot run (e.g. n too large) */
+} sa_status;
+
+typedef enum { SA_I16 = 0, SA_I32 = 1 } sa_wtype;
+
+/* Arithmetic of the sweeps.  MIXED: per-element FP32 (exp2/log2 on the SFU), potentials
+ * and stopping residual in FP64.  FP32: potentials in FP32 as well.  FP64: every step
+ * in FP64 (slow on GB300; a reference for the error of the other two). */
+typedef enum { SA_PREC_MIXED = 0, SA_PREC_FP32 = 1, SA_PREC_FP64 = 2 } sa_prec;
+
+/* Which sweep implementation sa_scale uses.  FUSED: one persistent cooperative kernel
+ * runs the whole schedule, one read of A per sweep.  PLAIN: separate row and column
+ * kernels per sweep launched from the host (two reads of A), the comparison path. */
+typedef enum { SA_KERNEL_AUTO = 0, SA_KERNEL_FUSED = 1, SA_KERNEL_PLAIN = 2 } sa_kernel;
+
+/* A device matrix: w points to n rows of ld weights of type wtype. */
+typedef struct {
+    const void* w;
+    sa_wtype wtype;
+    int32_t n;
+    int64_t ld;
+} sa_matrix;
+
+/* Options of the scaling phase (Sec. 4.2, Algorithm 1 with a fixed schedule). */
+typedef struct {
+    const double* p;          /* host array of n_p strictly increasing values > 0 */
+    int32_t n_p;
+    double tol;               /* eps of the eps-bistochastic stop (Sec. 4.2), per p step */
+    int32_t max_sweeps_per_p; /* cap per p step; reaching it sets converged = 0 */
+    sa_prec prec;
+    sa_kernel kernel;
+    int32_t warm_keep_v;      /* 0: multiply (u, v) by p_k / p_{k-1} between steps;
+                                 1: keep v as the deformed iteration of Sec. 3.2 does */
+    int32_t resume_from;      /* 0: start from v = 0 (v_0 = 1, Eq. dad1);  k > 0: d_u, d_v
+                                 hold potentials reached at p[k-1]; run steps k..n_p-1 */
+} sa_scale_opts;
+
+typedef struct {
+    int64_t sweeps_total;     /* sweeps over all steps run by this call */
+    double residual;          /* last stopping residual, max_j |c_j - 1| (FP64) */
+    double p_final;           /* p of the last step run */
+    int32_t converged;        /* 1 if every step reached tol */
+    int32_t steps_done;
+    int32_t fallback_rows;    /* rows recomputed with an exact max shift (range guard) */
+    int32_t kernel_used;      /* sa_kernel actually used */
+    double kernel_ms;         /* device time of the sweep kernels (CUDA events on the
+                                 context stream), excluding set-up and unit conversion */
+} sa_scale_info;
+
+/* Reduced instance B in CSR (Eq. matrixred).  Arrays are host memory owned by the
+ * library: release them with sa_csr_free.  Columns ascend within each row; w holds the
+ * original weights. */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    int64_t* row_ptr;         /* n + 1 */
+    int32_t* col;             /* nnz */
+    int32_t* w;               /* nnz */
+} sa_csr;
+
+typedef struct sa_ctx sa_ctx;
+
+/* Create a context on CUDA device `device` using stream `cuda_stream` (a cudaStream_t,
+ * NULL for the legacy default stream).  The context owns a growing device workspace. */
+sa_status sa_create(sa_ctx** ctx, int device, void* cuda_stream);
+void sa_destroy(sa_ctx* ctx);
+
+/* Message of the calling thread's most recent failure ("" if none). */
+const char* sa_last_error(void);
+
+/* Library build string (compile flags, arch). */
+const char* sa_version(void);
+
+/* Number of CUDA kernels this library has launched in the process so far (all
+ * contexts); a launch-count probe for benchmarks. */
+int64_t sa_kernel_launches(void);
+
+/*
+ * sa_scale: log-domain Sinkhorn (Sec. 4.1.2, Eqs. dad1-dad3 in log coordinates) for
+ * each p of opts->p in turn, each step until max_j |c_j - 1| <= tol for the row-
+ * stochastic iterate (the eps-bistochastic measure of Sec. 4.2) or max_sweeps_per_p.
+ *   d_u, d_v  device FP64[n], caller-owned.  Read as the warm start when
+ *             opts->resume_from > 0; written with the potentials at the last p run.
+ *   info      may be NULL.
+ * Returns SA_OK, SA_E_NOT_CONVERGED (potentials still written), SA_E_NONFINITE, or an
+ * argument/CUDA error.  Synchronises the context stream.
+ */
+sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* opts, double* d_u,
+                   double* d_v, sa_scale_info* info);
+
+/*
+ * sa_verify: FP64 row and column sums of X(p) from the potentials (one read of A).
+ *   d_rows, d_cols  device FP64[n] outputs (either may be NULL).
+ *   max_row_err, max_col_err  host outputs max |sum - 1| (either may be NULL).
+ */
+sa_status sa_verify(sa_ctx* ctx, const sa_matrix* a, double p, const double* d_u,
+                    const double* d_v, double* d_rows, double* d_cols, double* max_row_err,
+                    double* max_col_err);
+
+/*
+ * sa_prune: the reduced matrix B_ij = A_ij if x_ij(p) >= t, else 0 (Eq. matrixred),
+ * compacted to CSR.  t <= 0 selects t = 1/n (Sec. 4.2).  With guard != 0 the largest
+ * entry of every row and of every column of X(p) is kept as well (the paper leaves
+ * empty rows and columns open).  The keep test is p*log w - u - v >= log t, screened
+ * in FP32 and decided in FP64 near the threshold.
+ *   out     filled with library-owned host arrays (sa_csr_free).
+ *   log_ub  may be NULL; receives the approximate optimality certificate of Prop. aoc,
+ *           (1/p) (sum_i max_j (p log w_ij - v_j) + sum_j v_j) >= log w_opt(A).
+ */
+sa_status sa_prune(sa_ctx* ctx, const sa_matrix* a, double p, const double* d_u,
+                   const double* d_v, double t, int32_t guard, sa_csr* out, double* log_ub);
+
+/*
+ * sa_solve_reduced: exact max sum_i log w_{i sigma(i)} over permutations supported by B
+ * (host, sparse shortest augmenting paths; the sequential solve of B in Sec. 4.2).
+ *   perm       host int32[n] out: column of row i
+ *   sum_log_w  host out (may be NULL): sum_i log w_{i perm(i)}
+ *   alpha,beta host FP64[n] out (may be NULL): LP duals, alpha_i + beta_j >= log w_ij on
+ *              B with equality on the assignment
+ * Returns SA_E_NO_PERFECT_MATCHING when B holds no permutation.  Host only: needs no
+ * context and no GPU.
+ */
+sa_status sa_solve_reduced(const sa_csr* b, int32_t* perm, double* sum_log_w, double* alpha,
+                           double* beta);
+
+/*
+ * sa_certify: LP-duality check of (alpha, beta) against the whole of A (one read):
+ * entries with log w_ij - alpha_i - beta_j > tau violate dual feasibility.  No
+ * violation means an assignment tight for (alpha, beta) is optimal for A.  (Not in the
+ * paper: it turns the heuristic prune of Sec. 4.2 into an exact method.)
+ *   alpha, beta  host FP64[n]
+ *   n_viol       host out: number of violating entries
+ *   additions    may be NULL; receives up to max_add violating entries as CSR
+ */
+sa_status sa_certify(sa_ctx* ctx, const sa_matrix* a, const double* alpha, const double* beta,
+                     double tau, int64_t* n_viol, int64_t max_add, sa_csr* additions);
+
+void sa_csr_free(sa_csr* c);
+
+/* Result of the whole preprocessing + exact solve (Algorithm 1, fixed schedule). */
+typedef struct {
+    int32_t* perm;            /* caller-owned host int32[n]: optimal column of each row */
+    double sum_log_w;         /* sum_i log w_{i perm(i)} */
+    double log_ub;            /* certificate of Prop. aoc at the last p */
+    double gamma;             /* Eq. optratio: exp(log_ub - log w_opt(B_first)) */
+    int64_t nnz_first;        /* entries kept by the first prune */
+    int64_t nnz_final;        /* entries of the last reduced instance solved */
+    int32_t repairs;          /* certificate-driven re-solves */
+    int32_t reprunes;         /* re-prunes at t/16 after no perfect matching */
+    sa_scale_info scale;
+    double ms_scale, ms_prune, ms_solve, ms_certify;
+} sa_assign_result;
+
+/*
+ * sa_assign: scale (sa_scale), prune at t (sa_prune, guard on), solve B
+ * (sa_solve_reduced), then certify on A (sa_certify, tau = 1e-9) and re-solve with the
+ * violating entries added until none is left; the result is optimal for A.  If B has
+ * no perfect matching, re-prune at t/16 (finally t = 0, i.e. all of A).
+ */
+sa_status sa_assign(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* opts, double t,
+                    sa_assign_result* res);
+
+/*
+ * sa_assign_host: sa_assign on a HOST matrix (n x ld weights): copies it into a
+ * context-owned device buffer on the context stream first.  For end-to-end timing.
+ */
+sa_status sa_assign_host(sa_ctx* ctx, const void* host_w, sa_wtype wtype, int32_t n, int64_t ld,
+                         const sa_scale_opts* opts, double t, sa_assign_result* res);
+
+/*
+ * sa_narrow_i32_to_i16: exact int32 -> int16 copy (values must lie in [0, 32767]),
+ * halving the bytes the sweeps read.  d_dst has n rows of ld_dst.  *n_bad counts values
+ * out of range (those are clamped; treat n_bad > 0 as failure).
+ */
+sa_status sa_narrow_i32_to_i16(sa_ctx* ctx, const int32_t* d_src, int64_t ld_src, int16_t* d_dst,
+                               int64_t ld_dst, int32_t n, int64_t* n_bad);
+
+/* ---- Batched scaling of many independent small instances (one launch) -------------- */
+
+/*
+ * sa_batch_scale: scale k independent instances in one persistent launch.  Instance i
+ * is the device matrix d_w[i] (n[i] x ld[i] int16 or int32 per wtype, all the same
+ * type); its potentials go to d_u + off[i], d_v + off[i] (device FP64).  The schedule,
+ * tol and cap are shared.  Instances with n <= 512 run one per thread block; larger
+ * ones return SA_E_UNSUPPORTED.  Per-instance sweeps and status go to the host arrays
+ * sweeps[k] and status[k] (may be NULL).
+ *   d_w, d_n, d_ld, d_off  device arrays of length k (pointers, int32, int64, int64)
+ */
+sa_status sa_batch_scale(sa_ctx* ctx, int32_t k, const void* const* d_w, const int32_t* d_n,
+                         const int64_t* d_ld, const int64_t* d_off, sa_wtype wtype,
+                         const sa_scale_opts* opts, double* d_u, double* d_v, int32_t* sweeps,
+                         int32_t* status);
+
+/* ---- Continuous-batching server ---------------------------------------------------- */
+
+typedef struct sa_server sa_server;
+
+typedef struct {
+    int32_t n;
+    int32_t* perm;            /* library-owned until sa_result_release */
+    double sum_log_w;
+    double gamma;
+    int64_t sweeps;
+    int32_t status;           /* sa_status of the request */
+    double t_submit, t_start, t_done;  /* seconds on the server's monotonic clock */
+} sa_result;
+
+/* Start a server on `device` with a device-memory budget for resident requests. */
+sa_status sa_server_create(sa_server** s, int device, size_t hbm_budget, const sa_scale_opts* opts,
+                           int32_t solver_threads);
+void sa_server_destroy(sa_server* s);
+
+/* Submit an n x n host matrix (row-major, ld = n); the weights are copied before return.
+ * Returns SA_E_BUDGET if the request alone exceeds the budget. */
+sa_status sa_submit(sa_server* s, const void* host_w, sa_wtype wtype, int32_t n, uint64_t* ticket);
+
+/* SA_PENDING until the request is done; then SA_OK (or its error) with *out filled. */
+sa_status sa_poll(sa_server* s, uint64_t ticket, sa_result* out);
+void sa_result_release(sa_server* s, uint64_t ticket);
+
+/* Server clock (seconds), the one t_submit/t_start/t_done use. */
+double sa_server_now(const sa_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SA_H */

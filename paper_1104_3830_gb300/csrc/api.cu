@@ -1,0 +1,396 @@
+// api.cu -- the C ABI of libsa (include/sa.h): contexts, argument checks, the scaling
+// driver, pruning, the exact solve of the reduced instance with its duality repair loop
+// (Algorithm 1 of Sec. 4.2 with a fixed schedule), and host-input convenience entry.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sa_internal.h"
+
+namespace sa {
+
+static thread_local std::string tl_err;
+std::atomic<long long> g_kernel_launches{0};
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    tl_err = buf;
+}
+
+sa_status cuda_fail(cudaError_t e, const char* what) {
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    if (e == cudaErrorMemoryAllocation) return SA_E_NOMEM;
+    return SA_E_CUDA;
+}
+
+sa_status Workspace::reserve(size_t bytes) {
+    if (bytes <= size) return SA_OK;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    size = 0;
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    cudaError_t e = cudaMalloc(&ptr, want);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        return cuda_fail(e, "cudaMalloc(workspace)");
+    }
+    size = want;
+    return SA_OK;
+}
+Workspace::~Workspace() {
+    if (ptr) cudaFree(ptr);
+}
+sa_status PinnedBuf::reserve(size_t bytes) {
+    if (bytes <= size) return SA_OK;
+    if (ptr) cudaFreeHost(ptr);
+    ptr = nullptr;
+    size = 0;
+    size_t want = std::max(bytes, (size_t)4096);
+    cudaError_t e = cudaHostAlloc(&ptr, want, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        return cuda_fail(e, "cudaHostAlloc");
+    }
+    size = want;
+    return SA_OK;
+}
+PinnedBuf::~PinnedBuf() {
+    if (ptr) cudaFreeHost(ptr);
+}
+
+sa_status csr_alloc(sa_csr* c, int n, int64_t nnz) {
+    c->n = n;
+    c->nnz = nnz;
+    c->row_ptr = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    c->col = (int32_t*)malloc(sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1));
+    c->w = (int32_t*)malloc(sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1));
+    if (!c->row_ptr || !c->col || !c->w) {
+        free(c->row_ptr);
+        free(c->col);
+        free(c->w);
+        c->row_ptr = nullptr;
+        c->col = nullptr;
+        c->w = nullptr;
+        set_error("host allocation of %lld CSR entries failed", (long long)nnz);
+        return SA_E_NOMEM;
+    }
+    return SA_OK;
+}
+
+static sa_status check_matrix(const sa_matrix* a) {
+    if (!a || !a->w) { set_error("null matrix"); return SA_E_INVALID; }
+    if (a->n <= 0) { set_error("n must be positive (got %d)", a->n); return SA_E_INVALID; }
+    if (a->ld < a->n) { set_error("ld (%lld) < n (%d)", (long long)a->ld, a->n); return SA_E_INVALID; }
+    if (a->wtype != SA_I16 && a->wtype != SA_I32) { set_error("unknown weight type"); return SA_E_INVALID; }
+    return SA_OK;
+}
+
+static sa_status check_opts(const sa_scale_opts* o) {
+    if (!o || !o->p || o->n_p <= 0) { set_error("empty p schedule"); return SA_E_INVALID; }
+    for (int k = 0; k < o->n_p; ++k) {
+        if (!(o->p[k] > 0) || !std::isfinite(o->p[k])) { set_error("p[%d] must be finite and > 0", k); return SA_E_INVALID; }
+        if (k > 0 && !(o->p[k] > o->p[k - 1])) { set_error("p schedule must increase strictly"); return SA_E_INVALID; }
+    }
+    if (!(o->tol > 0)) { set_error("tol must be > 0"); return SA_E_INVALID; }
+    if (o->max_sweeps_per_p <= 0) { set_error("max_sweeps_per_p must be > 0"); return SA_E_INVALID; }
+    if (o->resume_from < 0 || o->resume_from >= o->n_p) { set_error("resume_from out of range"); return SA_E_INVALID; }
+    if (o->prec < SA_PREC_MIXED || o->prec > SA_PREC_FP64) { set_error("unknown precision"); return SA_E_INVALID; }
+    return SA_OK;
+}
+
+struct DeviceGuard {
+    explicit DeviceGuard(int dev) { cudaSetDevice(dev); }
+};
+
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// union of two CSRs with ascending columns; entries of `b` already in `a` are dropped
+static sa_status csr_union(const sa_csr& a, const sa_csr& b, sa_csr* out) {
+    const int n = a.n;
+    std::vector<int64_t> rp(n + 1, 0);
+    std::vector<int32_t> cols, ws;
+    cols.reserve(a.nnz + b.nnz);
+    ws.reserve(a.nnz + b.nnz);
+    for (int i = 0; i < n; ++i) {
+        int64_t x = a.row_ptr[i], xe = a.row_ptr[i + 1];
+        int64_t y = b.row_ptr[i], ye = b.row_ptr[i + 1];
+        while (x < xe || y < ye) {
+            if (y >= ye || (x < xe && a.col[x] < b.col[y])) { cols.push_back(a.col[x]); ws.push_back(a.w[x]); ++x; }
+            else if (x >= xe || b.col[y] < a.col[x]) { cols.push_back(b.col[y]); ws.push_back(b.w[y]); ++y; }
+            else { cols.push_back(a.col[x]); ws.push_back(a.w[x]); ++x; ++y; }
+        }
+        rp[i + 1] = (int64_t)cols.size();
+    }
+    sa_status rc = csr_alloc(out, n, (int64_t)cols.size());
+    if (rc) return rc;
+    memcpy(out->row_ptr, rp.data(), sizeof(int64_t) * (n + 1));
+    if (!cols.empty()) {
+        memcpy(out->col, cols.data(), sizeof(int32_t) * cols.size());
+        memcpy(out->w, ws.data(), sizeof(int32_t) * ws.size());
+    }
+    return SA_OK;
+}
+
+static sa_status solve_csr(const sa_csr& b, int32_t* perm, double* sum_log_w, double* alpha,
+                           double* beta) {
+    std::vector<double> lw((size_t)std::max<int64_t>(b.nnz, 1));
+    for (int64_t e = 0; e < b.nnz; ++e)
+        lw[e] = b.w[e] > 0 ? std::log((double)b.w[e]) : -std::numeric_limits<double>::infinity();
+    sa_status rc = sparse_assign(b.n, b.row_ptr, b.col, lw.data(), perm, alpha, beta);
+    if (rc) return rc;
+    if (sum_log_w) {
+        double s = 0.0;
+        for (int i = 0; i < b.n; ++i) {
+            for (int64_t e = b.row_ptr[i]; e < b.row_ptr[i + 1]; ++e)
+                if (b.col[e] == perm[i]) { s += lw[e]; break; }
+        }
+        *sum_log_w = s;
+    }
+    return SA_OK;
+}
+
+}  // namespace sa
+
+using namespace sa;
+
+extern "C" {
+
+const char* sa_last_error(void) { return tl_err.c_str(); }
+
+int64_t sa_kernel_launches(void) { return (int64_t)g_kernel_launches.load(); }
+
+const char* sa_version(void) {
+    return "libsa 1.0 (sm_103a; fused single-read log-domain Sinkhorn, CSR prune, sparse SAP solve)";
+}
+
+sa_status sa_create(sa_ctx** ctx, int device, void* cuda_stream) {
+    if (!ctx) { set_error("null ctx pointer"); return SA_E_INVALID; }
+    *ctx = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= count) { set_error("device %d out of range (%d devices)", device, count); return SA_E_INVALID; }
+    SA_CUDA(cudaSetDevice(device));
+    sa_ctx* c = new sa_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDeviceProperties"); }
+    c->num_sms = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    if (!prop.cooperativeLaunch) { delete c; set_error("device lacks cooperative launch"); return SA_E_UNSUPPORTED; }
+    *ctx = c;
+    return SA_OK;
+}
+
+void sa_destroy(sa_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    delete ctx;
+}
+
+sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double* d_u, double* d_v,
+                   sa_scale_info* info) {
+    if (!ctx) { set_error("null context"); return SA_E_INVALID; }
+    sa_status rc = check_matrix(a);
+    if (rc) return rc;
+    if ((rc = check_opts(o))) return rc;
+    if (!d_u || !d_v) { set_error("null potential buffers"); return SA_E_INVALID; }
+    DeviceGuard g(ctx->device);
+    sa_scale_info tmp{};
+    if (!info) info = &tmp;
+    memset(info, 0, sizeof(*info));
+    const int n = a->n;
+    // library units: log2
+    if (o->resume_from > 0) {
+        launch_scale_vec(d_u, n, kLog2e, ctx->stream);
+        launch_scale_vec(d_v, n, kLog2e, ctx->stream);
+    }
+    sa_kernel kind = o->kernel;
+    if (o->prec == SA_PREC_FP64) kind = SA_KERNEL_PLAIN;
+    else if (kind == SA_KERNEL_AUTO) kind = fused_supported(ctx, a) ? SA_KERNEL_FUSED : SA_KERNEL_PLAIN;
+    if (kind == SA_KERNEL_FUSED && !fused_supported(ctx, a)) {
+        set_error("fused kernel needs a 16-byte aligned base, ld*sizeof(w) %% 16 == 0 and n <= 12288");
+        return SA_E_UNSUPPORTED;
+    }
+    rc = kind == SA_KERNEL_FUSED ? scale_fused(ctx, a, o, d_u, d_v, info) : scale_plain(ctx, a, o, d_u, d_v, info);
+    if (rc == SA_OK || rc == SA_E_NOT_CONVERGED) {
+        launch_scale_vec(d_u, n, kLn2, ctx->stream);
+        launch_scale_vec(d_v, n, kLn2, ctx->stream);
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "sa_scale");
+    }
+    return rc;
+}
+
+sa_status sa_verify(sa_ctx* ctx, const sa_matrix* a, double p, const double* d_u, const double* d_v,
+                    double* d_rows, double* d_cols, double* max_row_err, double* max_col_err) {
+    if (!ctx) { set_error("null context"); return SA_E_INVALID; }
+    sa_status rc = check_matrix(a);
+    if (rc) return rc;
+    if (!d_u || !d_v || !(p > 0)) { set_error("bad potentials or p"); return SA_E_INVALID; }
+    DeviceGuard g(ctx->device);
+    return verify_device(ctx, a, p, d_u, d_v, d_rows, d_cols, max_row_err, max_col_err);
+}
+
+sa_status sa_prune(sa_ctx* ctx, const sa_matrix* a, double p, const double* d_u, const double* d_v, double t,
+                   int32_t guard, sa_csr* out, double* log_ub) {
+    if (!ctx || !out) { set_error("null context or output"); return SA_E_INVALID; }
+    sa_status rc = check_matrix(a);
+    if (rc) return rc;
+    if (!d_u || !d_v || !(p > 0)) { set_error("bad potentials or p"); return SA_E_INVALID; }
+    DeviceGuard g(ctx->device);
+    memset(out, 0, sizeof(*out));
+    return prune_device(ctx, a, p, d_u, d_v, t, guard, out, log_ub);
+}
+
+sa_status sa_solve_reduced(const sa_csr* b, int32_t* perm, double* sum_log_w, double* alpha, double* beta) {
+    if (!b || !perm || b->n <= 0 || !b->row_ptr || (b->nnz > 0 && (!b->col || !b->w))) {
+        set_error("bad reduced instance");
+        return SA_E_INVALID;
+    }
+    for (int64_t e = 0; e < b->nnz; ++e)
+        if (b->col[e] < 0 || b->col[e] >= b->n) { set_error("column index out of range"); return SA_E_INVALID; }
+    return solve_csr(*b, perm, sum_log_w, alpha, beta);
+}
+
+sa_status sa_certify(sa_ctx* ctx, const sa_matrix* a, const double* alpha, const double* beta, double tau,
+                     int64_t* n_viol, int64_t max_add, sa_csr* additions) {
+    if (!ctx || !alpha || !beta || !n_viol) { set_error("null argument"); return SA_E_INVALID; }
+    sa_status rc = check_matrix(a);
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
+    if (additions) memset(additions, 0, sizeof(*additions));
+    return certify_device(ctx, a, alpha, beta, tau, n_viol, max_add, additions);
+}
+
+void sa_csr_free(sa_csr* c) {
+    if (!c) return;
+    free(c->row_ptr);
+    free(c->col);
+    free(c->w);
+    c->row_ptr = nullptr;
+    c->col = nullptr;
+    c->w = nullptr;
+    c->nnz = 0;
+}
+
+sa_status sa_assign(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double t, sa_assign_result* res) {
+    if (!ctx || !res || !res->perm) { set_error("null context or result"); return SA_E_INVALID; }
+    sa_status rc = check_matrix(a);
+    if (rc) return rc;
+    if ((rc = check_opts(o))) return rc;
+    DeviceGuard g(ctx->device);
+    const int n = a->n;
+    double* d_uv = nullptr;
+    SA_CUDA(cudaMallocAsync((void**)&d_uv, 2 * sizeof(double) * n, ctx->stream));
+    double* d_u = d_uv;
+    double* d_v = d_uv + n;
+    double t0 = now_ms();
+    sa_scale_opts oo = *o;
+    oo.resume_from = 0;
+    rc = sa_scale(ctx, a, &oo, d_u, d_v, &res->scale);
+    double t1 = now_ms();
+    res->ms_scale = t1 - t0;
+    if (rc != SA_OK && rc != SA_E_NOT_CONVERGED) { cudaFreeAsync(d_uv, ctx->stream); return rc; }
+    const double p = o->p[o->n_p - 1];
+    if (!(t > 0)) t = 1.0 / n;
+    sa_csr B{};
+    double log_ub = 0.0;
+    std::vector<double> alpha(n), beta(n);
+    res->reprunes = 0;
+    res->repairs = 0;
+    res->ms_prune = res->ms_solve = res->ms_certify = 0.0;
+    double first_sum = 0.0;
+    bool have_first = false;
+    // prune + solve, re-pruning at t/16 while B holds no permutation
+    for (;;) {
+        double a0 = now_ms();
+        rc = prune_device(ctx, a, p, d_u, d_v, t, 1, &B, have_first ? nullptr : &log_ub);
+        double a1 = now_ms();
+        res->ms_prune += a1 - a0;
+        if (rc) { cudaFreeAsync(d_uv, ctx->stream); return rc; }
+        if (!have_first) res->nnz_first = B.nnz;
+        rc = solve_csr(B, res->perm, &res->sum_log_w, alpha.data(), beta.data());
+        res->ms_solve += now_ms() - a1;
+        if (rc == SA_OK) break;
+        sa_csr_free(&B);
+        if (rc != SA_E_NO_PERFECT_MATCHING) { cudaFreeAsync(d_uv, ctx->stream); return rc; }
+        if (t == 0.0) { cudaFreeAsync(d_uv, ctx->stream); return rc; }   // all of A: no support
+        res->reprunes++;
+        t = t / 16.0;
+        if (t < 1e-300) t = 0.0;
+        have_first = true;   // gamma refers to the first successful B below
+    }
+    first_sum = res->sum_log_w;
+    res->log_ub = log_ub;
+    res->gamma = std::exp(log_ub - first_sum);
+    // LP-duality repair: add violating entries of A until none is left
+    for (int iter = 0;; ++iter) {
+        double c0 = now_ms();
+        int64_t nv = 0;
+        sa_csr add{};
+        const int64_t max_add = std::max<int64_t>(4 * (int64_t)n, 1 << 16);
+        rc = certify_device(ctx, a, alpha.data(), beta.data(), 1e-9, &nv, max_add, &add);
+        res->ms_certify += now_ms() - c0;
+        if (rc) { sa_csr_free(&B); cudaFreeAsync(d_uv, ctx->stream); return rc; }
+        if (nv == 0) { sa_csr_free(&add); break; }
+        sa_csr merged{};
+        rc = csr_union(B, add, &merged);
+        sa_csr_free(&add);
+        sa_csr_free(&B);
+        if (rc) { cudaFreeAsync(d_uv, ctx->stream); return rc; }
+        B = merged;
+        res->repairs++;
+        double s0 = now_ms();
+        rc = solve_csr(B, res->perm, &res->sum_log_w, alpha.data(), beta.data());
+        res->ms_solve += now_ms() - s0;
+        if (rc) { sa_csr_free(&B); cudaFreeAsync(d_uv, ctx->stream); return rc; }
+        if (iter > 64) { set_error("duality repair did not settle"); sa_csr_free(&B); cudaFreeAsync(d_uv, ctx->stream); return SA_E_NOT_CONVERGED; }
+    }
+    res->nnz_final = B.nnz;
+    sa_csr_free(&B);
+    cudaFreeAsync(d_uv, ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sa_assign");
+    return SA_OK;
+}
+
+sa_status sa_assign_host(sa_ctx* ctx, const void* host_w, sa_wtype wtype, int32_t n, int64_t ld,
+                         const sa_scale_opts* o, double t, sa_assign_result* res) {
+    if (!ctx || !host_w || n <= 0 || ld < n) { set_error("bad host matrix"); return SA_E_INVALID; }
+    DeviceGuard g(ctx->device);
+    const int sz = wbytes(wtype);
+    // device copy with a 16-byte aligned pitch so the fused kernel can take it
+    const int64_t dld = (int64_t)align_up((size_t)n * sz, 16) / sz;
+    sa_status rc = ctx->input.reserve((size_t)dld * n * sz);
+    if (rc) return rc;
+    SA_CUDA(cudaMemcpy2DAsync(ctx->input.ptr, (size_t)dld * sz, host_w, (size_t)ld * sz, (size_t)n * sz, n,
+                              cudaMemcpyHostToDevice, ctx->stream));
+    sa_matrix a{ctx->input.ptr, wtype, n, dld};
+    return sa_assign(ctx, &a, o, t, res);
+}
+
+sa_status sa_narrow_i32_to_i16(sa_ctx* ctx, const int32_t* d_src, int64_t ld_src, int16_t* d_dst, int64_t ld_dst,
+                               int32_t n, int64_t* n_bad) {
+    if (!ctx || !d_src || !d_dst || n <= 0 || ld_src < n || ld_dst < n) { set_error("bad narrowing arguments"); return SA_E_INVALID; }
+    DeviceGuard g(ctx->device);
+    return narrow_device(ctx, d_src, ld_src, d_dst, ld_dst, n, n_bad);
+}
+
+}  // extern "C"

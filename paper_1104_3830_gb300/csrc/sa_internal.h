@@ -1,0 +1,127 @@
+// sa_internal.h -- host-side internals of libsa shared by the translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/sa.h"
+
+namespace sa {
+
+// Device-side error codes written to an int flag by kernels (0 = none).
+enum : int {
+    kErrNone = 0,
+    kErrTimeout = 1,     // a bounded wait gave up
+    kErrNonfinite = 2,   // a row or column sum was zero / not finite
+    kErrLaunch = 3,
+};
+
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr double kLog2e = 1.44269504088896340736;
+constexpr uint64_t kWaitTimeoutNs = 2000000000ull;  // 2 s per device wait
+
+void set_error(const char* fmt, ...);
+
+// Process-wide count of kernels this library has launched (sa_kernel_launches).
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launch(int k = 1) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
+sa_status cuda_fail(cudaError_t e, const char* what);
+
+#define SA_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return ::sa::cuda_fail(_e, #call);  \
+    } while (0)
+
+// Growable device workspace carved into named regions per call.
+struct Workspace {
+    void* ptr = nullptr;
+    size_t size = 0;
+    sa_status reserve(size_t bytes);
+    ~Workspace();
+};
+
+struct PinnedBuf {
+    void* ptr = nullptr;
+    size_t size = 0;
+    sa_status reserve(size_t bytes);
+    ~PinnedBuf();
+};
+
+}  // namespace sa
+
+struct sa_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    sa::Workspace ws;        // scratch for sweeps, prune, certify
+    sa::Workspace input;     // device copy of host inputs (sa_assign_host)
+    sa::PinnedBuf pinned;    // staging for small device->host results
+};
+
+namespace sa {
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+inline int wbytes(sa_wtype t) { return t == SA_I16 ? 2 : 4; }
+
+// Bump allocator over a reserved workspace.
+struct Carve {
+    char* base;
+    size_t off = 0;
+    explicit Carve(void* p) : base((char*)p) {}
+    template <typename T>
+    T* take(size_t count) {
+        off = align_up(off, 256);
+        T* r = (T*)(base + off);
+        off += count * sizeof(T);
+        return r;
+    }
+};
+
+// ---- sweeps (sweep_plain.cu, sweep_fused.cu) ------------------------------------------
+// Potentials inside the library are FP64 in log2 units: U = u / ln 2, V = v / ln 2.
+struct ScaleState {
+    double* U;   // n
+    double* V;   // n
+};
+sa_status scale_plain(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double* U,
+                      double* V, sa_scale_info* info);
+sa_status scale_fused(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double* U,
+                      double* V, sa_scale_info* info);
+sa_status scale_fp64(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double* U,
+                     double* V, sa_scale_info* info);
+bool fused_supported(const sa_ctx* ctx, const sa_matrix* a);
+size_t fused_workspace_bytes(const sa_ctx* ctx, const sa_matrix* a);
+
+// natural <-> log2 units, in place on the device (n doubles), y = x * f
+void launch_scale_vec(double* x, int n, double f, cudaStream_t s);
+// Vh = float(V), Vc = 2^(Vh - V)
+void launch_split_v(const double* V, float* Vh, float* Vc, int n, cudaStream_t s);
+
+// ---- prune / certify / verify (prune.cu) --------------------------------------------
+sa_status prune_device(sa_ctx* ctx, const sa_matrix* a, double p, const double* d_u,
+                       const double* d_v, double t, int guard, sa_csr* out, double* log_ub);
+sa_status certify_device(sa_ctx* ctx, const sa_matrix* a, const double* alpha,
+                         const double* beta, double tau, int64_t* n_viol, int64_t max_add,
+                         sa_csr* add);
+sa_status verify_device(sa_ctx* ctx, const sa_matrix* a, double p, const double* d_u,
+                        const double* d_v, double* d_rows, double* d_cols, double* max_row_err,
+                        double* max_col_err);
+
+sa_status narrow_device(sa_ctx* ctx, const int32_t* src, int64_t lds, int16_t* dst, int64_t ldd,
+                        int n, int64_t* n_bad);
+
+// ---- host exact solver (solve.cpp) ----------------------------------------------------
+// Max sum of logw over perfect matchings of a CSR bipartite graph (rows -> cols).
+// Returns SA_OK / SA_E_NO_PERFECT_MATCHING.
+sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const double* logw,
+                        int32_t* perm, double* alpha, double* beta);
+
+// csr helpers (api.cu)
+sa_status csr_alloc(sa_csr* c, int n, int64_t nnz);
+
+}  // namespace sa

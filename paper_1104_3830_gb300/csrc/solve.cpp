@@ -1,0 +1,133 @@
+// solve.cpp -- exact solve of the reduced instance B on the host (the sequential solve
+// of Sec. 4.2), by shortest augmenting paths on the sparse bipartite graph of B.
+//
+// Minimisation form: cost c_e = -log w_e on each kept entry.  Column prices v_j are kept
+// such that every assigned row i sits on a column of least reduced cost c_ij - v_j
+// (Jonker-Volgenant invariant).  Start: v_j = min_i c_ij and a greedy assignment on
+// zero-reduced-cost entries.  Each free row then runs Dijkstra over columns with a binary
+// heap until it reaches a free column; the prices of the columns finalised before the
+// target are lowered by (d_target - d_j) and the path is flipped.  At the end
+// u_i = c_{i,sigma(i)} - v_{sigma(i)} and (alpha, beta) = (-u, -v) are optimal LP duals
+// of the maximisation: alpha_i + beta_j >= log w_ij on B, with equality on sigma.
+#include <cmath>
+#include <cstdint>
+#include <queue>
+#include <utility>
+#include <vector>
+
+#include "sa_internal.h"
+
+namespace sa {
+
+sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const double* logw,
+                        int32_t* perm, double* alpha, double* beta) {
+    const double INF = std::numeric_limits<double>::infinity();
+    std::vector<double> v(n, INF);
+    for (int i = 0; i < n; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (!(logw[e] > -INF)) continue;
+            const double c = -logw[e];
+            if (c < v[col[e]]) v[col[e]] = c;
+        }
+    for (int j = 0; j < n; ++j)
+        if (v[j] == INF) {
+            set_error("reduced instance: column %d has no allowed entry", j);
+            return SA_E_NO_PERFECT_MATCHING;
+        }
+    std::vector<int32_t> rmatch(n, -1), cmatch(n, -1);
+    // greedy assignment on least-reduced-cost columns
+    for (int i = 0; i < n; ++i) {
+        double best = INF;
+        int bj = -1;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (!(logw[e] > -INF)) continue;
+            const double h = -logw[e] - v[col[e]];
+            if (h < best) { best = h; bj = col[e]; }
+        }
+        if (bj < 0) {
+            set_error("reduced instance: row %d has no allowed entry", i);
+            return SA_E_NO_PERFECT_MATCHING;
+        }
+        if (cmatch[bj] < 0) { cmatch[bj] = i; rmatch[i] = bj; }
+    }
+    std::vector<double> dist(n, INF);
+    std::vector<int32_t> pred(n, -1), stamp(n, -1), done(n, -1), scanned;
+    scanned.reserve(n);
+    typedef std::pair<double, int32_t> Item;
+    int epoch = 0;
+    for (int r = 0; r < n; ++r) {
+        if (rmatch[r] >= 0) continue;
+        ++epoch;
+        scanned.clear();
+        std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+        for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+            if (!(logw[e] > -INF)) continue;
+            const int j = col[e];
+            const double d = -logw[e] - v[j];
+            if (stamp[j] != epoch || d < dist[j]) {
+                stamp[j] = epoch;
+                dist[j] = d;
+                pred[j] = r;
+                heap.push(Item(d, j));
+            }
+        }
+        int sink = -1;
+        double dmin = INF;
+        while (!heap.empty()) {
+            Item top = heap.top();
+            heap.pop();
+            const int j = top.second;
+            if (done[j] == epoch || top.first > dist[j]) continue;
+            if (cmatch[j] < 0) { sink = j; dmin = dist[j]; break; }
+            done[j] = epoch;
+            scanned.push_back(j);
+            const int i = cmatch[j];
+            // reduced cost of the assigned entry (i, j); zero-length step through row i
+            double ci = INF;
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+                if (col[e] == j) { ci = -logw[e]; break; }
+            const double ui = ci - v[j];
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                if (!(logw[e] > -INF)) continue;
+                const int k = col[e];
+                if (done[k] == epoch) continue;
+                const double nd = dist[j] + (-logw[e] - v[k]) - ui;
+                if (stamp[k] != epoch || nd < dist[k]) {
+                    stamp[k] = epoch;
+                    dist[k] = nd;
+                    pred[k] = i;
+                    heap.push(Item(nd, k));
+                }
+            }
+        }
+        if (sink < 0) {
+            set_error("reduced instance has no perfect matching (row %d cannot be assigned)", r);
+            return SA_E_NO_PERFECT_MATCHING;
+        }
+        for (int j : scanned) v[j] += dist[j] - dmin;
+        // flip the alternating path ending at sink
+        int j = sink;
+        for (;;) {
+            const int i = pred[j];
+            cmatch[j] = i;
+            const int prev = rmatch[i];
+            rmatch[i] = j;
+            if (i == r) break;
+            j = prev;
+        }
+    }
+    for (int i = 0; i < n; ++i) perm[i] = rmatch[i];
+    if (alpha || beta) {
+        std::vector<double> u(n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            const int j = rmatch[i];
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+                if (col[e] == j) { u[i] = -logw[e] - v[j]; break; }
+        }
+        if (alpha) for (int i = 0; i < n; ++i) alpha[i] = -u[i];
+        if (beta) for (int j = 0; j < n; ++j) beta[j] = -v[j];
+    }
+    return SA_OK;
+}
+
+}  // namespace sa

@@ -1,0 +1,600 @@
+// sweep_fused.cu -- the single-read Sinkhorn sweep: one persistent cooperative kernel
+// runs every sweep of every p step of the schedule (Sec. 4.1.2 log-domain iteration,
+// Sec. 4.2 stopping rule) and reads A once per sweep.
+//
+// Work split.  Block b owns the row stripe [b*n/G, (b+1)*n/G).  Within a block every
+// thread owns a fixed set of 16-byte column chunks, so the column partial sums of the
+// stripe live in registers for the whole sweep.  Rows stream through a shared-memory
+// ring filled by the bulk-copy engine (cp.async.bulk + mbarrier), RING rows ahead.
+//
+// One sweep, in log2 units (U = u/ln2, V = v/ln2, L = log2 w):
+//   row i   t_ij = 2^(p (L_ij - Lr_i) - Vh_j) * c_j          (FP32, SFU ex2/lg2)
+//           s_i  = sum_j t_ij                                   (block reduction)
+//           S_j += t_ij / s_i        (column sums of the row-stochastic iterate)
+//           U_i  = p Lr_i + log2 s_i                           (row update, dad2)
+//   grid barrier; block b finalises a slice of columns:
+//           S_j  = sum_b S_j^(b)     (FP64, fixed order: deterministic)
+//           V_j += log2 S_j          (column update, dad3, FP64)
+//           residual = max_j |S_j - 1|  (eps-bistochastic measure, Sec. 4.2, FP64)
+//   grid barrier; every block reads the residual and takes the same decision.
+// Lr_i = float(U_i / p) is a per-row FP32 reference frozen during a p step: the row
+// normalisation cancels it exactly, and it keeps the FP32 exponent small (L - Lr is exact
+// when L and Lr are within a factor of two).  V_j is exact in FP64; the kernel applies it
+// as an FP32 head Vh_j = float(V_j) (frozen per step) times c_j = 2^(Vh_j - V_j), so
+// column updates smaller than an FP32 ulp of V are not lost.
+//
+// Rows whose sum leaves [2^-64, 2^64] (a stale shift, e.g. the first sweep at a large
+// p) are recomputed with the exact max shift of the paper and re-anchor Lr_i.
+//
+// Every wait is bounded (2 s); on expiry the kernel records kErrTimeout, drains its
+// outstanding bulk copies and returns.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "common.cuh"
+#include "sa_internal.h"
+
+namespace sa {
+
+struct FusedArgs {
+    const void* w;
+    int n;
+    int64_t ld;
+    unsigned row_bytes;   // bytes copied per row (multiple of 16)
+    const double* P;      // device copy of the schedule
+    int k0, n_p;
+    double tol;
+    int max_sweeps;
+    int keep_v;
+    int f32_potentials;   // SA_PREC_FP32: round U, V to FP32 after every update
+    double* U;            // n, log2 units
+    double* V;            // n, log2 units
+    float* Vh;            // n, FP32 head of V (frozen per step)
+    float* Vc;            // n, 2^(Vh - V)
+    float* part;          // G x npad column partials
+    int npad;
+    double* rpart;        // G residual partials
+    unsigned* bar;        // grid barrier words
+    int* err;
+    int* fallback;
+    int* sweeps_out;      // n_p
+    double* resid_out;    // n_p
+    int max_rows;         // max rows in any stripe (smem arrays)
+};
+
+namespace {
+
+template <typename WT>
+struct Vec;
+template <>
+struct Vec<int16_t> {
+    static constexpr int N = 8;
+    // decode 8 weights and return log2 of each
+    __device__ static __forceinline__ void log2w(const uint4& q, float* L) {
+        const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            L[2 * k] = lg2_approx(lo16_to_float(wd[k]));
+            L[2 * k + 1] = lg2_approx(hi16_to_float(wd[k]));
+        }
+    }
+};
+template <>
+struct Vec<int32_t> {
+    static constexpr int N = 4;
+    __device__ static __forceinline__ void log2w(const uint4& q, float* L) {
+        L[0] = lg2_approx((float)(int)q.x);
+        L[1] = lg2_approx((float)(int)q.y);
+        L[2] = lg2_approx((float)(int)q.z);
+        L[3] = lg2_approx((float)(int)q.w);
+    }
+};
+
+template <typename WT, int NT, int CH, int RING>
+__global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
+    constexpr int VEC = Vec<WT>::N;
+    constexpr int NW = NT / 32;
+    constexpr int M = CH * VEC;   // columns owned per thread
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* ring = smem;
+    uint64_t* mbar = (uint64_t*)(smem + (size_t)RING * A.row_bytes);
+    float* red = (float*)(mbar + RING);          // [2][NW]
+    float* red2 = red + 2 * NW;                  // [NW] slow path
+    float* Lr = red2 + NW;                       // [max_rows]
+    float* srow = Lr + A.max_rows;               // [max_rows]
+    double* redd = (double*)(srow + A.max_rows);   // [NW][32] (8-byte aligned: 3NW + 2 max_rows is even)
+    __shared__ int s_flag;
+
+    const int n = A.n;
+    const int G = gridDim.x;
+    const int b = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int r0 = (int)((int64_t)b * n / G);
+    const int r1 = (int)((int64_t)(b + 1) * n / G);
+    const int nrows = r1 - r0;
+    const int NC = (n + VEC - 1) / VEC;
+    const unsigned char* wbase = (const unsigned char*)A.w;
+    const size_t pitch = (size_t)A.ld * sizeof(WT);
+
+    if (tid == 0) {
+        for (int s = 0; s < RING; ++s) mbar_init(&mbar[s], 1);
+        mbar_fence_init();
+        s_flag = 0;
+    }
+    __syncthreads();
+
+    uint32_t iss = 0, it = 0;   // rows issued / consumed by this block, all sweeps
+    auto issue_row = [&](int q) {   // q = local row index; thread 0 only
+        const uint32_t slot = iss % RING;
+        mbar_arrive_expect_tx(&mbar[slot], A.row_bytes);
+        bulk_g2s(ring + (size_t)slot * A.row_bytes, wbase + (size_t)(r0 + q) * pitch, A.row_bytes,
+                 &mbar[slot]);
+        ++iss;
+    };
+    auto drain = [&]() {
+        if (tid == 0) {
+            for (uint32_t q = it; q < iss; ++q)
+                if (!mbar_wait(&mbar[q % RING], (q / RING) & 1u, A.err, kWaitTimeoutNs)) break;
+        }
+        __syncthreads();
+    };
+
+    // column ownership
+    int cidx[CH];
+    int nval[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+        cidx[k] = tid + k * NT;
+        nval[k] = cidx[k] < NC ? min(VEC, n - cidx[k] * VEC) : 0;
+    }
+
+    float S[M], vh[M], vc[M], t[M];
+    auto load_cols = [&]() {
+#pragma unroll
+        for (int k = 0; k < CH; ++k)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const int j = cidx[k] * VEC + e;
+                const bool ok = e < nval[k];
+                vh[k * VEC + e] = ok ? __ldcg(A.Vh + j) : 0.0f;
+                vc[k * VEC + e] = ok ? __ldcg(A.Vc + j) : 0.0f;
+            }
+    };
+
+    // prefetch the first rows of the first sweep
+    if (tid == 0)
+        for (int q = 0; q < min(RING, nrows); ++q) issue_row(q);
+
+    int buf = 0;
+    for (int k = A.k0; k < A.n_p; ++k) {
+        const double p = A.P[k];
+        const float pf = (float)p;
+        // per-step row references: U holds the row potentials reached at p[k-1]
+        // (zero on a fresh start), so U/p[k-1] is the per-row level of log2 w
+        {
+            const double pprev = (k > 0) ? A.P[k - 1] : p;
+            for (int q = tid; q < nrows; q += NT) Lr[q] = (float)(A.U[r0 + q] / pprev);
+        }
+        __syncthreads();
+        load_cols();
+        int sweeps = 0;
+        double resid = INFINITY;
+        bool done = false;
+        while (!done) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) S[m] = 0.0f;
+            // ---------------- row pass ----------------
+            for (int q = 0; q < nrows; ++q) {
+                const uint32_t slot = it % RING;
+                if (!mbar_wait(&mbar[slot], (it / RING) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
+                const unsigned char* rowp = ring + (size_t)slot * A.row_bytes;
+                const float lr = Lr[q];
+                float sp = 0.0f;
+#pragma unroll
+                for (int kk = 0; kk < CH; ++kk) {
+                    float L[VEC];
+                    if (nval[kk] > 0) {
+                        uint4 qv = *(const uint4*)(rowp + (size_t)cidx[kk] * 16);
+                        Vec<WT>::log2w(qv, L);
+                    }
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        const int m = kk * VEC + e;
+                        float tv = 0.0f;
+                        if (e < nval[kk]) tv = ex2_approx(fmaf(pf, L[e] - lr, -vh[m])) * vc[m];
+                        t[m] = tv;
+                        sp += tv;
+                    }
+                }
+                sp = warp_sum(sp);
+                if (lane == 0) red[buf * NW + wid] = sp;
+                __syncthreads();
+                if (s_flag) { drain(); return; }
+                float s = 0.0f;
+#pragma unroll
+                for (int x = 0; x < NW; ++x) s += red[buf * NW + x];
+                buf ^= 1;
+                const bool slow = !(s >= 0x1p-64f && s <= 0x1p64f);
+                if (!slow) {
+                    if (tid == 0) {
+                        srow[q] = s;
+                        if (q + RING < nrows) { fence_proxy_async_smem(); issue_row(q + RING); }
+                    }
+                    const float inv = 1.0f / s;
+#pragma unroll
+                    for (int m = 0; m < M; ++m) S[m] = fmaf(t[m], inv, S[m]);
+                } else {
+                    // exact max shift (the paper's form): recompute e, then t = 2^(e - max)
+                    float mx = -INFINITY;
+#pragma unroll
+                    for (int kk = 0; kk < CH; ++kk) {
+                        float L[VEC];
+                        if (nval[kk] > 0) {
+                            uint4 qv = *(const uint4*)(rowp + (size_t)cidx[kk] * 16);
+                            Vec<WT>::log2w(qv, L);
+                        }
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) {
+                            const int m = kk * VEC + e;
+                            float ev = -INFINITY;
+                            if (e < nval[kk]) ev = fmaf(pf, L[e] - lr, -vh[m]) + log2f(vc[m]);
+                            t[m] = ev;
+                            mx = fmaxf(mx, ev);
+                        }
+                    }
+                    mx = warp_max(mx);
+                    if (lane == 0) red2[wid] = mx;
+                    __syncthreads();
+                    float gm = -INFINITY;
+                    for (int x = 0; x < NW; ++x) gm = fmaxf(gm, red2[x]);
+                    float s2 = 0.0f;
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        t[m] = (gm > -INFINITY) ? ex2_approx(t[m] - gm) : 0.0f;
+                        s2 += t[m];
+                    }
+                    s2 = warp_sum(s2);
+                    __syncthreads();
+                    if (lane == 0) red2[wid] = s2;
+                    __syncthreads();
+                    float ss = 0.0f;
+                    for (int x = 0; x < NW; ++x) ss += red2[x];
+                    if (!(gm > -INFINITY) || !(ss > 0.0f)) {
+                        if (tid == 0) atomicCAS(A.err, 0, kErrNonfinite);
+                        ss = 1.0f;
+                    }
+                    const float inv = 1.0f / ss;
+#pragma unroll
+                    for (int m = 0; m < M; ++m) S[m] = fmaf(t[m], inv, S[m]);
+                    if (tid == 0) {
+                        // re-anchor the row reference at the exact row potential
+                        const double un = p * (double)lr + (double)gm + log2((double)ss);
+                        const float lrn = (float)(un / p);
+                        Lr[q] = lrn;
+                        srow[q] = (float)exp2(un - p * (double)lrn);
+                        atomicAdd(A.fallback, 1);
+                        if (q + RING < nrows) { fence_proxy_async_smem(); issue_row(q + RING); }
+                    }
+                    __syncthreads();
+                }
+                ++it;
+            }
+            // prefetch the first rows of the next sweep (same data every sweep)
+            if (tid == 0)
+                for (int q = 0; q < min(RING, nrows); ++q) issue_row(q);
+            // column partials of this stripe
+            float* pb = A.part + (size_t)b * A.npad;
+#pragma unroll
+            for (int kk = 0; kk < CH; ++kk) {
+                if (cidx[kk] < NC) {
+#pragma unroll
+                    for (int e = 0; e < VEC; e += 4)
+                        *(float4*)(pb + (size_t)cidx[kk] * VEC + e) =
+                            make_float4(S[kk * VEC + e], S[kk * VEC + e + 1], S[kk * VEC + e + 2],
+                                        S[kk * VEC + e + 3]);
+                }
+            }
+            ++sweeps;
+            if (!group_barrier(A.bar, G, A.err, kWaitTimeoutNs)) { drain(); return; }
+            // ---------------- column finalisation ----------------
+            double rmax = 0.0;
+            const int nblk = (n + 31) / 32;
+            for (int cb = b; cb < nblk; cb += G) {
+                const int j = cb * 32 + lane;
+                double acc = 0.0;
+                if (j < n) {
+                    // independent loads in flight (fixed summation order: deterministic)
+                    const float* pj = A.part + j;
+                    int g = wid;
+                    for (; g + 3 * NW < G; g += 4 * NW) {
+                        const float a0 = __ldcg(pj + (size_t)g * A.npad);
+                        const float a1 = __ldcg(pj + (size_t)(g + NW) * A.npad);
+                        const float a2 = __ldcg(pj + (size_t)(g + 2 * NW) * A.npad);
+                        const float a3 = __ldcg(pj + (size_t)(g + 3 * NW) * A.npad);
+                        acc += ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
+                    }
+                    for (; g < G; g += NW) acc += (double)__ldcg(pj + (size_t)g * A.npad);
+                }
+                redd[wid * 32 + lane] = acc;
+                __syncthreads();
+                if (wid == 0 && j < n) {
+                    double Sj = 0.0;
+                    for (int x = 0; x < NW; ++x) Sj += redd[x * 32 + lane];
+                    if (!(Sj > 0.0) || !isfinite(Sj)) atomicCAS(A.err, 0, kErrNonfinite);
+                    const double d = Sj - 1.0;
+                    rmax = fmax(rmax, fabs(d));
+                    double lg;
+                    if (fabs(d) < 1e-3) {
+                        // log2(1 + d) by its series, FP64 (|d| < 1e-3: 5 terms reach 1e-17)
+                        lg = d * (1.0 + d * (-0.5 + d * (1.0 / 3.0 + d * (-0.25 + d * 0.2)))) * kLog2e;
+                    } else {
+                        lg = log2(Sj);
+                    }
+                    double v = A.V[j] + lg;
+                    if (A.f32_potentials) v = (double)(float)v;
+                    A.V[j] = v;
+                    float h = A.Vh[j];
+                    if (A.f32_potentials || fabs((double)h - v) > 16.0) { h = (float)v; A.Vh[j] = h; }
+                    A.Vc[j] = ex2_approx((float)((double)h - v));
+                }
+                __syncthreads();
+            }
+            if (wid == 0) {
+                rmax = warp_max(rmax);
+                if (lane == 0) A.rpart[b] = rmax;
+            }
+            if (!group_barrier(A.bar, G, A.err, kWaitTimeoutNs)) { drain(); return; }
+            // ---------------- decision (identical in every block) ----------------
+            double r = 0.0;
+            for (int g = lane; g < G; g += 32) r = fmax(r, __ldcg(A.rpart + g));
+            r = warp_max(r);
+            resid = r;
+            done = (resid <= A.tol) || (sweeps >= A.max_sweeps);
+            if (!done) load_cols();
+        }
+        // step finished: write U for this stripe, record the step
+        for (int q = tid; q < nrows; q += NT) {
+            double u = p * (double)Lr[q] + log2((double)srow[q]);
+            if (A.f32_potentials) u = (double)(float)u;
+            A.U[r0 + q] = u;
+        }
+        if (b == 0 && tid == 0) {
+            A.sweeps_out[k] = sweeps;
+            A.resid_out[k] = resid;
+        }
+        if (k + 1 < A.n_p) {
+            // warm start of the next step: (U, V) *= p_{k+1}/p_k unless v is kept
+            const double f = A.keep_v ? 1.0 : A.P[k + 1] / p;
+            const int nblk = (n + 31) / 32;
+            for (int cb = b; cb < nblk; cb += G) {
+                const int j = cb * 32 + lane;
+                if (wid != 0 || j >= n) continue;
+                double v = A.V[j] * f;
+                A.V[j] = v;
+                float h = (float)v;
+                A.Vh[j] = h;
+                A.Vc[j] = ex2_approx((float)((double)h - v));
+            }
+            if (!group_barrier(A.bar, G, A.err, kWaitTimeoutNs)) { drain(); return; }
+        }
+    }
+    drain();
+}
+
+template <typename WT, int NT, int CH, int RING>
+sa_status launch_fused(sa_ctx* ctx, const FusedArgs& args, size_t smem, int* grid_out) {
+    auto kern = fused_kernel<WT, NT, CH, RING>;
+    SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+    if (per_sm < 1) {
+        set_error("fused sweep: kernel does not fit on an SM (smem %zu)", smem);
+        return SA_E_UNSUPPORTED;
+    }
+    int G = ctx->num_sms * per_sm;
+    // at least 8 rows per block (fewer blocks share each barrier for small n)
+    const int gmax_rows = args.n / 8 > 0 ? args.n / 8 : 1;
+    if (G > gmax_rows) G = gmax_rows;
+    if (*grid_out > 0 && *grid_out < G) G = *grid_out;
+    *grid_out = G;
+    FusedArgs a = args;
+    void* params[] = {&a};
+    SA_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(NT), params, smem, ctx->stream));
+    return SA_OK;
+}
+
+struct FusedCfg {
+    int nt, ch, ring;
+};
+
+FusedCfg pick_cfg(const sa_matrix* a, size_t smem_optin) {
+    const int vec = 16 / wbytes(a->wtype);
+    const int nc = (a->n + vec - 1) / vec;
+    FusedCfg c{0, 0, 0};
+    if (nc <= 128) c = {128, 1, 0};
+    else if (nc <= 256) c = {256, 1, 0};
+    else if (nc <= 512) c = {512, 1, 0};
+    else if (nc <= 1024) c = {512, 2, 0};
+    else if (nc <= 1536) c = {512, 3, 0};
+    else return c;
+    const size_t row_bytes = align_up((size_t)a->n * wbytes(a->wtype), 16);
+    const size_t budget = smem_optin > 16384 ? smem_optin - 16384 : 0;
+    int ring = (int)(budget / row_bytes);
+    if (ring > 8) ring = 8;
+    if (ring >= 6) ring = 6;
+    else if (ring >= 4) ring = 4;
+    else if (ring >= 2) ring = 2;
+    else ring = 0;
+    c.ring = ring;
+    if (ring == 0) c.nt = 0;
+    return c;
+}
+
+}  // namespace
+
+bool fused_supported(const sa_ctx* ctx, const sa_matrix* a) {
+    const int sz = wbytes(a->wtype);
+    if (((uintptr_t)a->w & 15) != 0) return false;
+    if (((size_t)a->ld * sz) % 16 != 0) return false;
+    if ((size_t)a->ld * sz < align_up((size_t)a->n * sz, 16)) return false;
+    return pick_cfg(a, ctx->smem_optin).nt > 0;
+}
+
+sa_status scale_fused(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double* U,
+                      double* V, sa_scale_info* info) {
+    const int n = a->n;
+    FusedCfg cfg = pick_cfg(a, ctx->smem_optin);
+    if (cfg.nt == 0) {
+        set_error("fused sweep: n=%d not supported by the fused kernel", n);
+        return SA_E_UNSUPPORTED;
+    }
+    cudaStream_t st = ctx->stream;
+    const int G_max = ctx->num_sms * 2;
+    const int npad = (int)align_up((size_t)n, 32);
+    // any grid has >= min(num_sms, n/8) blocks, so no stripe exceeds this many rows
+    const int gmin = std::max(1, std::min(ctx->num_sms, n / 8));
+    const int max_rows = (n + gmin - 1) / gmin + 1;
+    size_t need = (size_t)G_max * npad * 4 + (size_t)G_max * 8 + 2 * align_up((size_t)n * 4, 256) +
+                  (size_t)o->n_p * 16 + 8192;
+    sa_status rc = ctx->ws.reserve(need);
+    if (rc) return rc;
+    Carve cv(ctx->ws.ptr);
+    float* part = cv.take<float>((size_t)G_max * npad);
+    double* rpart = cv.take<double>(G_max);
+    float* Vh = cv.take<float>(n);
+    float* Vc = cv.take<float>(n);
+    double* P = cv.take<double>(o->n_p);
+    double* resid_out = cv.take<double>(o->n_p);
+    int* sweeps_out = cv.take<int>(o->n_p);
+    unsigned* bar = cv.take<unsigned>(2);
+    int* err = cv.take<int>(1);
+    int* fallback = cv.take<int>(1);
+    SA_CUDA(cudaMemcpyAsync(P, o->p, o->n_p * sizeof(double), cudaMemcpyHostToDevice, st));
+    SA_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+    SA_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    SA_CUDA(cudaMemsetAsync(fallback, 0, sizeof(int), st));
+    SA_CUDA(cudaMemsetAsync(sweeps_out, 0, o->n_p * sizeof(int), st));
+    const int k0 = o->resume_from > 0 ? o->resume_from : 0;
+    if (k0 == 0) {
+        SA_CUDA(cudaMemsetAsync(U, 0, n * sizeof(double), st));
+        SA_CUDA(cudaMemsetAsync(V, 0, n * sizeof(double), st));
+    } else if (!o->warm_keep_v) {
+        // warm start from step k0-1: scale to p[k0]; the kernel's first-step row
+        // reference divides U by p[k0-1] (the unscaled value), so scale V only.
+        launch_scale_vec(V, n, o->p[k0] / o->p[k0 - 1], st);
+    }
+    // Vh = float(V), Vc = 2^(Vh - V)
+    launch_split_v(V, Vh, Vc, n, st);
+    FusedArgs args{};
+    args.w = a->w;
+    args.n = n;
+    args.ld = a->ld;
+    args.row_bytes = (unsigned)align_up((size_t)n * wbytes(a->wtype), 16);
+    args.P = P;
+    args.k0 = k0;
+    args.n_p = o->n_p;
+    args.tol = o->tol;
+    args.max_sweeps = o->max_sweeps_per_p;
+    args.keep_v = o->warm_keep_v;
+    args.f32_potentials = o->prec == SA_PREC_FP32;
+    args.U = U;
+    args.V = V;
+    args.Vh = Vh;
+    args.Vc = Vc;
+    args.part = part;
+    args.npad = npad;
+    args.rpart = rpart;
+    args.bar = bar;
+    args.err = err;
+    args.fallback = fallback;
+    args.sweeps_out = sweeps_out;
+    args.resid_out = resid_out;
+    args.max_rows = max_rows;
+    const int NW = cfg.nt / 32;
+    size_t smem = (size_t)cfg.ring * args.row_bytes + cfg.ring * 8 + (3 * NW) * 4 +
+                  (size_t)2 * max_rows * 4 + NW * 32 * 8 + 64;
+    int G = G_max;
+    const bool i16 = a->wtype == SA_I16;
+    cudaEvent_t ev0, ev1;
+    SA_CUDA(cudaEventCreate(&ev0));
+    SA_CUDA(cudaEventCreate(&ev1));
+    SA_CUDA(cudaEventRecord(ev0, st));
+#define SA_LAUNCH(NT_, CH_, RING_)                                                              \
+    rc = i16 ? launch_fused<int16_t, NT_, CH_, RING_>(ctx, args, smem, &G)                    \
+             : launch_fused<int32_t, NT_, CH_, RING_>(ctx, args, smem, &G)
+    if (cfg.ring == 6) {
+        if (cfg.nt == 128) SA_LAUNCH(128, 1, 6);
+        else if (cfg.nt == 256) SA_LAUNCH(256, 1, 6);
+        else if (cfg.ch == 1) SA_LAUNCH(512, 1, 6);
+        else if (cfg.ch == 2) SA_LAUNCH(512, 2, 6);
+        else SA_LAUNCH(512, 3, 6);
+    } else if (cfg.ring == 4) {
+        if (cfg.ch == 2) SA_LAUNCH(512, 2, 4);
+        else SA_LAUNCH(512, 3, 4);
+    } else {
+        SA_LAUNCH(512, 3, 2);
+    }
+#undef SA_LAUNCH
+    if (rc) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); return rc; }
+    SA_CUDA(cudaEventRecord(ev1, st));
+    // results
+    sa_status prc = ctx->pinned.reserve(4096 + (size_t)o->n_p * 16);
+    if (prc) return prc;
+    char* hp = (char*)ctx->pinned.ptr;
+    int* h_err = (int*)hp;
+    int* h_fb = (int*)(hp + 8);
+    int* h_sw = (int*)(hp + 64);
+    double* h_rs = (double*)(hp + 64 + align_up((size_t)o->n_p * 4, 64));
+    SA_CUDA(cudaMemcpyAsync(h_err, err, 4, cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaMemcpyAsync(h_fb, fallback, 4, cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaMemcpyAsync(h_sw, sweeps_out, o->n_p * 4, cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaMemcpyAsync(h_rs, resid_out, o->n_p * 8, cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaStreamSynchronize(st));
+    float kms = 0.0f;
+    SA_CUDA(cudaEventElapsedTime(&kms, ev0, ev1));
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    int64_t total = 0;
+    int conv = 1;
+    for (int k = k0; k < o->n_p; ++k) {
+        total += h_sw[k];
+        if (!(h_rs[k] <= o->tol)) conv = 0;
+    }
+    if (info) {
+        info->sweeps_total = total;
+        info->residual = h_rs[o->n_p - 1];
+        info->p_final = o->p[o->n_p - 1];
+        info->converged = conv;
+        info->steps_done = o->n_p - k0;
+        info->fallback_rows = *h_fb;
+        info->kernel_used = SA_KERNEL_FUSED;
+        info->kernel_ms = kms;
+    }
+    if (*h_err == kErrTimeout) {
+        set_error("fused sweep: a bounded device wait timed out (grid of %d blocks)", G);
+        return SA_E_TIMEOUT;
+    }
+    if (*h_err == kErrNonfinite) {
+        set_error("fused sweep: a row or column lost all mass (matrix without support?)");
+        return SA_E_NONFINITE;
+    }
+    return conv ? SA_OK : SA_E_NOT_CONVERGED;
+}
+
+__global__ void split_v_kernel(const double* V, float* Vh, float* Vc, int n) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) {
+        double v = V[j];
+        float h = (float)v;
+        Vh[j] = h;
+        Vc[j] = ex2_approx((float)((double)h - v));
+    }
+}
+
+void launch_split_v(const double* V, float* Vh, float* Vc, int n, cudaStream_t s) {
+    if (n > 0) split_v_kernel<<<(n + 255) / 256, 256, 0, s>>>(V, Vh, Vc, n);
+    count_launch();
+}
+
+}  // namespace sa

@@ -1,0 +1,88 @@
+"""Batched scaling (sa_batch_scale, one persistent launch over many small instances)
+against the FP64 oracle, and each instance alone equal to the same instance inside the
+batch (the result of one instance does not depend on its neighbours)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1104_3830_gb300 import _lib as L
+from paper_1104_3830_gb300 import api
+from paper_1104_3830_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1104_3830_gb300 import build
+    build.build()
+    c = api.sa_create(0)
+    yield c
+    c.close()
+
+
+def batch_scale(ctx, mats, ps, tol=1e-6, sweeps=20000):
+    """Pack instances as device tensors and run sa_batch_scale; returns (u_list, v_list, sweeps, status)."""
+    devs = [api.to_device(m) for m in mats]
+    k = len(mats)
+    ptrs = torch.tensor([d.data_ptr() for d in devs], dtype=torch.int64, device="cuda")
+    ns = torch.tensor([m.shape[0] for m in mats], dtype=torch.int32, device="cuda")
+    lds = torch.tensor([d.stride(0) for d in devs], dtype=torch.int64, device="cuda")
+    offs_h = np.concatenate([[0], np.cumsum([m.shape[0] for m in mats])[:-1]]).astype(np.int64)
+    offs = torch.from_numpy(offs_h).cuda()
+    tot = int(sum(m.shape[0] for m in mats))
+    u = torch.zeros(tot, dtype=torch.float64, device="cuda")
+    v = torch.zeros(tot, dtype=torch.float64, device="cuda")
+    sw = np.zeros(k, dtype=np.int32)
+    st = np.zeros(k, dtype=np.int32)
+    o = L.make_opts(ps, tol, sweeps)
+    wt = L.SA_I16 if mats[0].dtype == np.int16 else L.SA_I32
+    rc = L.lib().sa_batch_scale(ctx.handle, k, ctypes.c_void_p(ptrs.data_ptr()), ctypes.c_void_p(ns.data_ptr()),
+                                ctypes.c_void_p(lds.data_ptr()), ctypes.c_void_p(offs.data_ptr()), wt,
+                                ctypes.byref(o), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                                sw.ctypes.data_as(L._I32P), st.ctypes.data_as(L._I32P))
+    uh, vh = u.cpu().numpy(), v.cpu().numpy()
+    us = [uh[o_:o_ + m.shape[0]] for o_, m in zip(offs_h, mats)]
+    vs = [vh[o_:o_ + m.shape[0]] for o_, m in zip(offs_h, mats)]
+    return rc, us, vs, sw, st
+
+
+@pytest.mark.parametrize("dtype", [np.int16, np.int32])
+def test_batch_matches_oracle(ctx, dtype):
+    sizes = [1, 2, 7, 16, 33, 100, 129, 250, 300, 512, 64, 17]
+    mats = [W.uniform(n, 1, 1000, 1000 + k, dtype=dtype) for k, n in enumerate(sizes)]
+    ps = [2.0 ** k for k in range(8)]
+    rc, us, vs, sw, st = batch_scale(ctx, mats, ps)
+    assert rc == 0 and np.all(st == 0), (rc, st)
+    for m, u, v in zip(mats, us, vs):
+        b = oracle.log_weights(m.astype(np.int64))
+        r, c = oracle.sums(b, ps[-1], u, v)
+        err = max(np.abs(r - 1).max(), np.abs(c - 1).max())
+        assert err < 2 * ps[-1] * np.log(2) * 1e-6 + 2e-6, (m.shape, err)
+        uo, vo, *_ = oracle.sinkhorn(b, ps, 1e-6, 20000)
+        xo = oracle.xmatrix(b, ps[-1], uo, vo)
+        xg = oracle.xmatrix(b, ps[-1], u, v)
+        assert np.max(np.abs(xg - xo)) < 5e-3
+
+
+def test_alone_equals_in_batch(ctx):
+    mats = [W.uniform(n, 1, 1000, 2000 + n, dtype=np.int16) for n in (40, 300, 120, 512, 90)]
+    ps = [1.0, 2.0, 4.0, 8.0, 16.0]
+    rc, us, vs, sw, st = batch_scale(ctx, mats, ps)
+    assert rc == 0
+    for k, m in enumerate(mats):
+        rc1, u1, v1, sw1, st1 = batch_scale(ctx, [m], ps)
+        assert rc1 == 0
+        # same instance, same block program: bit-identical potentials and sweep counts
+        assert sw1[0] == sw[k]
+        assert np.array_equal(u1[0], us[k]) and np.array_equal(v1[0], vs[k])
+
+
+def test_batch_rejects_large_n(ctx):
+    rc, *_ = batch_scale(ctx, [W.uniform(600, 1, 1000, 3, dtype=np.int16)], [1.0])
+    assert rc == L.SA_E_UNSUPPORTED

@@ -1,0 +1,45 @@
+"""Host exact solver of the reduced instance (sa_solve_reduced) against the oracle's
+dense Hungarian method: equal optimal products (exact integers) and valid LP duals.
+Runs on the CPU: the solver is host code behind the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1104_3830_gb300 import api
+
+
+def _csr(mask, w):
+    rows, cols = np.nonzero(mask)
+    rp = np.zeros(mask.shape[0] + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=mask.shape[0]), out=rp[1:])
+    return rp, cols.astype(np.int32), w[rows, cols].astype(np.int32)
+
+
+@pytest.mark.parametrize("n,density,hi", [(1, 1.0, 5), (2, 1.0, 9), (7, 1.0, 1000), (40, 0.15, 1000),
+                                          (200, 0.05, 30000), (300, 1.0, 1000), (257, 0.02, 7)])
+def test_matches_oracle(n, density, hi):
+    rng = np.random.default_rng(n * 7 + hi)
+    w = rng.integers(1, hi + 1, size=(n, n)).astype(np.int64)
+    mask = rng.random((n, n)) < density
+    mask[np.arange(n), rng.permutation(n)] = True
+    rp, col, wv = _csr(mask, w)
+    perm, s, al, be = api.sa_solve_reduced(rp, col, wv)
+    assert sorted(perm) == list(range(n)) and all(mask[i, perm[i]] for i in range(n))
+    b = np.where(mask, np.log(w.astype(float)), -np.inf)
+    ph, _, _, st = oracle.hungarian(b)
+    assert st == 0
+    assert oracle.perm_weight_exact(w, perm) == oracle.perm_weight_exact(w, ph)
+    # duals: feasible on B, tight on the assignment
+    assert oracle.dual_violations(b, al, be, 1e-9)[0] == 0
+    assert max(abs(al[i] + be[perm[i]] - b[i, perm[i]]) for i in range(n)) < 1e-9
+    assert abs(s - sum(b[i, perm[i]] for i in range(n))) < 1e-9
+
+
+def test_no_perfect_matching_is_reported():
+    # two rows that can only use the same column
+    w = np.ones((3, 3), dtype=np.int64)
+    mask = np.array([[1, 0, 0], [1, 0, 0], [1, 1, 1]], dtype=bool)
+    rp, col, wv = _csr(mask, w)
+    with pytest.raises(api.SaError) as e:
+        api.sa_solve_reduced(rp, col, wv)
+    assert e.value.status == -5
