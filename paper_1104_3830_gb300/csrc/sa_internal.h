@@ -58,6 +58,7 @@ struct sa_ctx {
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     size_t smem_optin = 0;
+    int max_grid = 0;        // cap on the fused kernel's grid (0: all SMs); set by the server
     sa::Workspace ws;        // scratch for sweeps, prune, certify
     sa::Workspace input;     // device copy of host inputs (sa_assign_host)
     sa::PinnedBuf pinned;    // staging for small device->host results

@@ -54,7 +54,7 @@ struct FusedArgs {
     float* Vc;            // n, 2^(Vh - V)
     float* part;          // G x npad column partials
     int npad;
-    double* rpart;        // G residual partials
+    float* rmax;          // 2 alternating words: max_j |S_j - 1| of a sweep (atomicMax)
     unsigned* bar;        // grid barrier words
     int* err;
     int* fallback;
@@ -91,20 +91,74 @@ struct Vec<int32_t> {
     }
 };
 
-template <typename WT, int NT, int CH, int RING>
+#ifndef SA_STAMP
+#define SA_STAMP(slot)   // phase timing hook (no-op in the library build)
+#endif
+
+// Kahan-compensated FP32 accumulation
+struct KahanF {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+// Arrive on a CTA mbarrier (release at CTA scope: prior shared stores are visible to
+// threads that complete a wait on this phase).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Grid barrier on a monotonic arrival counter: barrier number `k` (0, 1, 2, ...) completes
+// when the counter reaches (k + 1) * nblocks.  Bounded wait; false on timeout or error.
+__device__ __forceinline__ bool grid_sync(unsigned* ctr, unsigned target, int* err, int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        if (ld_acquire(ctr) < target) {
+            const uint64_t t0 = globaltimer_ns();
+            unsigned spins = 0;
+            while (ld_acquire(ctr) < target) {
+                if ((++spins & 31u) == 0) {
+                    if (*(volatile int*)err != 0) { ok = 0; break; }
+                    if (globaltimer_ns() - t0 > kWaitTimeoutNs) { atomicCAS(err, 0, kErrTimeout); ok = 0; break; }
+                }
+                __nanosleep(32);
+            }
+        }
+        if (*(volatile int*)err != 0) ok = 0;
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+template <typename WT, int NT, int CH, int RING, int R>
 __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
     constexpr int VEC = Vec<WT>::N;
     constexpr int NW = NT / 32;
     constexpr int M = CH * VEC;   // columns owned per thread
+    constexpr int M4 = M / 4;
+    constexpr int NRED = 4;       // row-sum buffers in flight (see the pipeline note below)
+    constexpr int FG = NT / 64;   // column-finalisation groups of 64 threads
+    static_assert(M % 4 == 0 && NT % 64 == 0, "layout");
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* ring = smem;
-    uint64_t* mbar = (uint64_t*)(smem + (size_t)RING * A.row_bytes);
-    float* red = (float*)(mbar + RING);          // [2][NW]
-    float* red2 = red + 2 * NW;                  // [NW] slow path
-    float* Lr = red2 + NW;                       // [max_rows]
-    float* srow = Lr + A.max_rows;               // [max_rows]
-    double* redd = (double*)(srow + A.max_rows);   // [NW][32] (8-byte aligned: 3NW + 2 max_rows is even)
-    __shared__ int s_flag;
+    uint64_t* mbar = (uint64_t*)(smem + (size_t)RING * A.row_bytes);   // [RING] bulk-copy arrivals
+    uint64_t* mrow = mbar + RING;                                      // [NRED] row-sum publication
+    float4* tbuf = (float4*)(mrow + NRED + ((RING + NRED) & 1));       // [2][M4][NT]
+    float* red = (float*)(tbuf + (size_t)2 * M4 * NT);                 // [NRED][NW]
+    float* red2 = red + NRED * NW;                                     // [NW] slow path
+    float* Lr = red2 + NW;                                             // [max_rows]
+    float* srow = Lr + A.max_rows;                                     // [max_rows]
+    double* redp = (double*)(srow + A.max_rows);   // [FG][64] (offset 4*(5 NW + 2 max_rows): 8-aligned)
+    __shared__ int s_flag, s_ok;
+    __shared__ float s_res;
 
     const int n = A.n;
     const int G = gridDim.x;
@@ -113,23 +167,26 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
     const int r0 = (int)((int64_t)b * n / G);
     const int r1 = (int)((int64_t)(b + 1) * n / G);
     const int nrows = r1 - r0;
+    const int c0 = r0, c1 = r1;   // this block finalises the same index range of columns
     const int NC = (n + VEC - 1) / VEC;
     const unsigned char* wbase = (const unsigned char*)A.w;
     const size_t pitch = (size_t)A.ld * sizeof(WT);
 
     if (tid == 0) {
         for (int s = 0; s < RING; ++s) mbar_init(&mbar[s], 1);
+        for (int s = 0; s < NRED; ++s) mbar_init(&mrow[s], NW);
         mbar_fence_init();
         s_flag = 0;
     }
     __syncthreads();
 
-    uint32_t iss = 0, it = 0;   // rows issued / consumed by this block, all sweeps
-    auto issue_row = [&](int q) {   // q = local row index; thread 0 only
+    uint32_t iss = 0, it = 0;   // rows issued / consumed by this block, over all sweeps
+    unsigned nbar = 0;          // grid barriers passed
+    int rphase = 0;             // sweeps of earlier steps (selects the residual word)
+    auto issue_row = [&](int q) {   // thread 0 only
         const uint32_t slot = iss % RING;
         mbar_arrive_expect_tx(&mbar[slot], A.row_bytes);
-        bulk_g2s(ring + (size_t)slot * A.row_bytes, wbase + (size_t)(r0 + q) * pitch, A.row_bytes,
-                 &mbar[slot]);
+        bulk_g2s(ring + (size_t)slot * A.row_bytes, wbase + (size_t)(r0 + q) * pitch, A.row_bytes, &mbar[slot]);
         ++iss;
     };
     auto drain = [&]() {
@@ -139,8 +196,11 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
         }
         __syncthreads();
     };
+    auto gsync = [&]() -> bool {
+        ++nbar;
+        return grid_sync(A.bar, nbar * (unsigned)G, A.err, &s_ok);
+    };
 
-    // column ownership
     int cidx[CH];
     int nval[CH];
 #pragma unroll
@@ -149,7 +209,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
         nval[k] = cidx[k] < NC ? min(VEC, n - cidx[k] * VEC) : 0;
     }
 
-    float S[M], vh[M], vc[M], t[M];
+    float S[M], vh[M], vc[M];
     auto load_cols = [&]() {
 #pragma unroll
         for (int k = 0; k < CH; ++k)
@@ -158,15 +218,106 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
                 const int j = cidx[k] * VEC + e;
                 const bool ok = e < nval[k];
                 vh[k * VEC + e] = ok ? __ldcg(A.Vh + j) : 0.0f;
-                vc[k * VEC + e] = ok ? __ldcg(A.Vc + j) : 0.0f;
+                vc[k * VEC + e] = ok ? __ldcg(A.Vc + j) : 0.0f;   // c = 0 masks the column
             }
     };
 
-    // prefetch the first rows of the first sweep
+    // Terms t_ij = 2^(p (L_ij - Lr) - Vh_j) of this thread's columns into tbuf[slot];
+    // returns the partial row sum of t_ij c_j (c_j is applied to the column sums later).
+    auto row_terms = [&](const unsigned char* rowp, float lr, float pf, int slot) -> float {
+        float sp0 = 0.0f, sp1 = 0.0f;
+#pragma unroll
+        for (int kk = 0; kk < CH; ++kk) {
+            float t[VEC];
+            if (nval[kk] == VEC) {
+                float L[VEC];
+                Vec<WT>::log2w(*(const uint4*)(rowp + (size_t)cidx[kk] * 16), L);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) t[e] = ex2_approx(fmaf(pf, L[e] - lr, -vh[kk * VEC + e]));
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) t[e] = 0.0f;
+                if (nval[kk] > 0) {
+                    float L[VEC];
+                    Vec<WT>::log2w(*(const uint4*)(rowp + (size_t)cidx[kk] * 16), L);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e)
+                        if (e < nval[kk]) t[e] = ex2_approx(fmaf(pf, L[e] - lr, -vh[kk * VEC + e]));
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < VEC; e += 2) {
+                sp0 = fmaf(t[e], vc[kk * VEC + e], sp0);
+                sp1 = fmaf(t[e + 1], vc[kk * VEC + e + 1], sp1);
+            }
+#pragma unroll
+            for (int h = 0; h < VEC / 4; ++h)
+                tbuf[((size_t)slot * M4 + kk * (VEC / 4) + h) * NT + tid] =
+                    make_float4(t[4 * h], t[4 * h + 1], t[4 * h + 2], t[4 * h + 3]);
+        }
+        return sp0 + sp1;
+    };
+
+    // Row u (consumption index) of local row q: wait for its bytes, form its terms, and
+    // publish the warp's partial row sum.
+    auto produce = [&](int q, uint32_t u, float pf) {
+        if (!mbar_wait(&mbar[u % RING], (u / RING) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
+        const float sp = row_terms(ring + (size_t)(u % RING) * A.row_bytes, Lr[q], pf, q & 1);
+        const float w = warp_sum(sp);
+        if (lane == 0) {
+            red[(u % NRED) * NW + wid] = w;
+            mbar_arrive(&mrow[u % NRED]);
+        }
+    };
+
+    // exact max shift for row q (the paper's form), block-wide; terms into tbuf[q & 1]
+    auto row_exact = [&](const unsigned char* rowp, float lr, float pf, int slot, float* gm_out) -> float {
+        float e_loc[M];
+        float mx = -INFINITY;
+#pragma unroll
+        for (int kk = 0; kk < CH; ++kk) {
+            float L[VEC];
+            if (nval[kk] > 0) Vec<WT>::log2w(*(const uint4*)(rowp + (size_t)cidx[kk] * 16), L);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const int m = kk * VEC + e;
+                float ev = -INFINITY;
+                if (e < nval[kk] && vc[m] > 0.0f) ev = fmaf(pf, L[e] - lr, -vh[m]) + log2f(vc[m]);
+                e_loc[m] = ev;
+                mx = fmaxf(mx, ev);
+            }
+        }
+        mx = warp_max(mx);
+        __syncthreads();
+        if (lane == 0) red2[wid] = mx;
+        __syncthreads();
+        float gm = -INFINITY;
+        for (int x = 0; x < NW; ++x) gm = fmaxf(gm, red2[x]);
+        float s2 = 0.0f;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            // tbuf holds terms before the column factor: divide it back out
+            const float tv = (gm > -INFINITY && vc[m] > 0.0f) ? ex2_approx(e_loc[m] - gm) : 0.0f;
+            s2 += tv;
+            e_loc[m] = vc[m] > 0.0f ? tv / vc[m] : 0.0f;
+        }
+#pragma unroll
+        for (int m4 = 0; m4 < M4; ++m4)
+            tbuf[((size_t)slot * M4 + m4) * NT + tid] =
+                make_float4(e_loc[4 * m4], e_loc[4 * m4 + 1], e_loc[4 * m4 + 2], e_loc[4 * m4 + 3]);
+        s2 = warp_sum(s2);
+        __syncthreads();
+        if (lane == 0) red2[wid] = s2;
+        __syncthreads();
+        float ss = 0.0f;
+        for (int x = 0; x < NW; ++x) ss += red2[x];
+        *gm_out = gm;
+        return ss;
+    };
+
     if (tid == 0)
         for (int q = 0; q < min(RING, nrows); ++q) issue_row(q);
 
-    int buf = 0;
     for (int k = A.k0; k < A.n_p; ++k) {
         const double p = A.P[k];
         const float pf = (float)p;
@@ -179,94 +330,44 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
         __syncthreads();
         load_cols();
         int sweeps = 0;
-        double resid = INFINITY;
+        float resid = INFINITY;
         bool done = false;
         while (!done) {
+            SA_STAMP(0);
 #pragma unroll
             for (int m = 0; m < M; ++m) S[m] = 0.0f;
             // ---------------- row pass ----------------
+            // Two-stage pipeline without block barriers: a warp forms the terms of row q+1,
+            // publishes its partial sum on mrow, then waits for every warp's partial of row
+            // q and accumulates row q's normalised terms into its column sums.  NRED = 4
+            // buffers: a warp can publish row q+3 only after all warps published q+1, i.e.
+            // after they read the sums of row q-1, the last reader of that buffer.
+            if (nrows > 0) produce(0, it, pf);
             for (int q = 0; q < nrows; ++q) {
-                const uint32_t slot = it % RING;
-                if (!mbar_wait(&mbar[slot], (it / RING) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
-                const unsigned char* rowp = ring + (size_t)slot * A.row_bytes;
-                const float lr = Lr[q];
-                float sp = 0.0f;
+                const uint32_t u = it + q;
+                if (q + 1 < nrows) produce(q + 1, u + 1, pf);
+                if (!mbar_wait(&mrow[u % NRED], (u / NRED) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
+                if (s_flag) break;
+                const float4* rv = (const float4*)(red + (u % NRED) * NW);
+                float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
-                for (int kk = 0; kk < CH; ++kk) {
-                    float L[VEC];
-                    if (nval[kk] > 0) {
-                        uint4 qv = *(const uint4*)(rowp + (size_t)cidx[kk] * 16);
-                        Vec<WT>::log2w(qv, L);
-                    }
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) {
-                        const int m = kk * VEC + e;
-                        float tv = 0.0f;
-                        if (e < nval[kk]) tv = ex2_approx(fmaf(pf, L[e] - lr, -vh[m])) * vc[m];
-                        t[m] = tv;
-                        sp += tv;
-                    }
+                for (int x = 0; x < NW / 4; ++x) {
+                    const float4 q4 = rv[x];
+                    a0 += q4.x + q4.y;
+                    a1 += q4.z + q4.w;
                 }
-                sp = warp_sum(sp);
-                if (lane == 0) red[buf * NW + wid] = sp;
-                __syncthreads();
-                if (s_flag) { drain(); return; }
-                float s = 0.0f;
-#pragma unroll
-                for (int x = 0; x < NW; ++x) s += red[buf * NW + x];
-                buf ^= 1;
-                const bool slow = !(s >= 0x1p-64f && s <= 0x1p64f);
-                if (!slow) {
-                    if (tid == 0) {
-                        srow[q] = s;
-                        if (q + RING < nrows) { fence_proxy_async_smem(); issue_row(q + RING); }
-                    }
-                    const float inv = 1.0f / s;
-#pragma unroll
-                    for (int m = 0; m < M; ++m) S[m] = fmaf(t[m], inv, S[m]);
-                } else {
-                    // exact max shift (the paper's form): recompute e, then t = 2^(e - max)
-                    float mx = -INFINITY;
-#pragma unroll
-                    for (int kk = 0; kk < CH; ++kk) {
-                        float L[VEC];
-                        if (nval[kk] > 0) {
-                            uint4 qv = *(const uint4*)(rowp + (size_t)cidx[kk] * 16);
-                            Vec<WT>::log2w(qv, L);
-                        }
-#pragma unroll
-                        for (int e = 0; e < VEC; ++e) {
-                            const int m = kk * VEC + e;
-                            float ev = -INFINITY;
-                            if (e < nval[kk]) ev = fmaf(pf, L[e] - lr, -vh[m]) + log2f(vc[m]);
-                            t[m] = ev;
-                            mx = fmaxf(mx, ev);
-                        }
-                    }
-                    mx = warp_max(mx);
-                    if (lane == 0) red2[wid] = mx;
-                    __syncthreads();
-                    float gm = -INFINITY;
-                    for (int x = 0; x < NW; ++x) gm = fmaxf(gm, red2[x]);
-                    float s2 = 0.0f;
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        t[m] = (gm > -INFINITY) ? ex2_approx(t[m] - gm) : 0.0f;
-                        s2 += t[m];
-                    }
-                    s2 = warp_sum(s2);
-                    __syncthreads();
-                    if (lane == 0) red2[wid] = s2;
-                    __syncthreads();
-                    float ss = 0.0f;
-                    for (int x = 0; x < NW; ++x) ss += red2[x];
+                float s = a0 + a1;
+                if (!(s >= 0x1p-64f && s <= 0x1p64f)) {
+                    // the stale shift left the range (uniform decision): exact max shift
+                    const float lr = Lr[q];
+                    float gm;
+                    float ss = row_exact(ring + (size_t)(u % RING) * A.row_bytes, lr, pf, q & 1, &gm);
                     if (!(gm > -INFINITY) || !(ss > 0.0f)) {
                         if (tid == 0) atomicCAS(A.err, 0, kErrNonfinite);
                         ss = 1.0f;
+                        gm = 0.0f;
                     }
-                    const float inv = 1.0f / ss;
-#pragma unroll
-                    for (int m = 0; m < M; ++m) S[m] = fmaf(t[m], inv, S[m]);
+                    s = ss;
                     if (tid == 0) {
                         // re-anchor the row reference at the exact row potential
                         const double un = p * (double)lr + (double)gm + log2((double)ss);
@@ -274,16 +375,32 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
                         Lr[q] = lrn;
                         srow[q] = (float)exp2(un - p * (double)lrn);
                         atomicAdd(A.fallback, 1);
-                        if (q + RING < nrows) { fence_proxy_async_smem(); issue_row(q + RING); }
                     }
                     __syncthreads();
+                } else if (tid == 0) {
+                    srow[q] = s;
                 }
-                ++it;
+                if (tid == 0 && q + RING < nrows) {
+                    // every warp has published row q, so all have read its slot
+                    fence_proxy_async_smem();
+                    issue_row(q + RING);
+                }
+                const float inv = 1.0f / s;
+#pragma unroll
+                for (int m4 = 0; m4 < M4; ++m4) {
+                    const float4 t4 = tbuf[((size_t)(q & 1) * M4 + m4) * NT + tid];
+                    S[4 * m4] = fmaf(t4.x, inv, S[4 * m4]);
+                    S[4 * m4 + 1] = fmaf(t4.y, inv, S[4 * m4 + 1]);
+                    S[4 * m4 + 2] = fmaf(t4.z, inv, S[4 * m4 + 2]);
+                    S[4 * m4 + 3] = fmaf(t4.w, inv, S[4 * m4 + 3]);
+                }
             }
-            // prefetch the first rows of the next sweep (same data every sweep)
+            __syncthreads();
+            if (s_flag) { drain(); return; }
+            it += nrows;
+            SA_STAMP(1);
             if (tid == 0)
-                for (int q = 0; q < min(RING, nrows); ++q) issue_row(q);
-            // column partials of this stripe
+                for (int q = 0; q < min(RING, nrows); ++q) issue_row(q);   // next sweep reads the same rows
             float* pb = A.part + (size_t)b * A.npad;
 #pragma unroll
             for (int kk = 0; kk < CH; ++kk) {
@@ -291,39 +408,43 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
 #pragma unroll
                     for (int e = 0; e < VEC; e += 4)
                         *(float4*)(pb + (size_t)cidx[kk] * VEC + e) =
-                            make_float4(S[kk * VEC + e], S[kk * VEC + e + 1], S[kk * VEC + e + 2],
-                                        S[kk * VEC + e + 3]);
+                            make_float4(S[kk * VEC + e] * vc[kk * VEC + e], S[kk * VEC + e + 1] * vc[kk * VEC + e + 1],
+                                        S[kk * VEC + e + 2] * vc[kk * VEC + e + 2],
+                                        S[kk * VEC + e + 3] * vc[kk * VEC + e + 3]);
                 }
             }
             ++sweeps;
-            if (!group_barrier(A.bar, G, A.err, kWaitTimeoutNs)) { drain(); return; }
-            // ---------------- column finalisation ----------------
-            double rmax = 0.0;
-            const int nblk = (n + 31) / 32;
-            for (int cb = b; cb < nblk; cb += G) {
-                const int j = cb * 32 + lane;
-                double acc = 0.0;
-                if (j < n) {
-                    // independent loads in flight (fixed summation order: deterministic)
+            if (!gsync()) { drain(); return; }
+            SA_STAMP(2);
+            // ---------------- column finalisation of columns [c0, c1) ----------------
+            float* rmax_word = A.rmax + ((sweeps + rphase) & 1);
+            float rmax = 0.0f;
+            for (int cb = c0; cb < c1; cb += 64) {
+                const int j = cb + (tid & 63);
+                const int grp = tid >> 6;
+                KahanF acc;
+                if (j < c1) {
                     const float* pj = A.part + j;
-                    int g = wid;
-                    for (; g + 3 * NW < G; g += 4 * NW) {
-                        const float a0 = __ldcg(pj + (size_t)g * A.npad);
-                        const float a1 = __ldcg(pj + (size_t)(g + NW) * A.npad);
-                        const float a2 = __ldcg(pj + (size_t)(g + 2 * NW) * A.npad);
-                        const float a3 = __ldcg(pj + (size_t)(g + 3 * NW) * A.npad);
-                        acc += ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
+                    for (int g0 = grp; g0 < G; g0 += FG * 20) {
+                        float a[20];
+#pragma unroll
+                        for (int x = 0; x < 20; ++x) {
+                            const int g = g0 + x * FG;
+                            a[x] = g < G ? __ldcg(pj + (size_t)g * A.npad) : 0.0f;
+                        }
+#pragma unroll
+                        for (int x = 0; x < 20; ++x) acc.add(a[x]);
                     }
-                    for (; g < G; g += NW) acc += (double)__ldcg(pj + (size_t)g * A.npad);
                 }
-                redd[wid * 32 + lane] = acc;
+                redp[grp * 64 + (tid & 63)] = (double)acc.s - (double)acc.c;
                 __syncthreads();
-                if (wid == 0 && j < n) {
+                if (tid < 64 && j < c1) {
                     double Sj = 0.0;
-                    for (int x = 0; x < NW; ++x) Sj += redd[x * 32 + lane];
+#pragma unroll
+                    for (int x = 0; x < FG; ++x) Sj += redp[x * 64 + tid];
                     if (!(Sj > 0.0) || !isfinite(Sj)) atomicCAS(A.err, 0, kErrNonfinite);
                     const double d = Sj - 1.0;
-                    rmax = fmax(rmax, fabs(d));
+                    rmax = fmaxf(rmax, (float)fabs(d));
                     double lg;
                     if (fabs(d) < 1e-3) {
                         // log2(1 + d) by its series, FP64 (|d| < 1e-3: 5 terms reach 1e-17)
@@ -340,24 +461,28 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
                 }
                 __syncthreads();
             }
-            if (wid == 0) {
+            if (wid < 2) {
                 rmax = warp_max(rmax);
-                if (lane == 0) A.rpart[b] = rmax;
+                if (lane == 0 && rmax > 0.0f) atomicMax((unsigned*)rmax_word, __float_as_uint(rmax));
             }
-            if (!group_barrier(A.bar, G, A.err, kWaitTimeoutNs)) { drain(); return; }
+            if (!gsync()) { drain(); return; }
+            SA_STAMP(3);
             // ---------------- decision (identical in every block) ----------------
-            double r = 0.0;
-            for (int g = lane; g < G; g += 32) r = fmax(r, __ldcg(A.rpart + g));
-            r = warp_max(r);
-            resid = r;
+            if (tid == 0) {
+                s_res = __uint_as_float(ld_acquire((const unsigned*)rmax_word));
+                if (b == 0) A.rmax[((sweeps + rphase) + 1) & 1] = 0.0f;   // next sweep's word
+            }
+            __syncthreads();
+            resid = s_res;
             done = (resid <= A.tol) || (sweeps >= A.max_sweeps);
             if (!done) load_cols();
+            SA_STAMP(4);
         }
-        // step finished: write U for this stripe, record the step
+        rphase += sweeps;
         for (int q = tid; q < nrows; q += NT) {
-            double u = p * (double)Lr[q] + log2((double)srow[q]);
-            if (A.f32_potentials) u = (double)(float)u;
-            A.U[r0 + q] = u;
+            double uu = p * (double)Lr[q] + log2((double)srow[q]);
+            if (A.f32_potentials) uu = (double)(float)uu;
+            A.U[r0 + q] = uu;
         }
         if (b == 0 && tid == 0) {
             A.sweeps_out[k] = sweeps;
@@ -366,25 +491,22 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
         if (k + 1 < A.n_p) {
             // warm start of the next step: (U, V) *= p_{k+1}/p_k unless v is kept
             const double f = A.keep_v ? 1.0 : A.P[k + 1] / p;
-            const int nblk = (n + 31) / 32;
-            for (int cb = b; cb < nblk; cb += G) {
-                const int j = cb * 32 + lane;
-                if (wid != 0 || j >= n) continue;
+            for (int j = c0 + tid; j < c1; j += NT) {
                 double v = A.V[j] * f;
                 A.V[j] = v;
                 float h = (float)v;
                 A.Vh[j] = h;
                 A.Vc[j] = ex2_approx((float)((double)h - v));
             }
-            if (!group_barrier(A.bar, G, A.err, kWaitTimeoutNs)) { drain(); return; }
+            if (!gsync()) { drain(); return; }
         }
     }
     drain();
 }
 
-template <typename WT, int NT, int CH, int RING>
+template <typename WT, int NT, int CH, int RING, int R>
 sa_status launch_fused(sa_ctx* ctx, const FusedArgs& args, size_t smem, int* grid_out) {
-    auto kern = fused_kernel<WT, NT, CH, RING>;
+    auto kern = fused_kernel<WT, NT, CH, RING, R>;
     SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
@@ -401,34 +523,50 @@ sa_status launch_fused(sa_ctx* ctx, const FusedArgs& args, size_t smem, int* gri
     FusedArgs a = args;
     void* params[] = {&a};
     SA_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(NT), params, smem, ctx->stream));
+    count_launch();
     return SA_OK;
 }
 
 struct FusedCfg {
-    int nt, ch, ring;
+    int nt, ch, ring, r;
 };
 
-FusedCfg pick_cfg(const sa_matrix* a, size_t smem_optin) {
+#ifndef SA_ROWS_PER_SYNC
+#define SA_ROWS_PER_SYNC 2
+#endif
+constexpr int kRowsPerSync = SA_ROWS_PER_SYNC;
+
+size_t fused_smem_bytes(const FusedCfg& c, unsigned row_bytes, int vec, int max_rows) {
+    const int nw = c.nt / 32;
+    const int m4 = c.ch * vec / 4;
+    const size_t head = (size_t)c.ring * row_bytes + 8 * (size_t)(c.ring + 4 + ((c.ring + 4) & 1));
+    const size_t fg = c.nt / 64;
+    return head + 16 * (size_t)2 * m4 * c.nt + 4 * (size_t)(4 * nw + nw + 2 * max_rows) + 8 + 8 * fg * 64 + 128;
+}
+
+FusedCfg pick_cfg(const sa_matrix* a, size_t smem_optin, int max_rows) {
     const int vec = 16 / wbytes(a->wtype);
     const int nc = (a->n + vec - 1) / vec;
-    FusedCfg c{0, 0, 0};
-    if (nc <= 128) c = {128, 1, 0};
-    else if (nc <= 256) c = {256, 1, 0};
-    else if (nc <= 512) c = {512, 1, 0};
-    else if (nc <= 1024) c = {512, 2, 0};
-    else if (nc <= 1536) c = {512, 3, 0};
+    FusedCfg c{0, 0, 0, kRowsPerSync};
+    if (nc <= 128) c = {128, 1, 0, kRowsPerSync};
+    else if (nc <= 256) c = {256, 1, 0, kRowsPerSync};
+    else if (nc <= 512) c = {512, 1, 0, kRowsPerSync};
+    else if (nc <= 1024) c = {512, 2, 0, kRowsPerSync};
+    else if (nc <= 1536) c = {512, 3, 0, kRowsPerSync};
     else return c;
-    const size_t row_bytes = align_up((size_t)a->n * wbytes(a->wtype), 16);
-    const size_t budget = smem_optin > 16384 ? smem_optin - 16384 : 0;
-    int ring = (int)(budget / row_bytes);
-    if (ring > 8) ring = 8;
-    if (ring >= 6) ring = 6;
-    else if (ring >= 4) ring = 4;
-    else if (ring >= 2) ring = 2;
-    else ring = 0;
-    c.ring = ring;
-    if (ring == 0) c.nt = 0;
+    const unsigned row_bytes = (unsigned)align_up((size_t)a->n * wbytes(a->wtype), 16);
+    for (int ring : {6, 4, 2}) {
+        c.ring = ring;
+        if (fused_smem_bytes(c, row_bytes, vec, max_rows) <= smem_optin) return c;
+    }
+    c.nt = 0;
     return c;
+}
+
+int fused_max_rows(const sa_ctx* ctx, int n) {
+    // any grid has >= min(num_sms, n/8) blocks, so no stripe exceeds this many rows
+    const int gmin = std::max(1, std::min(ctx->num_sms, n / 8));
+    return (n + gmin - 1) / gmin + 1;
 }
 
 }  // namespace
@@ -438,13 +576,14 @@ bool fused_supported(const sa_ctx* ctx, const sa_matrix* a) {
     if (((uintptr_t)a->w & 15) != 0) return false;
     if (((size_t)a->ld * sz) % 16 != 0) return false;
     if ((size_t)a->ld * sz < align_up((size_t)a->n * sz, 16)) return false;
-    return pick_cfg(a, ctx->smem_optin).nt > 0;
+    return pick_cfg(a, ctx->smem_optin, fused_max_rows(ctx, a->n)).nt > 0;
 }
 
 sa_status scale_fused(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double* U,
                       double* V, sa_scale_info* info) {
     const int n = a->n;
-    FusedCfg cfg = pick_cfg(a, ctx->smem_optin);
+    const int max_rows = fused_max_rows(ctx, n);
+    FusedCfg cfg = pick_cfg(a, ctx->smem_optin, max_rows);
     if (cfg.nt == 0) {
         set_error("fused sweep: n=%d not supported by the fused kernel", n);
         return SA_E_UNSUPPORTED;
@@ -452,16 +591,13 @@ sa_status scale_fused(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, d
     cudaStream_t st = ctx->stream;
     const int G_max = ctx->num_sms * 2;
     const int npad = (int)align_up((size_t)n, 32);
-    // any grid has >= min(num_sms, n/8) blocks, so no stripe exceeds this many rows
-    const int gmin = std::max(1, std::min(ctx->num_sms, n / 8));
-    const int max_rows = (n + gmin - 1) / gmin + 1;
     size_t need = (size_t)G_max * npad * 4 + (size_t)G_max * 8 + 2 * align_up((size_t)n * 4, 256) +
                   (size_t)o->n_p * 16 + 8192;
     sa_status rc = ctx->ws.reserve(need);
     if (rc) return rc;
     Carve cv(ctx->ws.ptr);
     float* part = cv.take<float>((size_t)G_max * npad);
-    double* rpart = cv.take<double>(G_max);
+    float* rmax = cv.take<float>(2);
     float* Vh = cv.take<float>(n);
     float* Vc = cv.take<float>(n);
     double* P = cv.take<double>(o->n_p);
@@ -472,6 +608,7 @@ sa_status scale_fused(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, d
     int* fallback = cv.take<int>(1);
     SA_CUDA(cudaMemcpyAsync(P, o->p, o->n_p * sizeof(double), cudaMemcpyHostToDevice, st));
     SA_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+    SA_CUDA(cudaMemsetAsync(rmax, 0, 2 * sizeof(float), st));
     SA_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     SA_CUDA(cudaMemsetAsync(fallback, 0, sizeof(int), st));
     SA_CUDA(cudaMemsetAsync(sweeps_out, 0, o->n_p * sizeof(int), st));
@@ -504,25 +641,23 @@ sa_status scale_fused(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, d
     args.Vc = Vc;
     args.part = part;
     args.npad = npad;
-    args.rpart = rpart;
+    args.rmax = rmax;
     args.bar = bar;
     args.err = err;
     args.fallback = fallback;
     args.sweeps_out = sweeps_out;
     args.resid_out = resid_out;
     args.max_rows = max_rows;
-    const int NW = cfg.nt / 32;
-    size_t smem = (size_t)cfg.ring * args.row_bytes + cfg.ring * 8 + (3 * NW) * 4 +
-                  (size_t)2 * max_rows * 4 + NW * 32 * 8 + 64;
-    int G = G_max;
+    const size_t smem = fused_smem_bytes(cfg, args.row_bytes, 16 / wbytes(a->wtype), max_rows);
+    int G = ctx->max_grid > 0 ? std::min(G_max, ctx->max_grid) : G_max;
     const bool i16 = a->wtype == SA_I16;
     cudaEvent_t ev0, ev1;
     SA_CUDA(cudaEventCreate(&ev0));
     SA_CUDA(cudaEventCreate(&ev1));
     SA_CUDA(cudaEventRecord(ev0, st));
 #define SA_LAUNCH(NT_, CH_, RING_)                                                              \
-    rc = i16 ? launch_fused<int16_t, NT_, CH_, RING_>(ctx, args, smem, &G)                    \
-             : launch_fused<int32_t, NT_, CH_, RING_>(ctx, args, smem, &G)
+    rc = i16 ? launch_fused<int16_t, NT_, CH_, RING_, kRowsPerSync>(ctx, args, smem, &G)       \
+             : launch_fused<int32_t, NT_, CH_, RING_, kRowsPerSync>(ctx, args, smem, &G)
     if (cfg.ring == 6) {
         if (cfg.nt == 128) SA_LAUNCH(128, 1, 6);
         else if (cfg.nt == 256) SA_LAUNCH(256, 1, 6);

@@ -56,18 +56,33 @@ def batch_scale(ctx, mats, ps, tol=1e-6, sweeps=20000):
 def test_batch_matches_oracle(ctx, dtype):
     sizes = [1, 2, 7, 16, 33, 100, 129, 250, 300, 512, 64, 17]
     mats = [W.uniform(n, 1, 1000, 1000 + k, dtype=dtype) for k, n in enumerate(sizes)]
-    ps = [2.0 ** k for k in range(8)]
+    ps = [2.0 ** k for k in range(6)]
     rc, us, vs, sw, st = batch_scale(ctx, mats, ps)
     assert rc == 0 and np.all(st == 0), (rc, st)
     for m, u, v in zip(mats, us, vs):
         b = oracle.log_weights(m.astype(np.int64))
         r, c = oracle.sums(b, ps[-1], u, v)
         err = max(np.abs(r - 1).max(), np.abs(c - 1).max())
-        assert err < 2 * ps[-1] * np.log(2) * 1e-6 + 2e-6, (m.shape, err)
-        uo, vo, *_ = oracle.sinkhorn(b, ps, 1e-6, 20000)
+        assert err < 2 * ps[-1] * np.log(2) * 1e-6 + 4e-6, (m.shape, err)
+        uo, vo, _, _, sto = oracle.sinkhorn(b, ps, 1e-6, 20000)
+        assert sto == 0
         xo = oracle.xmatrix(b, ps[-1], uo, vo)
         xg = oracle.xmatrix(b, ps[-1], u, v)
-        assert np.max(np.abs(xg - xo)) < 5e-3
+        assert np.max(np.abs(xg - xo)) < 1e-4
+
+
+def test_batch_not_converged_like_oracle(ctx):
+    # small uniform instances at p = 128 are nearly decomposable: the oracle hits the
+    # cap on exactly these, and so must the batch (status 1, SA_E_NOT_CONVERGED overall)
+    sizes = [7, 16, 17, 100, 300]
+    mats = [W.uniform(n, 1, 1000, 1000 + k, dtype=np.int16) for k, n in zip([2, 3, 11, 5, 8], sizes)]
+    ps = [2.0 ** k for k in range(8)]
+    rc, us, vs, sw, st = batch_scale(ctx, mats, ps, sweeps=3000)
+    assert rc == L.SA_E_NOT_CONVERGED
+    for m, s in zip(mats, st):
+        b = oracle.log_weights(m.astype(np.int64))
+        sto = oracle.sinkhorn(b, ps, 1e-6, 3000)[4]
+        assert s == (1 if sto == oracle.NOT_CONVERGED else 0), (m.shape, s, sto)
 
 
 def test_alone_equals_in_batch(ctx):
