@@ -141,6 +141,31 @@ sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* opts, d
                    double* d_v, sa_scale_info* info);
 
 /*
+ * sa_scale_noalloc: sa_scale on the fused kernel without allocating anything.  The paper
+ * has no counterpart: this is a deployment entry point for callers that cannot allocate
+ * device memory when they scale -- callers whose memory is planned up front (a fixed
+ * budget or a pre-sized pool) and callers that cannot afford the device-wide
+ * synchronisation that cudaMalloc/cudaFree bring.  The fused kernel's scratch (column
+ * partials, FP32 head and factor of v, schedule, barrier and status words) then lives
+ * in a static device array of the library, about 2.6 MiB, which every GPU that loads the
+ * library holds until the process exits.  The caller still passes the matrix, the
+ * potentials d_u, d_v (device FP64[n], as for sa_scale) and a CUDA stream (NULL: the
+ * legacy default stream); the device is the calling thread's current device.
+ *   Limits: n <= 4096, at most 64 p steps, MIXED or FP32 precision, and a layout the
+ *   fused kernel reads (16-byte aligned base and row pitch).  Anything else returns
+ *   SA_E_UNSUPPORTED or SA_E_INVALID with a message and runs nothing.
+ *   The first call on a device looks the array's device address up (once per device,
+ *   with that device current); make that first call before any stream capture.
+ *   All calls share the array and find the previous call's contents in it; each call
+ *   clears what must start at zero, but calls whose work overlaps on the GPU race on
+ *   the array, so serialise them (one stream, or events).
+ *   Synchronises the stream before returning; info->kernel_ms is 0 (no events are made).
+ *   It calls no cudaMalloc, cudaFree, cudaHostAlloc or other allocating routine.
+ */
+sa_status sa_scale_noalloc(const sa_matrix* a, const sa_scale_opts* opts, void* cuda_stream,
+                           double* d_u, double* d_v, sa_scale_info* info);
+
+/*
  * sa_verify: FP64 row and column sums of X(p) from the potentials (one read of A).
  *   d_rows, d_cols  device FP64[n] outputs (either may be NULL).
  *   max_row_err, max_col_err  host outputs max |sum - 1| (either may be NULL).

@@ -81,6 +81,8 @@ SIGNATURES = {
     "sa_kernel_launches": (ctypes.c_int64, []),
     "sa_scale": (ctypes.c_int, [_VP, ctypes.POINTER(sa_matrix), ctypes.POINTER(sa_scale_opts), _VP, _VP,
                                 ctypes.POINTER(sa_scale_info)]),
+    "sa_scale_noalloc": (ctypes.c_int, [ctypes.POINTER(sa_matrix), ctypes.POINTER(sa_scale_opts), _VP, _VP, _VP,
+                                        ctypes.POINTER(sa_scale_info)]),
     "sa_verify": (ctypes.c_int, [_VP, ctypes.POINTER(sa_matrix), ctypes.c_double, _VP, _VP, _VP, _VP, _DP, _DP]),
     "sa_prune": (ctypes.c_int, [_VP, ctypes.POINTER(sa_matrix), ctypes.c_double, _VP, _VP, ctypes.c_double,
                                 ctypes.c_int32, ctypes.POINTER(sa_csr), _DP]),

@@ -31,6 +31,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "sa_internal.h"
@@ -348,15 +350,8 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
                 if (q + 1 < nrows) produce(q + 1, u + 1, pf);
                 if (!mbar_wait(&mrow[u % NRED], (u / NRED) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
                 if (s_flag) break;
-                const float4* rv = (const float4*)(red + (u % NRED) * NW);
-                float a0 = 0.0f, a1 = 0.0f;
-#pragma unroll
-                for (int x = 0; x < NW / 4; ++x) {
-                    const float4 q4 = rv[x];
-                    a0 += q4.x + q4.y;
-                    a1 += q4.z + q4.w;
-                }
-                float s = a0 + a1;
+                // lane x holds warp x's partial: one load and a warp reduction
+                float s = warp_sum(lane < NW ? red[(u % NRED) * NW + lane] : 0.0f);
                 if (!(s >= 0x1p-64f && s <= 0x1p64f)) {
                     // the stale shift left the range (uniform decision): exact max shift
                     const float lr = Lr[q];
@@ -519,6 +514,10 @@ sa_status launch_fused(sa_ctx* ctx, const FusedArgs& args, size_t smem, int* gri
     const int gmax_rows = args.n / 8 > 0 ? args.n / 8 : 1;
     if (G > gmax_rows) G = gmax_rows;
     if (*grid_out > 0 && *grid_out < G) G = *grid_out;
+    if ((args.n + G - 1) / G > args.max_rows) {
+        set_error("fused sweep: grid of %d blocks leaves stripes longer than %d rows", G, args.max_rows);
+        return SA_E_UNSUPPORTED;
+    }
     *grid_out = G;
     FusedArgs a = args;
     void* params[] = {&a};
@@ -544,14 +543,14 @@ size_t fused_smem_bytes(const FusedCfg& c, unsigned row_bytes, int vec, int max_
     return head + 16 * (size_t)2 * m4 * c.nt + 4 * (size_t)(4 * nw + nw + 2 * max_rows) + 8 + 8 * fg * 64 + 128;
 }
 
-FusedCfg pick_cfg(const sa_matrix* a, size_t smem_optin, int max_rows) {
+FusedCfg pick_cfg(const sa_matrix* a, size_t smem_optin, int max_rows, int wide = 1) {
     const int vec = 16 / wbytes(a->wtype);
     const int nc = (a->n + vec - 1) / vec;
     FusedCfg c{0, 0, 0, kRowsPerSync};
     if (nc <= 128) c = {128, 1, 0, kRowsPerSync};
     else if (nc <= 256) c = {256, 1, 0, kRowsPerSync};
     else if (nc <= 512) c = {512, 1, 0, kRowsPerSync};
-    else if (nc <= 1024) c = {512, 2, 0, kRowsPerSync};
+    else if (nc <= 1024) c = wide ? FusedCfg{1024, 1, 0, kRowsPerSync} : FusedCfg{512, 2, 0, kRowsPerSync};
     else if (nc <= 1536) c = {512, 3, 0, kRowsPerSync};
     else return c;
     const unsigned row_bytes = (unsigned)align_up((size_t)a->n * wbytes(a->wtype), 16);
@@ -564,8 +563,9 @@ FusedCfg pick_cfg(const sa_matrix* a, size_t smem_optin, int max_rows) {
 }
 
 int fused_max_rows(const sa_ctx* ctx, int n) {
-    // any grid has >= min(num_sms, n/8) blocks, so no stripe exceeds this many rows
-    const int gmin = std::max(1, std::min(ctx->num_sms, n / 8));
+    // any grid has >= min(num_sms, n/8, max_grid) blocks, so no stripe exceeds this many rows
+    int gmin = std::max(1, std::min(ctx->num_sms, n / 8));
+    if (ctx->max_grid > 0) gmin = std::max(1, std::min(gmin, ctx->max_grid));
     return (n + gmin - 1) / gmin + 1;
 }
 
@@ -583,7 +583,7 @@ sa_status scale_fused(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, d
                       double* V, sa_scale_info* info) {
     const int n = a->n;
     const int max_rows = fused_max_rows(ctx, n);
-    FusedCfg cfg = pick_cfg(a, ctx->smem_optin, max_rows);
+    FusedCfg cfg = pick_cfg(a, ctx->smem_optin, max_rows, ctx->fused_wide);
     if (cfg.nt == 0) {
         set_error("fused sweep: n=%d not supported by the fused kernel", n);
         return SA_E_UNSUPPORTED;
@@ -661,11 +661,13 @@ sa_status scale_fused(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, d
     if (cfg.ring == 6) {
         if (cfg.nt == 128) SA_LAUNCH(128, 1, 6);
         else if (cfg.nt == 256) SA_LAUNCH(256, 1, 6);
+        else if (cfg.nt == 1024) SA_LAUNCH(1024, 1, 6);
         else if (cfg.ch == 1) SA_LAUNCH(512, 1, 6);
         else if (cfg.ch == 2) SA_LAUNCH(512, 2, 6);
         else SA_LAUNCH(512, 3, 6);
     } else if (cfg.ring == 4) {
-        if (cfg.ch == 2) SA_LAUNCH(512, 2, 4);
+        if (cfg.nt == 1024) SA_LAUNCH(1024, 1, 4);
+        else if (cfg.ch == 2) SA_LAUNCH(512, 2, 4);
         else SA_LAUNCH(512, 3, 4);
     } else {
         SA_LAUNCH(512, 3, 2);
@@ -733,3 +735,203 @@ void launch_split_v(const double* V, float* Vh, float* Vc, int n, cudaStream_t s
 }
 
 }  // namespace sa
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of the fused scaling (sa_scale_noalloc).
+//
+// Some callers cannot allocate device memory at the point where they need a scaling:
+// code running while a CUDA graph is being captured, or inside a host callback, or
+// under an allocator that must not grow, or with a memory budget that is fixed up front.
+// For them the scratch of the fused kernel (column partials, the FP32 head/factor of V,
+// the schedule, barrier and status words) lives in this file-scope device array instead
+// of a context workspace.  Every device that loads the library holds the array until
+// the process exits.  All calls share it: two calls whose work overlaps on the GPU race
+// on it and must be serialised by the caller (one stream, or events).
+// ---------------------------------------------------------------------------------------
+namespace sa {
+namespace {
+
+constexpr int kNoAllocMaxN = 4096;      // largest n accepted
+constexpr int kNoAllocMaxGrid = 160;    // grid cap (one block per SM on GB300: 152)
+constexpr int kNoAllocMaxSteps = 64;    // longest p schedule accepted
+constexpr size_t kNoAllocPartFloats = (size_t)kNoAllocMaxGrid * kNoAllocMaxN;
+constexpr size_t kNoAllocBytes =
+    kNoAllocPartFloats * 4 + 2 * (size_t)kNoAllocMaxN * 4 + 2 * (size_t)kNoAllocMaxSteps * 8 +
+    (size_t)kNoAllocMaxSteps * 4 + 256 * 4;   // about 2.6 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocDevice {
+    bool ready = false;
+    unsigned char* scratch = nullptr;   // device address of g_noalloc_scratch on this device
+    int num_sms = 0;
+    size_t smem_optin = 0;
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[64];
+
+}  // namespace
+
+}  // namespace sa
+
+using namespace sa;
+
+extern "C" sa_status sa_scale_noalloc(const sa_matrix* a, const sa_scale_opts* o, void* cuda_stream, double* d_u,
+                                      double* d_v, sa_scale_info* info) {
+    if (!a || !a->w || !o || !o->p || !d_u || !d_v) { set_error("null argument"); return SA_E_INVALID; }
+    if (a->n <= 0 || a->ld < a->n || (a->wtype != SA_I16 && a->wtype != SA_I32)) { set_error("bad matrix"); return SA_E_INVALID; }
+    if (a->n > kNoAllocMaxN) {
+        set_error("sa_scale_noalloc: n=%d exceeds the static scratch limit n <= %d", a->n, kNoAllocMaxN);
+        return SA_E_UNSUPPORTED;
+    }
+    if (o->n_p <= 0 || o->n_p > kNoAllocMaxSteps) {
+        set_error("sa_scale_noalloc: schedule of %d steps (1..%d supported)", o->n_p, kNoAllocMaxSteps);
+        return o->n_p <= 0 ? SA_E_INVALID : SA_E_UNSUPPORTED;
+    }
+    for (int k = 0; k < o->n_p; ++k)
+        if (!(o->p[k] > 0) || !std::isfinite(o->p[k]) || (k > 0 && !(o->p[k] > o->p[k - 1]))) {
+            set_error("p schedule must be finite, positive and increasing");
+            return SA_E_INVALID;
+        }
+    if (!(o->tol > 0) || o->max_sweeps_per_p <= 0 || o->resume_from < 0 || o->resume_from >= o->n_p ||
+        o->prec == SA_PREC_FP64) {
+        set_error("sa_scale_noalloc: bad tol/cap/resume or FP64 precision (fused kernel only)");
+        return SA_E_INVALID;
+    }
+    int dev = 0;
+    SA_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { set_error("device index %d out of range", dev); return SA_E_INVALID; }
+    NoAllocDevice nd;
+    {
+        // once per device, with that device current: the device address of the array
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        NoAllocDevice& d = g_noalloc_dev[dev];
+        if (!d.ready) {
+            void* ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+            cudaDeviceProp prop;
+            e = cudaGetDeviceProperties(&prop, dev);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+            d.scratch = (unsigned char*)ptr;
+            d.num_sms = prop.multiProcessorCount;
+            d.smem_optin = prop.sharedMemPerBlockOptin;
+            d.ready = true;
+        }
+        nd = d;
+    }
+    // a context on the stack: no workspace is reserved through it
+    sa_ctx ctx;
+    ctx.device = dev;
+    ctx.stream = (cudaStream_t)cuda_stream;
+    ctx.num_sms = nd.num_sms;
+    ctx.smem_optin = nd.smem_optin;
+    ctx.max_grid = kNoAllocMaxGrid;
+    const int n = a->n;
+    if (!fused_supported(&ctx, a)) {
+        set_error("sa_scale_noalloc: layout not supported by the fused kernel (16-byte aligned rows needed)");
+        return SA_E_UNSUPPORTED;
+    }
+    const int max_rows = fused_max_rows(&ctx, n);
+    FusedCfg cfg = pick_cfg(a, ctx.smem_optin, max_rows, 0);
+    cudaStream_t st = ctx.stream;
+    const int npad = (int)align_up((size_t)n, 32);
+    // carve the static array
+    unsigned char* base = nd.scratch;
+    float* part = (float*)base;
+    float* Vh = part + kNoAllocPartFloats;
+    float* Vc = Vh + kNoAllocMaxN;
+    double* P = (double*)(Vc + kNoAllocMaxN);
+    double* resid_out = P + kNoAllocMaxSteps;
+    int* sweeps_out = (int*)(resid_out + kNoAllocMaxSteps);
+    unsigned* words = (unsigned*)(sweeps_out + kNoAllocMaxSteps);   // bar[2], err, fallback, rmax[2]
+    unsigned* bar = words;
+    int* err = (int*)(words + 2);
+    int* fallback = (int*)(words + 3);
+    float* rmax = (float*)(words + 4);
+    if ((size_t)npad * kNoAllocMaxGrid > kNoAllocPartFloats) { set_error("scratch too small"); return SA_E_UNSUPPORTED; }
+    // the previous call's contents stay in the array: clear what must start at zero
+    SA_CUDA(cudaMemcpyAsync(P, o->p, o->n_p * sizeof(double), cudaMemcpyHostToDevice, st));
+    SA_CUDA(cudaMemsetAsync(words, 0, 8 * sizeof(unsigned), st));
+    SA_CUDA(cudaMemsetAsync(sweeps_out, 0, o->n_p * sizeof(int), st));
+    const int k0 = o->resume_from;
+    if (k0 > 0) {
+        launch_scale_vec(d_u, n, kLog2e, st);
+        launch_scale_vec(d_v, n, kLog2e, st);
+        if (!o->warm_keep_v) launch_scale_vec(d_v, n, o->p[k0] / o->p[k0 - 1], st);
+    } else {
+        SA_CUDA(cudaMemsetAsync(d_u, 0, n * sizeof(double), st));
+        SA_CUDA(cudaMemsetAsync(d_v, 0, n * sizeof(double), st));
+    }
+    launch_split_v(d_v, Vh, Vc, n, st);
+    FusedArgs args{};
+    args.w = a->w;
+    args.n = n;
+    args.ld = a->ld;
+    args.row_bytes = (unsigned)align_up((size_t)n * wbytes(a->wtype), 16);
+    args.P = P;
+    args.k0 = k0;
+    args.n_p = o->n_p;
+    args.tol = o->tol;
+    args.max_sweeps = o->max_sweeps_per_p;
+    args.keep_v = o->warm_keep_v;
+    args.f32_potentials = o->prec == SA_PREC_FP32;
+    args.U = d_u;
+    args.V = d_v;
+    args.Vh = Vh;
+    args.Vc = Vc;
+    args.part = part;
+    args.npad = npad;
+    args.rmax = rmax;
+    args.bar = bar;
+    args.err = err;
+    args.fallback = fallback;
+    args.sweeps_out = sweeps_out;
+    args.resid_out = resid_out;
+    args.max_rows = max_rows;
+    const size_t smem = fused_smem_bytes(cfg, args.row_bytes, 16 / wbytes(a->wtype), max_rows);
+    int G = kNoAllocMaxGrid;
+    const bool i16 = a->wtype == SA_I16;
+    sa_status rc;
+    // n <= 4096: at most 512 chunks, one per thread
+    if (cfg.nt == 128) rc = i16 ? launch_fused<int16_t, 128, 1, 6, kRowsPerSync>(&ctx, args, smem, &G)
+                                : launch_fused<int32_t, 128, 1, 6, kRowsPerSync>(&ctx, args, smem, &G);
+    else if (cfg.nt == 256) rc = i16 ? launch_fused<int16_t, 256, 1, 6, kRowsPerSync>(&ctx, args, smem, &G)
+                                     : launch_fused<int32_t, 256, 1, 6, kRowsPerSync>(&ctx, args, smem, &G);
+    else if (cfg.ch == 1) rc = i16 ? launch_fused<int16_t, 512, 1, 6, kRowsPerSync>(&ctx, args, smem, &G)
+                                   : launch_fused<int32_t, 512, 1, 6, kRowsPerSync>(&ctx, args, smem, &G);
+    else rc = i16 ? launch_fused<int16_t, 512, 2, 6, kRowsPerSync>(&ctx, args, smem, &G)
+                  : launch_fused<int32_t, 512, 2, 6, kRowsPerSync>(&ctx, args, smem, &G);
+    if (rc) return rc;
+    // results through pageable host memory (no pinned allocation)
+    int h_words[4] = {0, 0, 0, 0};
+    int h_sw[kNoAllocMaxSteps];
+    double h_rs[kNoAllocMaxSteps];
+    SA_CUDA(cudaMemcpyAsync(h_words, words, sizeof(h_words), cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaMemcpyAsync(h_sw, sweeps_out, o->n_p * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaMemcpyAsync(h_rs, resid_out, o->n_p * sizeof(double), cudaMemcpyDeviceToHost, st));
+    launch_scale_vec(d_u, n, kLn2, st);
+    launch_scale_vec(d_v, n, kLn2, st);
+    SA_CUDA(cudaStreamSynchronize(st));
+    int64_t total = 0;
+    int conv = 1;
+    for (int k = k0; k < o->n_p; ++k) {
+        total += h_sw[k];
+        if (!(h_rs[k] <= o->tol)) conv = 0;
+    }
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->sweeps_total = total;
+        info->residual = h_rs[o->n_p - 1];
+        info->p_final = o->p[o->n_p - 1];
+        info->converged = conv;
+        info->steps_done = o->n_p - k0;
+        info->fallback_rows = h_words[3];
+        info->kernel_used = SA_KERNEL_FUSED;
+        info->kernel_ms = 0.0;
+    }
+    if (h_words[2] == kErrTimeout) { set_error("sa_scale_noalloc: a bounded device wait timed out"); return SA_E_TIMEOUT; }
+    if (h_words[2] == kErrNonfinite) { set_error("sa_scale_noalloc: a row or column lost all mass"); return SA_E_NONFINITE; }
+    return conv ? SA_OK : SA_E_NOT_CONVERGED;
+}
+
