@@ -191,7 +191,10 @@ sa_status sa_create(sa_ctx** ctx, int device, void* cuda_stream) {
     if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDeviceProperties"); }
     c->num_sms = prop.multiProcessorCount;
     c->smem_optin = prop.sharedMemPerBlockOptin;
-    if (const char* wv = getenv("SA_FUSED_WIDE")) c->fused_wide = atoi(wv) != 0;
+    if (const char* wv = getenv("SA_FUSED_NT")) {
+        const int v = atoi(wv);
+        if (v == 256 || v == 512) c->fused_nt = v;
+    }
     if (!prop.cooperativeLaunch) { delete c; set_error("device lacks cooperative launch"); return SA_E_UNSUPPORTED; }
     *ctx = c;
     return SA_OK;

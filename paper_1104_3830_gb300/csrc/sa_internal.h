@@ -59,8 +59,8 @@ struct sa_ctx {
     int num_sms = 0;
     size_t smem_optin = 0;
     int max_grid = 0;        // cap on the fused kernel's grid (0: all SMs); set by the server
-    int fused_wide = 1;      // n in (4096, 8192] int16: 1024 threads x 8 columns (1) or 512 x 16 (0);
-                             // SA_FUSED_WIDE=0 in the environment selects the narrow form
+    int fused_nt = 512;      // threads per block of the fused kernel when 512 < chunks <= 1024
+                             // (256 or 512; SA_FUSED_NT in the environment overrides)
     sa::Workspace ws;        // scratch for sweeps, prune, certify
     sa::Workspace input;     // device copy of host inputs (sa_assign_host)
     sa::PinnedBuf pinned;    // staging for small device->host results

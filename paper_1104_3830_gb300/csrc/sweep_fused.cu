@@ -3,25 +3,29 @@
 // Sec. 4.2 stopping rule) and reads A once per sweep.
 //
 // Work split.  Block b owns the row stripe [b*n/G, (b+1)*n/G).  Within a block every
-// thread owns a fixed set of 16-byte column chunks, so the column partial sums of the
-// stripe live in registers for the whole sweep.  Rows stream through a shared-memory
-// ring filled by the bulk-copy engine (cp.async.bulk + mbarrier), RING rows ahead.
+// compute thread owns a fixed set of 16-byte column chunks, so the column partial sums of
+// the stripe live in registers for the whole sweep.  One extra producer warp streams the
+// rows through a shared-memory ring with the bulk-copy engine (cp.async.bulk + mbarrier):
+// a slot is refilled as soon as every compute warp has released it (empty mbarrier), so
+// copy issue and copy latency stay off the compute warps' path.
 //
 // One sweep, in log2 units (U = u/ln2, V = v/ln2, L = log2 w):
-//   row i   t_ij = 2^(p (L_ij - Lr_i) - Vh_j) * c_j          (FP32, SFU ex2/lg2)
+//   row i   t_ij = 2^(p log2(w_ij a_i) - Vh_j) * c_j          (FP32, SFU ex2/lg2)
 //           s_i  = sum_j t_ij                                   (block reduction)
 //           S_j += t_ij / s_i        (column sums of the row-stochastic iterate)
-//           U_i  = p Lr_i + log2 s_i                           (row update, dad2)
+//           U_i  = -p log2 a_i + log2 s_i                       (row update, dad2)
 //   grid barrier; block b finalises a slice of columns:
 //           S_j  = sum_b S_j^(b)     (FP64, fixed order: deterministic)
 //           V_j += log2 S_j          (column update, dad3, FP64)
 //           residual = max_j |S_j - 1|  (eps-bistochastic measure, Sec. 4.2, FP64)
 //   grid barrier; every block reads the residual and takes the same decision.
-// Lr_i = float(U_i / p) is a per-row FP32 reference frozen during a p step: the row
-// normalisation cancels it exactly, and it keeps the FP32 exponent small (L - Lr is exact
-// when L and Lr are within a factor of two).  V_j is exact in FP64; the kernel applies it
-// as an FP32 head Vh_j = float(V_j) (frozen per step) times c_j = 2^(Vh_j - V_j), so
-// column updates smaller than an FP32 ulp of V are not lost.
+// a_i = float(2^(-U_i/p)) is a per-row FP32 scale frozen during a p step: the row
+// normalisation cancels it exactly, and it keeps log2(w a) small for the entries that
+// matter, so the SFU logarithm's absolute error stays small.  w a is formed exactly up to
+// one rounding (int16: the integer is decoded by a byte permute into a float with a
+// 2^23 bias and one FMA removes the bias and applies a).  V_j is exact in FP64; the kernel
+// applies it as an FP32 head Vh_j = float(V_j) (frozen per step) times c_j = 2^(Vh_j - V_j),
+// so column updates smaller than an FP32 ulp of V are not lost.
 //
 // Rows whose sum leaves [2^-64, 2^64] (a stale shift, e.g. the first sweep at a large
 // p) are recomputed with the exact max shift of the paper and re-anchor Lr_i.
@@ -72,24 +76,25 @@ struct Vec;
 template <>
 struct Vec<int16_t> {
     static constexpr int N = 8;
-    // decode 8 weights and return log2 of each
-    __device__ static __forceinline__ void log2w(const uint4& q, float* L) {
+    // log2(w * a) of 8 weights: the byte permute places w in the mantissa of 2^23, and one
+    // FMA forms (2^23 + w) a - 2^23 a = w a exactly rounded (ca = -2^23 a is exact)
+    __device__ static __forceinline__ void log2w(const uint4& q, float a, float ca, float* L) {
         const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            L[2 * k] = lg2_approx(lo16_to_float(wd[k]));
-            L[2 * k + 1] = lg2_approx(hi16_to_float(wd[k]));
+            L[2 * k] = lg2_approx(fmaf(__uint_as_float(__byte_perm(wd[k], 0x4B00u, 0x5410u)), a, ca));
+            L[2 * k + 1] = lg2_approx(fmaf(__uint_as_float(__byte_perm(wd[k], 0x4B00u, 0x5432u)), a, ca));
         }
     }
 };
 template <>
 struct Vec<int32_t> {
     static constexpr int N = 4;
-    __device__ static __forceinline__ void log2w(const uint4& q, float* L) {
-        L[0] = lg2_approx((float)(int)q.x);
-        L[1] = lg2_approx((float)(int)q.y);
-        L[2] = lg2_approx((float)(int)q.z);
-        L[3] = lg2_approx((float)(int)q.w);
+    __device__ static __forceinline__ void log2w(const uint4& q, float a, float, float* L) {
+        L[0] = lg2_approx((float)(int)q.x * a);
+        L[1] = lg2_approx((float)(int)q.y * a);
+        L[2] = lg2_approx((float)(int)q.z * a);
+        L[3] = lg2_approx((float)(int)q.w * a);
     }
 };
 
@@ -140,8 +145,14 @@ __device__ __forceinline__ bool grid_sync(unsigned* ctr, unsigned target, int* e
     return *s_ok != 0;
 }
 
+// Named barrier over the NT compute threads (the producer warp does not take part).
+__device__ __forceinline__ void compute_sync(int nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Block = NT compute threads + one producer warp that streams the rows into the ring.
 template <typename WT, int NT, int CH, int RING, int R>
-__global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
+__global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
     constexpr int VEC = Vec<WT>::N;
     constexpr int NW = NT / 32;
     constexpr int M = CH * VEC;   // columns owned per thread
@@ -151,14 +162,15 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
     static_assert(M % 4 == 0 && NT % 64 == 0, "layout");
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* ring = smem;
-    uint64_t* mbar = (uint64_t*)(smem + (size_t)RING * A.row_bytes);   // [RING] bulk-copy arrivals
-    uint64_t* mrow = mbar + RING;                                      // [NRED] row-sum publication
-    float4* tbuf = (float4*)(mrow + NRED + ((RING + NRED) & 1));       // [2][M4][NT]
-    float* red = (float*)(tbuf + (size_t)2 * M4 * NT);                 // [NRED][NW]
-    float* red2 = red + NRED * NW;                                     // [NW] slow path
+    uint64_t* mbar = (uint64_t*)(smem + (size_t)RING * A.row_bytes);   // [RING] bulk-copy arrivals (full)
+    uint64_t* mempty = mbar + RING;                                    // [RING] slot read by every warp (empty)
+    uint64_t* mrow = mempty + RING;                                    // [NRED] row-sum publication
+    float4* tbuf = (float4*)(mrow + NRED + ((2 * RING + NRED) & 1));   // [4][M4][NT]
+    float* red = (float*)(tbuf + (size_t)4 * M4 * NT);                 // [NRED][2][NW]
+    float* red2 = red + NRED * 2 * NW;                                 // [NW] slow path
     float* Lr = red2 + NW;                                             // [max_rows]
     float* srow = Lr + A.max_rows;                                     // [max_rows]
-    double* redp = (double*)(srow + A.max_rows);   // [FG][64] (offset 4*(5 NW + 2 max_rows): 8-aligned)
+    double* redp = (double*)(srow + A.max_rows);   // [FG][64] (offset 4*(9 NW + 2 max_rows): 8-aligned)
     __shared__ int s_flag, s_ok;
     __shared__ float s_res;
 
@@ -166,6 +178,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
     const int G = gridDim.x;
     const int b = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const bool producer = wid == NW;   // the extra warp: bulk copies only
     const int r0 = (int)((int64_t)b * n / G);
     const int r1 = (int)((int64_t)(b + 1) * n / G);
     const int nrows = r1 - r0;
@@ -176,6 +189,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
 
     if (tid == 0) {
         for (int s = 0; s < RING; ++s) mbar_init(&mbar[s], 1);
+        for (int s = 0; s < RING; ++s) mbar_init(&mempty[s], NW);
         for (int s = 0; s < NRED; ++s) mbar_init(&mrow[s], NW);
         mbar_fence_init();
         s_flag = 0;
@@ -183,16 +197,31 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
     __syncthreads();
 
     uint32_t iss = 0, it = 0;   // rows issued / consumed by this block, over all sweeps
+    uint32_t gbase = 0;         // row stages completed by this block, over all sweeps
     unsigned nbar = 0;          // grid barriers passed
     int rphase = 0;             // sweeps of earlier steps (selects the residual word)
-    auto issue_row = [&](int q) {   // thread 0 only
+    auto issue_row = [&](int q) {   // producer lane 0 only
         const uint32_t slot = iss % RING;
         mbar_arrive_expect_tx(&mbar[slot], A.row_bytes);
         bulk_g2s(ring + (size_t)slot * A.row_bytes, wbase + (size_t)(r0 + q) * pitch, A.row_bytes, &mbar[slot]);
         ++iss;
     };
+    // The producer issues consumption indices in order (index u holds local row u % nrows),
+    // each into the slot freed by the index RING earlier once every compute warp has read it.
+    auto produce_rows = [&](uint32_t upto) {   // producer lane 0 only
+        while (iss < upto) {
+            if (iss >= (uint32_t)RING) {
+                const uint32_t prev = iss - RING;
+                if (!mbar_wait(&mempty[prev % RING], (prev / RING) & 1u, A.err, kWaitTimeoutNs)) {
+                    s_flag = 1;
+                    return;
+                }
+            }
+            issue_row((int)(iss % (uint32_t)nrows));
+        }
+    };
     auto drain = [&]() {
-        if (tid == 0) {
+        if (producer && lane == 0) {
             for (uint32_t q = it; q < iss; ++q)
                 if (!mbar_wait(&mbar[q % RING], (q / RING) & 1u, A.err, kWaitTimeoutNs)) break;
         }
@@ -208,7 +237,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
         cidx[k] = tid + k * NT;
-        nval[k] = cidx[k] < NC ? min(VEC, n - cidx[k] * VEC) : 0;
+        nval[k] = (!producer && cidx[k] < NC) ? min(VEC, n - cidx[k] * VEC) : 0;
     }
 
     float S[M], vh[M], vc[M];
@@ -224,27 +253,29 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
             }
     };
 
-    // Terms t_ij = 2^(p (L_ij - Lr) - Vh_j) of this thread's columns into tbuf[slot];
-    // returns the partial row sum of t_ij c_j (c_j is applied to the column sums later).
-    auto row_terms = [&](const unsigned char* rowp, float lr, float pf, int slot) -> float {
+    // Terms t_ij = 2^(p log2(w_ij a_i) - Vh_j) of this thread's columns into tbuf[slot];
+    // a_i = 2^-Lr_i is the row's scale (log2(w a) is small for the entries that matter).
+    // Returns the partial row sum of t_ij c_j (c_j is applied to the column sums later).
+    auto row_terms = [&](const unsigned char* rowp, float a, float pf, int slot) -> float {
+        const float ca = -8388608.0f * a;
         float sp0 = 0.0f, sp1 = 0.0f;
 #pragma unroll
         for (int kk = 0; kk < CH; ++kk) {
             float t[VEC];
             if (nval[kk] == VEC) {
                 float L[VEC];
-                Vec<WT>::log2w(*(const uint4*)(rowp + (size_t)cidx[kk] * 16), L);
+                Vec<WT>::log2w(*(const uint4*)(rowp + (size_t)cidx[kk] * 16), a, ca, L);
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) t[e] = ex2_approx(fmaf(pf, L[e] - lr, -vh[kk * VEC + e]));
+                for (int e = 0; e < VEC; ++e) t[e] = ex2_approx(fmaf(pf, L[e], -vh[kk * VEC + e]));
             } else {
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) t[e] = 0.0f;
                 if (nval[kk] > 0) {
                     float L[VEC];
-                    Vec<WT>::log2w(*(const uint4*)(rowp + (size_t)cidx[kk] * 16), L);
+                    Vec<WT>::log2w(*(const uint4*)(rowp + (size_t)cidx[kk] * 16), a, ca, L);
 #pragma unroll
                     for (int e = 0; e < VEC; ++e)
-                        if (e < nval[kk]) t[e] = ex2_approx(fmaf(pf, L[e] - lr, -vh[kk * VEC + e]));
+                        if (e < nval[kk]) t[e] = ex2_approx(fmaf(pf, L[e], -vh[kk * VEC + e]));
                 }
             }
 #pragma unroll
@@ -260,39 +291,60 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
         return sp0 + sp1;
     };
 
-    // Row u (consumption index) of local row q: wait for its bytes, form its terms, and
-    // publish the warp's partial row sum.
-    auto produce = [&](int q, uint32_t u, float pf) {
-        if (!mbar_wait(&mbar[u % RING], (u / RING) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
-        const float sp = row_terms(ring + (size_t)(u % RING) * A.row_bytes, Lr[q], pf, q & 1);
-        const float w = warp_sum(sp);
+    // Stage g = local rows 2g and 2g+1: wait for their bytes, form their terms (tbuf slots
+    // 2(g&1) and 2(g&1)+1), and publish the warp's two partial row sums on mrow[g % NRED].
+    // Two rows per stage halve the reductions, waits and copy issues per row, and give each
+    // warp two independent rows of work to interleave.
+    auto produce = [&](int g, float pf) {
+        const int q0 = 2 * g;
+        const bool two = q0 + 1 < nrows;
+        const uint32_t u0 = it + q0;
+        bool ok = mbar_wait(&mbar[u0 % RING], (u0 / RING) & 1u, A.err, kWaitTimeoutNs);
+        if (two) ok = mbar_wait(&mbar[(u0 + 1) % RING], ((u0 + 1) / RING) & 1u, A.err, kWaitTimeoutNs) && ok;
+        if (!ok) s_flag = 1;
+        const int ts = (g & 1) * 2;
+        const float sp0 = row_terms(ring + (size_t)(u0 % RING) * A.row_bytes, Lr[q0], pf, ts);
+        const float sp1 = two ? row_terms(ring + (size_t)((u0 + 1) % RING) * A.row_bytes, Lr[q0 + 1], pf, ts + 1) : 0.0f;
+        // this warp is done with the rows' slots (an exact-max redo reads the row from
+        // global memory): hand them back to the producer
+        __syncwarp();
         if (lane == 0) {
-            red[(u % NRED) * NW + wid] = w;
-            mbar_arrive(&mrow[u % NRED]);
+            mbar_arrive(&mempty[u0 % RING]);
+            if (two) mbar_arrive(&mempty[(u0 + 1) % RING]);
+        }
+
+        const float w0 = warp_sum(sp0);
+        const float w1 = warp_sum(sp1);
+        if (lane == 0) {
+            const uint32_t gs = gbase + g;   // stage count over all sweeps: mbarrier phase
+            red[((gs % NRED) * 2) * NW + wid] = w0;
+            red[((gs % NRED) * 2 + 1) * NW + wid] = w1;
+            mbar_arrive(&mrow[gs % NRED]);
         }
     };
 
     // exact max shift for row q (the paper's form), block-wide; terms into tbuf[q & 1]
-    auto row_exact = [&](const unsigned char* rowp, float lr, float pf, int slot, float* gm_out) -> float {
+    auto row_exact = [&](const unsigned char* rowp, float a, float pf, int slot, float* gm_out) -> float {
         float e_loc[M];
         float mx = -INFINITY;
+        const float ca = -8388608.0f * a;
 #pragma unroll
         for (int kk = 0; kk < CH; ++kk) {
             float L[VEC];
-            if (nval[kk] > 0) Vec<WT>::log2w(*(const uint4*)(rowp + (size_t)cidx[kk] * 16), L);
+            if (nval[kk] > 0) Vec<WT>::log2w(*(const uint4*)(rowp + (size_t)cidx[kk] * 16), a, ca, L);
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
                 const int m = kk * VEC + e;
                 float ev = -INFINITY;
-                if (e < nval[kk] && vc[m] > 0.0f) ev = fmaf(pf, L[e] - lr, -vh[m]) + log2f(vc[m]);
+                if (e < nval[kk] && vc[m] > 0.0f) ev = fmaf(pf, L[e], -vh[m]) + log2f(vc[m]);
                 e_loc[m] = ev;
                 mx = fmaxf(mx, ev);
             }
         }
         mx = warp_max(mx);
-        __syncthreads();
+        compute_sync(NT);
         if (lane == 0) red2[wid] = mx;
-        __syncthreads();
+        compute_sync(NT);
         float gm = -INFINITY;
         for (int x = 0; x < NW; ++x) gm = fmaxf(gm, red2[x]);
         float s2 = 0.0f;
@@ -308,26 +360,26 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
             tbuf[((size_t)slot * M4 + m4) * NT + tid] =
                 make_float4(e_loc[4 * m4], e_loc[4 * m4 + 1], e_loc[4 * m4 + 2], e_loc[4 * m4 + 3]);
         s2 = warp_sum(s2);
-        __syncthreads();
+        compute_sync(NT);
         if (lane == 0) red2[wid] = s2;
-        __syncthreads();
+        compute_sync(NT);
         float ss = 0.0f;
         for (int x = 0; x < NW; ++x) ss += red2[x];
         *gm_out = gm;
         return ss;
     };
 
-    if (tid == 0)
-        for (int q = 0; q < min(RING, nrows); ++q) issue_row(q);
-
     for (int k = A.k0; k < A.n_p; ++k) {
         const double p = A.P[k];
         const float pf = (float)p;
         // per-step row references: U holds the row potentials reached at p[k-1]
         // (zero on a fresh start), so U/p[k-1] is the per-row level of log2 w
+        // (Lr holds the row scale a_i = 2^-(U_i/p[k-1]) as an FP32 number; the row's
+        //  potential is recovered exactly as U_i = -p log2(a_i) + log2(s_i) in FP64)
         {
             const double pprev = (k > 0) ? A.P[k - 1] : p;
-            for (int q = tid; q < nrows; q += NT) Lr[q] = (float)(A.U[r0 + q] / pprev);
+            if (!producer)
+                for (int q = tid; q < nrows; q += NT) Lr[q] = (float)exp2(-fmin(fmax(A.U[r0 + q] / pprev, -120.0), 120.0));
         }
         __syncthreads();
         load_cols();
@@ -344,62 +396,81 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
             // q and accumulates row q's normalised terms into its column sums.  NRED = 4
             // buffers: a warp can publish row q+3 only after all warps published q+1, i.e.
             // after they read the sums of row q-1, the last reader of that buffer.
-            if (nrows > 0) produce(0, it, pf);
-            for (int q = 0; q < nrows; ++q) {
-                const uint32_t u = it + q;
-                if (q + 1 < nrows) produce(q + 1, u + 1, pf);
-                if (!mbar_wait(&mrow[u % NRED], (u / NRED) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
+            const int nst = producer ? 0 : (nrows + 1) / 2;
+            if (producer && lane == 0) produce_rows(it + (uint32_t)nrows + (uint32_t)min(RING, nrows));
+            if (nst > 0) produce(0, pf);
+            for (int g = 0; g < nst; ++g) {
+                const int q0 = 2 * g;
+                const int nr = min(2, nrows - q0);
+                if (g + 1 < nst) produce(g + 1, pf);
+                const uint32_t gs = gbase + g;
+                if (!mbar_wait(&mrow[gs % NRED], (gs / NRED) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
                 if (s_flag) break;
-                // lane x holds warp x's partial: one load and a warp reduction
-                float s = warp_sum(lane < NW ? red[(u % NRED) * NW + lane] : 0.0f);
-                if (!(s >= 0x1p-64f && s <= 0x1p64f)) {
+                float srs[2];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float4* rv = (const float4*)(red + ((gs % NRED) * 2 + r) * NW);
+                    float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+                    for (int x = 0; x < NW / 4; ++x) {
+                        const float4 q4 = rv[x];
+                        a0 += q4.x + q4.y;
+                        a1 += q4.z + q4.w;
+                    }
+                    srs[r] = a0 + a1;
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    if (r >= nr || (srs[r] >= 0x1p-64f && srs[r] <= 0x1p64f)) continue;
                     // the stale shift left the range (uniform decision): exact max shift
-                    const float lr = Lr[q];
+                    const int q = q0 + r;
+                    const float ar = Lr[q];
                     float gm;
-                    float ss = row_exact(ring + (size_t)(u % RING) * A.row_bytes, lr, pf, q & 1, &gm);
+                    float ss = row_exact(wbase + (size_t)(r0 + q) * pitch, ar, pf, (g & 1) * 2 + r, &gm);
                     if (!(gm > -INFINITY) || !(ss > 0.0f)) {
                         if (tid == 0) atomicCAS(A.err, 0, kErrNonfinite);
                         ss = 1.0f;
                         gm = 0.0f;
                     }
-                    s = ss;
+                    srs[r] = -ss;   // marks a re-anchored row (negative: srow already set)
                     if (tid == 0) {
-                        // re-anchor the row reference at the exact row potential
-                        const double un = p * (double)lr + (double)gm + log2((double)ss);
-                        const float lrn = (float)(un / p);
-                        Lr[q] = lrn;
-                        srow[q] = (float)exp2(un - p * (double)lrn);
+                        // re-anchor the row scale at the exact row potential
+                        const double un = -p * log2((double)ar) + (double)gm + log2((double)ss);
+                        const float an = (float)exp2(-un / p);
+                        Lr[q] = an;
+                        srow[q] = (float)exp2(un + p * log2((double)an));
                         atomicAdd(A.fallback, 1);
                     }
-                    __syncthreads();
-                } else if (tid == 0) {
-                    srow[q] = s;
+                    compute_sync(NT);
                 }
-                if (tid == 0 && q + RING < nrows) {
-                    // every warp has published row q, so all have read its slot
-                    fence_proxy_async_smem();
-                    issue_row(q + RING);
+                if (tid == 0) {
+                    for (int r = 0; r < nr; ++r)
+                        if (srs[r] > 0.0f) srow[q0 + r] = srs[r];
                 }
-                const float inv = 1.0f / s;
 #pragma unroll
-                for (int m4 = 0; m4 < M4; ++m4) {
-                    const float4 t4 = tbuf[((size_t)(q & 1) * M4 + m4) * NT + tid];
-                    S[4 * m4] = fmaf(t4.x, inv, S[4 * m4]);
-                    S[4 * m4 + 1] = fmaf(t4.y, inv, S[4 * m4 + 1]);
-                    S[4 * m4 + 2] = fmaf(t4.z, inv, S[4 * m4 + 2]);
-                    S[4 * m4 + 3] = fmaf(t4.w, inv, S[4 * m4 + 3]);
+                for (int r = 0; r < 2; ++r) {
+                    if (r >= nr) break;
+                    const float inv = rcp_approx(fabsf(srs[r]));
+                    const float4* tb = tbuf + (size_t)((g & 1) * 2 + r) * M4 * NT + tid;
+#pragma unroll
+                    for (int m4 = 0; m4 < M4; ++m4) {
+                        const float4 t4 = tb[(size_t)m4 * NT];
+                        S[4 * m4] = fmaf(t4.x, inv, S[4 * m4]);
+                        S[4 * m4 + 1] = fmaf(t4.y, inv, S[4 * m4 + 1]);
+                        S[4 * m4 + 2] = fmaf(t4.z, inv, S[4 * m4 + 2]);
+                        S[4 * m4 + 3] = fmaf(t4.w, inv, S[4 * m4 + 3]);
+                    }
                 }
             }
             __syncthreads();
             if (s_flag) { drain(); return; }
             it += nrows;
+            gbase += (nrows + 1) / 2;
             SA_STAMP(1);
-            if (tid == 0)
-                for (int q = 0; q < min(RING, nrows); ++q) issue_row(q);   // next sweep reads the same rows
             float* pb = A.part + (size_t)b * A.npad;
 #pragma unroll
             for (int kk = 0; kk < CH; ++kk) {
-                if (cidx[kk] < NC) {
+                if (nval[kk] > 0) {   // the producer warp owns no columns
 #pragma unroll
                     for (int e = 0; e < VEC; e += 4)
                         *(float4*)(pb + (size_t)cidx[kk] * VEC + e) =
@@ -418,7 +489,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
                 const int j = cb + (tid & 63);
                 const int grp = tid >> 6;
                 KahanF acc;
-                if (j < c1) {
+                if (!producer && j < c1) {
                     const float* pj = A.part + j;
                     for (int g0 = grp; g0 < G; g0 += FG * 20) {
                         float a[20];
@@ -431,7 +502,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
                         for (int x = 0; x < 20; ++x) acc.add(a[x]);
                     }
                 }
-                redp[grp * 64 + (tid & 63)] = (double)acc.s - (double)acc.c;
+                if (!producer) redp[grp * 64 + (tid & 63)] = (double)acc.s - (double)acc.c;
                 __syncthreads();
                 if (tid < 64 && j < c1) {
                     double Sj = 0.0;
@@ -474,8 +545,8 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
             SA_STAMP(4);
         }
         rphase += sweeps;
-        for (int q = tid; q < nrows; q += NT) {
-            double uu = p * (double)Lr[q] + log2((double)srow[q]);
+        for (int q = tid; q < nrows && !producer; q += NT) {
+            double uu = -p * log2((double)Lr[q]) + log2((double)srow[q]);
             if (A.f32_potentials) uu = (double)(float)uu;
             A.U[r0 + q] = uu;
         }
@@ -486,7 +557,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
         if (k + 1 < A.n_p) {
             // warm start of the next step: (U, V) *= p_{k+1}/p_k unless v is kept
             const double f = A.keep_v ? 1.0 : A.P[k + 1] / p;
-            for (int j = c0 + tid; j < c1; j += NT) {
+            for (int j = c0 + tid; j < c1 && !producer; j += NT) {
                 double v = A.V[j] * f;
                 A.V[j] = v;
                 float h = (float)v;
@@ -504,7 +575,7 @@ sa_status launch_fused(sa_ctx* ctx, const FusedArgs& args, size_t smem, int* gri
     auto kern = fused_kernel<WT, NT, CH, RING, R>;
     SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+    SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT + 32, smem));
     if (per_sm < 1) {
         set_error("fused sweep: kernel does not fit on an SM (smem %zu)", smem);
         return SA_E_UNSUPPORTED;
@@ -521,7 +592,7 @@ sa_status launch_fused(sa_ctx* ctx, const FusedArgs& args, size_t smem, int* gri
     *grid_out = G;
     FusedArgs a = args;
     void* params[] = {&a};
-    SA_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(NT), params, smem, ctx->stream));
+    SA_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(NT + 32), params, smem, ctx->stream));
     count_launch();
     return SA_OK;
 }
@@ -538,23 +609,27 @@ constexpr int kRowsPerSync = SA_ROWS_PER_SYNC;
 size_t fused_smem_bytes(const FusedCfg& c, unsigned row_bytes, int vec, int max_rows) {
     const int nw = c.nt / 32;
     const int m4 = c.ch * vec / 4;
-    const size_t head = (size_t)c.ring * row_bytes + 8 * (size_t)(c.ring + 4 + ((c.ring + 4) & 1));
+    const size_t head = (size_t)c.ring * row_bytes + 8 * (size_t)(2 * c.ring + 4 + ((2 * c.ring + 4) & 1));
     const size_t fg = c.nt / 64;
-    return head + 16 * (size_t)2 * m4 * c.nt + 4 * (size_t)(4 * nw + nw + 2 * max_rows) + 8 + 8 * fg * 64 + 128;
+    // + 1 KiB for the kernel's static shared variables and alignment
+    return head + 16 * (size_t)4 * m4 * c.nt + 4 * (size_t)(8 * nw + nw + 2 * max_rows) + 8 + 8 * fg * 64 + 1024;
 }
 
-FusedCfg pick_cfg(const sa_matrix* a, size_t smem_optin, int max_rows, int wide = 1) {
+// nt_pref: compute threads per block for 512 < chunks <= 1024 (256 x 4 or 512 x 2 chunks;
+// 1024 compute threads plus the producer warp exceed the block size limit)
+FusedCfg pick_cfg(const sa_matrix* a, size_t smem_optin, int max_rows, int nt_pref = 512) {
     const int vec = 16 / wbytes(a->wtype);
     const int nc = (a->n + vec - 1) / vec;
     FusedCfg c{0, 0, 0, kRowsPerSync};
     if (nc <= 128) c = {128, 1, 0, kRowsPerSync};
     else if (nc <= 256) c = {256, 1, 0, kRowsPerSync};
     else if (nc <= 512) c = {512, 1, 0, kRowsPerSync};
-    else if (nc <= 1024) c = wide ? FusedCfg{1024, 1, 0, kRowsPerSync} : FusedCfg{512, 2, 0, kRowsPerSync};
-    else if (nc <= 1536) c = {512, 3, 0, kRowsPerSync};
-    else return c;
+    else if (nc <= 1024) {
+        if (nt_pref == 256) c = {256, 4, 0, kRowsPerSync};
+        else c = {512, 2, 0, kRowsPerSync};
+    } else return c;
     const unsigned row_bytes = (unsigned)align_up((size_t)a->n * wbytes(a->wtype), 16);
-    for (int ring : {6, 4, 2}) {
+    for (int ring : {6, 5, 4}) {
         c.ring = ring;
         if (fused_smem_bytes(c, row_bytes, vec, max_rows) <= smem_optin) return c;
     }
@@ -583,7 +658,7 @@ sa_status scale_fused(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, d
                       double* V, sa_scale_info* info) {
     const int n = a->n;
     const int max_rows = fused_max_rows(ctx, n);
-    FusedCfg cfg = pick_cfg(a, ctx->smem_optin, max_rows, ctx->fused_wide);
+    FusedCfg cfg = pick_cfg(a, ctx->smem_optin, max_rows, ctx->fused_nt);
     if (cfg.nt == 0) {
         set_error("fused sweep: n=%d not supported by the fused kernel", n);
         return SA_E_UNSUPPORTED;
@@ -660,17 +735,16 @@ sa_status scale_fused(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, d
              : launch_fused<int32_t, NT_, CH_, RING_, kRowsPerSync>(ctx, args, smem, &G)
     if (cfg.ring == 6) {
         if (cfg.nt == 128) SA_LAUNCH(128, 1, 6);
-        else if (cfg.nt == 256) SA_LAUNCH(256, 1, 6);
-        else if (cfg.nt == 1024) SA_LAUNCH(1024, 1, 6);
+        else if (cfg.nt == 256 && cfg.ch == 1) SA_LAUNCH(256, 1, 6);
+        else if (cfg.nt == 256) SA_LAUNCH(256, 4, 6);
         else if (cfg.ch == 1) SA_LAUNCH(512, 1, 6);
-        else if (cfg.ch == 2) SA_LAUNCH(512, 2, 6);
-        else SA_LAUNCH(512, 3, 6);
-    } else if (cfg.ring == 4) {
-        if (cfg.nt == 1024) SA_LAUNCH(1024, 1, 4);
-        else if (cfg.ch == 2) SA_LAUNCH(512, 2, 4);
-        else SA_LAUNCH(512, 3, 4);
+        else SA_LAUNCH(512, 2, 6);
+    } else if (cfg.ring == 5) {
+        if (cfg.nt == 256) SA_LAUNCH(256, 4, 5);
+        else SA_LAUNCH(512, 2, 5);
     } else {
-        SA_LAUNCH(512, 3, 2);
+        if (cfg.nt == 256) SA_LAUNCH(256, 4, 4);
+        else SA_LAUNCH(512, 2, 4);
     }
 #undef SA_LAUNCH
     if (rc) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); return rc; }
@@ -833,7 +907,7 @@ extern "C" sa_status sa_scale_noalloc(const sa_matrix* a, const sa_scale_opts* o
         return SA_E_UNSUPPORTED;
     }
     const int max_rows = fused_max_rows(&ctx, n);
-    FusedCfg cfg = pick_cfg(a, ctx.smem_optin, max_rows, 0);
+    FusedCfg cfg = pick_cfg(a, ctx.smem_optin, max_rows, 512);
     cudaStream_t st = ctx.stream;
     const int npad = (int)align_up((size_t)n, 32);
     // carve the static array
@@ -893,15 +967,19 @@ extern "C" sa_status sa_scale_noalloc(const sa_matrix* a, const sa_scale_opts* o
     int G = kNoAllocMaxGrid;
     const bool i16 = a->wtype == SA_I16;
     sa_status rc;
-    // n <= 4096: at most 512 chunks, one per thread
+    // n <= 4096: int16 has at most 512 chunks (one per thread), int32 up to 1024 (512 x 2)
     if (cfg.nt == 128) rc = i16 ? launch_fused<int16_t, 128, 1, 6, kRowsPerSync>(&ctx, args, smem, &G)
                                 : launch_fused<int32_t, 128, 1, 6, kRowsPerSync>(&ctx, args, smem, &G);
     else if (cfg.nt == 256) rc = i16 ? launch_fused<int16_t, 256, 1, 6, kRowsPerSync>(&ctx, args, smem, &G)
                                      : launch_fused<int32_t, 256, 1, 6, kRowsPerSync>(&ctx, args, smem, &G);
     else if (cfg.ch == 1) rc = i16 ? launch_fused<int16_t, 512, 1, 6, kRowsPerSync>(&ctx, args, smem, &G)
                                    : launch_fused<int32_t, 512, 1, 6, kRowsPerSync>(&ctx, args, smem, &G);
-    else rc = i16 ? launch_fused<int16_t, 512, 2, 6, kRowsPerSync>(&ctx, args, smem, &G)
-                  : launch_fused<int32_t, 512, 2, 6, kRowsPerSync>(&ctx, args, smem, &G);
+    else if (cfg.ring == 6) rc = i16 ? launch_fused<int16_t, 512, 2, 6, kRowsPerSync>(&ctx, args, smem, &G)
+                                     : launch_fused<int32_t, 512, 2, 6, kRowsPerSync>(&ctx, args, smem, &G);
+    else if (cfg.ring == 5) rc = i16 ? launch_fused<int16_t, 512, 2, 5, kRowsPerSync>(&ctx, args, smem, &G)
+                                     : launch_fused<int32_t, 512, 2, 5, kRowsPerSync>(&ctx, args, smem, &G);
+    else rc = i16 ? launch_fused<int16_t, 512, 2, 4, kRowsPerSync>(&ctx, args, smem, &G)
+                  : launch_fused<int32_t, 512, 2, 4, kRowsPerSync>(&ctx, args, smem, &G);
     if (rc) return rc;
     // results through pageable host memory (no pinned allocation)
     int h_words[4] = {0, 0, 0, 0};
