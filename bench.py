@@ -45,6 +45,26 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+# DRAM bytes per sweep of the fused kernel (dram__bytes.sum from one ncu capture of the
+# p = 1, 2 case of the planted n=8192 int16 instance, per sweep), valid only for the kernel
+# source it was taken on: any change to the kernel makes the figure unknown (null).
+TRAFFIC_SOURCE = "ncu capture, planted n=8192 int16, p=1,2 (6 sweeps), scaled per sweep"
+_TRAFFIC = {(8192, 2): 146.6e6}
+_TRAFFIC_SRC_SHA256 = {
+    "paper_1104_3830_gb300/csrc/sweep_fused.cu": "d1dcdbec1f63cfa05cc957fb78fc37e575de7385961ea5596cdca59bd7eef491",
+    "paper_1104_3830_gb300/csrc/common.cuh": "e16bf96e14128dd20b644d1aca4ec0085d06a37a1d9f040b585c32c72d919518",
+}
+
+
+def fused_traffic_per_sweep(n, wbytes):
+    import hashlib
+    for rel, want in _TRAFFIC_SRC_SHA256.items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != want:
+                return None
+    return _TRAFFIC.get((n, wbytes))
+
+
 def workload(name):
     from paper_1104_3830_gb300 import workloads as W
     if name == "planted8192":
@@ -429,8 +449,13 @@ def main():
     kernel_ms = statistics.mean(kms)
     alg_bytes = sweeps_per_step * n * n * w.dtype.itemsize
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    traffic = fused_traffic_per_sweep(n, w.dtype.itemsize)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "fused_kernel (persistent Sinkhorn sweep)",
+                "traffic": traffic * sweeps_per_step if traffic else None,
+                "traffic_per_sweep": traffic, "traffic_source": TRAFFIC_SOURCE if traffic else
+                "none for this kernel source or size",
+                "kernel": ("fused_kernel (persistent Sinkhorn sweep)" if res["scale"].get("kernel_used") == 1
+                           else "row_lse_kernel + col_partial_kernel (plain sweep)"),
                 "peak_source": f"{peak_kind} hbm_gbs", "sweep_us": kernel_ms * 1e3 / max(sweeps_per_step, 1)}
 
     # end to end through the C ABI with the matrix in pinned host memory
@@ -457,7 +482,9 @@ def main():
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 (exp/sum), f64 potentials", "data": "synthetic",
                 "config": dict(cfg, n=n, sweeps_per_step=sweeps_per_step, parallelism=f"replicas x{world}",
-                               l2="flushed between steps (256 MiB write)", impl="fused persistent kernel",
+                               l2="flushed between steps (256 MiB write)",
+                               impl=("fused persistent kernel" if res["scale"].get("kernel_used") == 1
+                                     else "plain row/column kernels"),
                                nnz_first=res["nnz_first"], gamma=res["gamma"], repairs=res["repairs"],
                                ms_scale=res["ms_scale"], ms_prune=res["ms_prune"], ms_solve=res["ms_solve"],
                                ms_certify=res["ms_certify"], converged=res["scale"]["converged"]),
