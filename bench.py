@@ -56,6 +56,11 @@ _TRAFFIC_SRC_SHA256 = {
 }
 
 
+KERNEL_NAMES = {1: "fused_kernel (single-read persistent sweep, SFU exp2/log2 per element)",
+                2: "row_lse_kernel + col_partial_kernel (plain sweep, host loop)",
+                3: "step_kernel (persistent sweep over the per-step FP32 matrix)"}
+
+
 def fused_traffic_per_sweep(n, wbytes):
     import hashlib
     for rel, want in _TRAFFIC_SRC_SHA256.items():
@@ -371,6 +376,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="planted8192")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "step", "fused", "plain"],
+                    help="sweep implementation of sa_scale (auto: the library's choice)")
     ap.add_argument("--max-sweeps", type=int, default=20000)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--plain-sample", type=int, default=128)
@@ -414,7 +421,7 @@ def main():
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        api.sa_assign(ctx, d, ps, 1e-6, args.max_sweeps)
+        api.sa_assign(ctx, d, ps, 1e-6, args.max_sweeps, kernel=args.kernel)
     barrier()
     times, sweeps, kms, res = [], 0, [], None
     launches0 = _lib.lib().sa_kernel_launches()
@@ -424,7 +431,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            res = api.sa_assign(ctx, d, ps, 1e-6, args.max_sweeps)
+            res = api.sa_assign(ctx, d, ps, 1e-6, args.max_sweeps, kernel=args.kernel)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -443,32 +450,38 @@ def main():
         all_sweeps = float(sweeps)
     value = all_sweeps / (total_ms / 1e3)
 
-    # roofline of the dominant kernel: the fused sweep, algorithmic bytes = n^2 * 2 per sweep
+    # roofline of the dominant kernel (the scaling kernel: over 99% of the step).
+    # Algorithmic bytes per sweep = n^2 * (bytes per weight): one read of the integer matrix.
+    # The step kernel reads its FP32 step matrix instead (n * ceil(n/4)*4 * 4 bytes per
+    # sweep), reported beside as bytes_read_per_sweep.
     peak, peak_kind = load_peaks()
     sweeps_per_step = sweeps / args.steps
     kernel_ms = statistics.mean(kms)
+    used = res["scale"].get("kernel_used")
     alg_bytes = sweeps_per_step * n * n * w.dtype.itemsize
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
-    traffic = fused_traffic_per_sweep(n, w.dtype.itemsize)
+    read_per_sweep = (n * ((n + 3) // 4 * 4) * 4) if used == 3 else (n * n * w.dtype.itemsize * (2 if used == 2 else 1))
+    traffic = fused_traffic_per_sweep(n, w.dtype.itemsize) if used == 1 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic * sweeps_per_step if traffic else None,
                 "traffic_per_sweep": traffic, "traffic_source": TRAFFIC_SOURCE if traffic else
                 "none for this kernel source or size",
-                "kernel": ("fused_kernel (persistent Sinkhorn sweep)" if res["scale"].get("kernel_used") == 1
-                           else "row_lse_kernel + col_partial_kernel (plain sweep)"),
+                "kernel": KERNEL_NAMES.get(used, "?"),
+                "bytes_read_per_sweep": read_per_sweep,
+                "frac_of_bytes_read": read_per_sweep * sweeps_per_step / (kernel_ms / 1e3) / 1e9 / peak,
                 "peak_source": f"{peak_kind} hbm_gbs", "sweep_us": kernel_ms * 1e3 / max(sweeps_per_step, 1)}
 
     # end to end through the C ABI with the matrix in pinned host memory
     pinned = torch.from_numpy(np.ascontiguousarray(w)).pin_memory()
     hw = pinned.numpy()
-    api.sa_assign_host(ctx, hw, ps, 1e-6, args.max_sweeps)
+    api.sa_assign_host(ctx, hw, ps, 1e-6, args.max_sweeps, kernel=args.kernel)
     e2e_t, e2e_sw = [], 0
     for _ in range(max(1, min(args.steps, 3))):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r2 = api.sa_assign_host(ctx, hw, ps, 1e-6, args.max_sweeps)
+        r2 = api.sa_assign_host(ctx, hw, ps, 1e-6, args.max_sweeps, kernel=args.kernel)
         e1.record(stream)
         e1.synchronize()
         e2e_t.append(e0.elapsed_time(e1))
@@ -483,8 +496,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 (exp/sum), f64 potentials", "data": "synthetic",
                 "config": dict(cfg, n=n, sweeps_per_step=sweeps_per_step, parallelism=f"replicas x{world}",
                                l2="flushed between steps (256 MiB write)",
-                               impl=("fused persistent kernel" if res["scale"].get("kernel_used") == 1
-                                     else "plain row/column kernels"),
+                               impl=KERNEL_NAMES.get(res["scale"].get("kernel_used"), "?"),
                                nnz_first=res["nnz_first"], gamma=res["gamma"], repairs=res["repairs"],
                                ms_scale=res["ms_scale"], ms_prune=res["ms_prune"], ms_solve=res["ms_solve"],
                                ms_certify=res["ms_certify"], converged=res["scale"]["converged"]),

@@ -60,10 +60,21 @@ typedef enum { SA_I16 = 0, SA_I32 = 1 } sa_wtype;
  * in FP64 (slow on GB300; a reference for the error of the other two). */
 typedef enum { SA_PREC_MIXED = 0, SA_PREC_FP32 = 1, SA_PREC_FP64 = 2 } sa_prec;
 
-/* Which sweep implementation sa_scale uses.  FUSED: one persistent cooperative kernel
- * runs the whole schedule, one read of A per sweep.  PLAIN: separate row and column
- * kernels per sweep launched from the host (two reads of A), the comparison path. */
-typedef enum { SA_KERNEL_AUTO = 0, SA_KERNEL_FUSED = 1, SA_KERNEL_PLAIN = 2 } sa_kernel;
+/* Which sweep implementation sa_scale uses.
+ * FUSED: one persistent cooperative kernel runs the whole schedule, one read of the
+ *   integer matrix per sweep, exp2/log2 of every element on the SFU in FP32.  The SFU
+ *   logarithm's absolute error (about 2^-21) is multiplied by p in the exponent, so the
+ *   FP64-checked row and column sums of the result are off by about 1.3e-7 p.
+ * PLAIN: separate row and column kernels per sweep launched from the host (two reads of
+ *   the matrix per sweep), the comparison path; the only path for SA_PREC_FP64.
+ * STEP: one persistent cooperative kernel; at the start of every p step it evaluates
+ *   K = 2^(p log2 w - C_i - V_j) once (FP64 exponent from an exact log2 table, one FP32
+ *   rounding) into a workspace of n * ceil(n/4)*4 floats, and each sweep reads K once
+ *   (4 bytes per element): no per-element SFU work in the sweeps and an error that does
+ *   not grow with p.  Needs n <= 12288.
+ * AUTO: STEP for SA_PREC_MIXED when it applies, else FUSED when it applies, else PLAIN;
+ *   PLAIN for SA_PREC_FP64. */
+typedef enum { SA_KERNEL_AUTO = 0, SA_KERNEL_FUSED = 1, SA_KERNEL_PLAIN = 2, SA_KERNEL_STEP = 3 } sa_kernel;
 
 /* A device matrix: w points to n rows of ld weights of type wtype. */
 typedef struct {

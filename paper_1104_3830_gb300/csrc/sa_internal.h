@@ -98,6 +98,10 @@ sa_status scale_fused(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, d
 sa_status scale_fp64(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double* U,
                      double* V, sa_scale_info* info);
 bool fused_supported(const sa_ctx* ctx, const sa_matrix* a);
+// sweep_step.cu: the per-step FP32 matrix path (SA_KERNEL_STEP)
+sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double* U,
+                     double* V, sa_scale_info* info);
+bool step_supported(const sa_ctx* ctx, const sa_matrix* a);
 size_t fused_workspace_bytes(const sa_ctx* ctx, const sa_matrix* a);
 
 // natural <-> log2 units, in place on the device (n doubles), y = x * f

@@ -4,10 +4,11 @@
 //
 // Work split.  Block b owns the row stripe [b*n/G, (b+1)*n/G).  Within a block every
 // compute thread owns a fixed set of 16-byte column chunks, so the column partial sums of
-// the stripe live in registers for the whole sweep.  One extra producer warp streams the
-// rows through a shared-memory ring with the bulk-copy engine (cp.async.bulk + mbarrier):
-// a slot is refilled as soon as every compute warp has released it (empty mbarrier), so
-// copy issue and copy latency stay off the compute warps' path.
+// the stripe live in registers for the whole sweep.  Rows stream through a shared-memory
+// ring filled by the bulk-copy engine (cp.async.bulk + mbarrier).  Each warp counts its
+// release of a slot on a shared counter; the warp whose release completes the count
+// refills the slot at once with the row RING positions ahead, so nobody waits to issue a
+// copy and a slot is reused as soon as the last reader is done with it.
 //
 // One sweep, in log2 units (U = u/ln2, V = v/ln2, L = log2 w):
 //   row i   t_ij = 2^(p log2(w_ij a_i) - Vh_j) * c_j          (FP32, SFU ex2/lg2)
@@ -113,12 +114,6 @@ struct KahanF {
     }
 };
 
-// Arrive on a CTA mbarrier (release at CTA scope: prior shared stores are visible to
-// threads that complete a wait on this phase).
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 // Grid barrier on a monotonic arrival counter: barrier number `k` (0, 1, 2, ...) completes
 // when the counter reaches (k + 1) * nblocks.  Bounded wait; false on timeout or error.
 __device__ __forceinline__ bool grid_sync(unsigned* ctr, unsigned target, int* err, int* s_ok) {
@@ -145,14 +140,16 @@ __device__ __forceinline__ bool grid_sync(unsigned* ctr, unsigned target, int* e
     return *s_ok != 0;
 }
 
-// Named barrier over the NT compute threads (the producer warp does not take part).
-__device__ __forceinline__ void compute_sync(int nthreads) {
-    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+// Shared-memory fetch-and-add with acquire-release semantics at CTA scope: the caller's
+// earlier reads are ordered before it, and the releases it observes before what follows.
+__device__ __forceinline__ unsigned atom_add_acq_rel_cta(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_u32(p)), "r"(v) : "memory");
+    return old;
 }
 
-// Block = NT compute threads + one producer warp that streams the rows into the ring.
 template <typename WT, int NT, int CH, int RING, int R>
-__global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
+__global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
     constexpr int VEC = Vec<WT>::N;
     constexpr int NW = NT / 32;
     constexpr int M = CH * VEC;   // columns owned per thread
@@ -163,9 +160,10 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* ring = smem;
     uint64_t* mbar = (uint64_t*)(smem + (size_t)RING * A.row_bytes);   // [RING] bulk-copy arrivals (full)
-    uint64_t* mempty = mbar + RING;                                    // [RING] slot read by every warp (empty)
-    uint64_t* mrow = mempty + RING;                                    // [NRED] row-sum publication
-    float4* tbuf = (float4*)(mrow + NRED + ((2 * RING + NRED) & 1));   // [4][M4][NT]
+    uint64_t* mrow = mbar + RING;                                      // [NRED] row-sum publication
+    unsigned* rel_cnt = (unsigned*)(mrow + NRED);                      // [RING] warp releases per slot
+    unsigned* iss_cnt = rel_cnt + RING;                                // [RING] copies issued per slot
+    float4* tbuf = (float4*)(mrow + NRED + RING + ((2 * RING + NRED) & 1));   // [4][M4][NT]
     float* red = (float*)(tbuf + (size_t)4 * M4 * NT);                 // [NRED][2][NW]
     float* red2 = red + NRED * 2 * NW;                                 // [NW] slow path
     float* Lr = red2 + NW;                                             // [max_rows]
@@ -178,7 +176,6 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
     const int G = gridDim.x;
     const int b = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const bool producer = wid == NW;   // the extra warp: bulk copies only
     const int r0 = (int)((int64_t)b * n / G);
     const int r1 = (int)((int64_t)(b + 1) * n / G);
     const int nrows = r1 - r0;
@@ -189,41 +186,43 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
 
     if (tid == 0) {
         for (int s = 0; s < RING; ++s) mbar_init(&mbar[s], 1);
-        for (int s = 0; s < RING; ++s) mbar_init(&mempty[s], NW);
+        for (int s = 0; s < RING; ++s) rel_cnt[s] = iss_cnt[s] = 0;
         for (int s = 0; s < NRED; ++s) mbar_init(&mrow[s], NW);
         mbar_fence_init();
         s_flag = 0;
     }
     __syncthreads();
 
-    uint32_t iss = 0, it = 0;   // rows issued / consumed by this block, over all sweeps
+    uint32_t it = 0;            // rows consumed by this block, over all sweeps
     uint32_t gbase = 0;         // row stages completed by this block, over all sweeps
     unsigned nbar = 0;          // grid barriers passed
     int rphase = 0;             // sweeps of earlier steps (selects the residual word)
-    auto issue_row = [&](int q) {   // producer lane 0 only
-        const uint32_t slot = iss % RING;
+    // Consumption index u holds local row u % nrows in slot u % RING (phase u / RING).
+    auto issue_index = [&](uint32_t u) {   // one thread
+        const uint32_t slot = u % RING;
+        const int q = (int)(u % (uint32_t)nrows);
+        iss_cnt[slot] += 1;
         mbar_arrive_expect_tx(&mbar[slot], A.row_bytes);
         bulk_g2s(ring + (size_t)slot * A.row_bytes, wbase + (size_t)(r0 + q) * pitch, A.row_bytes, &mbar[slot]);
-        ++iss;
     };
-    // The producer issues consumption indices in order (index u holds local row u % nrows),
-    // each into the slot freed by the index RING earlier once every compute warp has read it.
-    auto produce_rows = [&](uint32_t upto) {   // producer lane 0 only
-        while (iss < upto) {
-            if (iss >= (uint32_t)RING) {
-                const uint32_t prev = iss - RING;
-                if (!mbar_wait(&mempty[prev % RING], (prev / RING) & 1u, A.err, kWaitTimeoutNs)) {
-                    s_flag = 1;
-                    return;
-                }
-            }
-            issue_row((int)(iss % (uint32_t)nrows));
+    // lane 0, after __syncwarp: the warp is done reading index u; the last of the NW
+    // warps refills the slot with index u + RING
+    auto release_index = [&](uint32_t u) {
+        const uint32_t slot = u % RING;
+        const unsigned old = atom_add_acq_rel_cta(&rel_cnt[slot], 1u);
+        if ((old + 1u) % (unsigned)NW == 0u) {
+            fence_proxy_async_smem();
+            issue_index(u + RING);
         }
     };
+    // wait for the last copy issued into every slot (bounded), so none is in flight at exit
     auto drain = [&]() {
-        if (producer && lane == 0) {
-            for (uint32_t q = it; q < iss; ++q)
-                if (!mbar_wait(&mbar[q % RING], (q / RING) & 1u, A.err, kWaitTimeoutNs)) break;
+        __syncthreads();
+        if (tid == 0) {
+            for (int s = 0; s < RING; ++s) {
+                const unsigned k = iss_cnt[s];
+                if (k > 0u && !mbar_wait(&mbar[s], (k - 1u) & 1u, A.err, kWaitTimeoutNs)) break;
+            }
         }
         __syncthreads();
     };
@@ -232,12 +231,15 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
         return grid_sync(A.bar, nbar * (unsigned)G, A.err, &s_ok);
     };
 
+    if (tid == 0 && nrows > 0)
+        for (uint32_t u = 0; u < (uint32_t)RING; ++u) issue_index(u);   // the first RING rows
+
     int cidx[CH];
     int nval[CH];
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
         cidx[k] = tid + k * NT;
-        nval[k] = (!producer && cidx[k] < NC) ? min(VEC, n - cidx[k] * VEC) : 0;
+        nval[k] = cidx[k] < NC ? min(VEC, n - cidx[k] * VEC) : 0;
     }
 
     float S[M], vh[M], vc[M];
@@ -306,11 +308,11 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
         const float sp0 = row_terms(ring + (size_t)(u0 % RING) * A.row_bytes, Lr[q0], pf, ts);
         const float sp1 = two ? row_terms(ring + (size_t)((u0 + 1) % RING) * A.row_bytes, Lr[q0 + 1], pf, ts + 1) : 0.0f;
         // this warp is done with the rows' slots (an exact-max redo reads the row from
-        // global memory): hand them back to the producer
+        // global memory): release them
         __syncwarp();
         if (lane == 0) {
-            mbar_arrive(&mempty[u0 % RING]);
-            if (two) mbar_arrive(&mempty[(u0 + 1) % RING]);
+            release_index(u0);
+            if (two) release_index(u0 + 1);
         }
 
         const float w0 = warp_sum(sp0);
@@ -342,9 +344,9 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
             }
         }
         mx = warp_max(mx);
-        compute_sync(NT);
+        __syncthreads();
         if (lane == 0) red2[wid] = mx;
-        compute_sync(NT);
+        __syncthreads();
         float gm = -INFINITY;
         for (int x = 0; x < NW; ++x) gm = fmaxf(gm, red2[x]);
         float s2 = 0.0f;
@@ -360,9 +362,9 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
             tbuf[((size_t)slot * M4 + m4) * NT + tid] =
                 make_float4(e_loc[4 * m4], e_loc[4 * m4 + 1], e_loc[4 * m4 + 2], e_loc[4 * m4 + 3]);
         s2 = warp_sum(s2);
-        compute_sync(NT);
+        __syncthreads();
         if (lane == 0) red2[wid] = s2;
-        compute_sync(NT);
+        __syncthreads();
         float ss = 0.0f;
         for (int x = 0; x < NW; ++x) ss += red2[x];
         *gm_out = gm;
@@ -378,8 +380,7 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
         //  potential is recovered exactly as U_i = -p log2(a_i) + log2(s_i) in FP64)
         {
             const double pprev = (k > 0) ? A.P[k - 1] : p;
-            if (!producer)
-                for (int q = tid; q < nrows; q += NT) Lr[q] = (float)exp2(-fmin(fmax(A.U[r0 + q] / pprev, -120.0), 120.0));
+            for (int q = tid; q < nrows; q += NT) Lr[q] = (float)exp2(-fmin(fmax(A.U[r0 + q] / pprev, -120.0), 120.0));
         }
         __syncthreads();
         load_cols();
@@ -396,8 +397,7 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
             // q and accumulates row q's normalised terms into its column sums.  NRED = 4
             // buffers: a warp can publish row q+3 only after all warps published q+1, i.e.
             // after they read the sums of row q-1, the last reader of that buffer.
-            const int nst = producer ? 0 : (nrows + 1) / 2;
-            if (producer && lane == 0) produce_rows(it + (uint32_t)nrows + (uint32_t)min(RING, nrows));
+            const int nst = (nrows + 1) / 2;
             if (nst > 0) produce(0, pf);
             for (int g = 0; g < nst; ++g) {
                 const int q0 = 2 * g;
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
                         srow[q] = (float)exp2(un + p * log2((double)an));
                         atomicAdd(A.fallback, 1);
                     }
-                    compute_sync(NT);
+                    __syncthreads();
                 }
                 if (tid == 0) {
                     for (int r = 0; r < nr; ++r)
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
             float* pb = A.part + (size_t)b * A.npad;
 #pragma unroll
             for (int kk = 0; kk < CH; ++kk) {
-                if (nval[kk] > 0) {   // the producer warp owns no columns
+                if (nval[kk] > 0) {
 #pragma unroll
                     for (int e = 0; e < VEC; e += 4)
                         *(float4*)(pb + (size_t)cidx[kk] * VEC + e) =
@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
                 const int j = cb + (tid & 63);
                 const int grp = tid >> 6;
                 KahanF acc;
-                if (!producer && j < c1) {
+                if (j < c1) {
                     const float* pj = A.part + j;
                     for (int g0 = grp; g0 < G; g0 += FG * 20) {
                         float a[20];
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
                         for (int x = 0; x < 20; ++x) acc.add(a[x]);
                     }
                 }
-                if (!producer) redp[grp * 64 + (tid & 63)] = (double)acc.s - (double)acc.c;
+                redp[grp * 64 + (tid & 63)] = (double)acc.s - (double)acc.c;
                 __syncthreads();
                 if (tid < 64 && j < c1) {
                     double Sj = 0.0;
@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
             SA_STAMP(4);
         }
         rphase += sweeps;
-        for (int q = tid; q < nrows && !producer; q += NT) {
+        for (int q = tid; q < nrows; q += NT) {
             double uu = -p * log2((double)Lr[q]) + log2((double)srow[q]);
             if (A.f32_potentials) uu = (double)(float)uu;
             A.U[r0 + q] = uu;
@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(NT + 32, 1) fused_kernel(FusedArgs A) {
         if (k + 1 < A.n_p) {
             // warm start of the next step: (U, V) *= p_{k+1}/p_k unless v is kept
             const double f = A.keep_v ? 1.0 : A.P[k + 1] / p;
-            for (int j = c0 + tid; j < c1 && !producer; j += NT) {
+            for (int j = c0 + tid; j < c1; j += NT) {
                 double v = A.V[j] * f;
                 A.V[j] = v;
                 float h = (float)v;
@@ -575,7 +575,7 @@ sa_status launch_fused(sa_ctx* ctx, const FusedArgs& args, size_t smem, int* gri
     auto kern = fused_kernel<WT, NT, CH, RING, R>;
     SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT + 32, smem));
+    SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
     if (per_sm < 1) {
         set_error("fused sweep: kernel does not fit on an SM (smem %zu)", smem);
         return SA_E_UNSUPPORTED;
@@ -592,7 +592,7 @@ sa_status launch_fused(sa_ctx* ctx, const FusedArgs& args, size_t smem, int* gri
     *grid_out = G;
     FusedArgs a = args;
     void* params[] = {&a};
-    SA_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(NT + 32), params, smem, ctx->stream));
+    SA_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(NT), params, smem, ctx->stream));
     count_launch();
     return SA_OK;
 }
@@ -615,8 +615,7 @@ size_t fused_smem_bytes(const FusedCfg& c, unsigned row_bytes, int vec, int max_
     return head + 16 * (size_t)4 * m4 * c.nt + 4 * (size_t)(8 * nw + nw + 2 * max_rows) + 8 + 8 * fg * 64 + 1024;
 }
 
-// nt_pref: compute threads per block for 512 < chunks <= 1024 (256 x 4 or 512 x 2 chunks;
-// 1024 compute threads plus the producer warp exceed the block size limit)
+// nt_pref: threads per block for 512 < chunks <= 1024 (256 x 4 or 512 x 2 chunks)
 FusedCfg pick_cfg(const sa_matrix* a, size_t smem_optin, int max_rows, int nt_pref = 512) {
     const int vec = 16 / wbytes(a->wtype);
     const int nc = (a->n + vec - 1) / vec;

@@ -1,0 +1,727 @@
+// sweep_step.cu -- fused Sinkhorn sweep over a per-step FP32 matrix (Sec. 4.1.2 log-domain
+// iteration, Sec. 4.2 stopping rule, deformed warm start between p steps as in Sec. 4.1).
+//
+// At the start of every p step each block evaluates, for its own row stripe,
+//     K_ij = 2^(p log2 w_ij - C_i - V_j)        (C_i ~ max_j (p log2 w_ij - V_j))
+// once, with the exponent formed in FP64 from an exact FP64 table of log2 w, and stores K as
+// FP32 in a global workspace.  K is the iterate X(p) at the step start, so every entry is
+// in [0, ~1] and its relative error (about 2e-7) does not grow with p.  Within the step
+// the potentials move only through a column factor c_j = 2^(Vs_j - V_j) (Vs = V at the
+// step start) and the fresh row sums, so a sweep is
+//     s_i  = sum_j K_ij c_j,     S_j = c_j sum_i K_ij / s_i,     V_j += log2 S_j
+// and U_i = C_i + log2 s_i.  No logarithm or exponential is evaluated per entry and sweep.
+//
+// Work split, ring and barriers follow the single-read sweep: block b owns the row stripe
+// [b n/G, (b+1) n/G) and finalises the same index range of columns; each thread owns fixed
+// 16-byte chunks (4 columns) of every row, keeping its column partial sums in registers;
+// rows stream through a shared-memory ring by bulk copies (cp.async.bulk + mbarrier).
+// Because K stays in the ring slot until the row sum is known, the second use of a row
+// (the column accumulation) re-reads the slot: no stash of terms is needed.  The warp
+// whose release completes a slot's count refills it with the row RING positions ahead.
+//
+// Every wait is bounded (2 s); on expiry the kernel records kErrTimeout, waits for its
+// outstanding copies (bounded) and returns.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "common.cuh"
+#include "sa_internal.h"
+
+namespace sa {
+
+namespace {
+
+constexpr int kStepNred = 4;   // row-sum publication buffers
+
+struct StepArgs {
+    const void* w;
+    int n;
+    int64_t ld;            // elements
+    int i16;               // weights are int16 (else int32)
+    float* K;              // n x ldk, FP32
+    int64_t ldk;           // floats, multiple of 4
+    unsigned row_bytes;    // bytes copied per K row (multiple of 16)
+    int ring;              // ring slots (>= 4)
+    const double* tab;     // log2 k for k = 0..kTab-1 (tab[0] = -inf)
+    const double* P;       // schedule
+    int k0, n_p;
+    double tol;
+    int max_sweeps;
+    int keep_v;
+    double* U;             // n, log2 units
+    double* V;             // n, log2 units
+    double* Vs;            // n, V at the step start
+    float* Cf;             // n, 2^(Vs - V)
+    float* part;           // G x npad column partials
+    int npad;
+    float* rmax;           // 2 alternating residual words
+    unsigned* bar;         // grid barrier counter
+    int* err;
+    int* sweeps_out;       // n_p
+    double* resid_out;     // n_p
+    int max_rows;
+};
+
+constexpr int kTab = 32768;
+
+__global__ void log2_table_kernel(double* tab) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < kTab) tab[k] = k > 0 ? log2((double)k) : -INFINITY;
+}
+
+__device__ __forceinline__ void load_w4(const StepArgs& A, int64_t row, int j, int cnt, int w[4]) {
+    if (A.i16) {
+        const int16_t* p = (const int16_t*)A.w + row * A.ld + j;
+        if (cnt == 4) {
+            const uint2 q = *(const uint2*)p;
+            w[0] = (int16_t)(q.x & 0xffffu);
+            w[1] = (int16_t)(q.x >> 16);
+            w[2] = (int16_t)(q.y & 0xffffu);
+            w[3] = (int16_t)(q.y >> 16);
+        } else {
+            for (int e = 0; e < 4; ++e) w[e] = e < cnt ? p[e] : 0;
+        }
+    } else {
+        const int32_t* p = (const int32_t*)A.w + row * A.ld + j;
+        if (cnt == 4) {
+            const int4 q = *(const int4*)p;
+            w[0] = q.x;
+            w[1] = q.y;
+            w[2] = q.z;
+            w[3] = q.w;
+        } else {
+            for (int e = 0; e < 4; ++e) w[e] = e < cnt ? p[e] : 0;
+        }
+    }
+}
+
+// exact log2 of a positive integer weight in FP64 (table for the int16 range)
+__device__ __forceinline__ double wlog2(const double* tab, int w) {
+    return w < kTab ? __ldg(tab + (w > 0 ? w : 0)) : log2((double)w);
+}
+
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_u32(p)), "r"(v) : "memory");
+    return old;
+}
+
+// orders this thread's generic-proxy accesses (global and shared) before later bulk copies
+__device__ __forceinline__ void fence_proxy_async_all() {
+    asm volatile("fence.proxy.async;" ::: "memory");
+}
+
+__device__ __forceinline__ bool step_grid_sync(unsigned* ctr, unsigned target, int* err, int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        if (ld_acquire(ctr) < target) {
+            const uint64_t t0 = globaltimer_ns();
+            unsigned spins = 0;
+            while (ld_acquire(ctr) < target) {
+                if ((++spins & 31u) == 0) {
+                    if (*(volatile int*)err != 0) { ok = 0; break; }
+                    if (globaltimer_ns() - t0 > kWaitTimeoutNs) { atomicCAS(err, 0, kErrTimeout); ok = 0; break; }
+                }
+                __nanosleep(32);
+            }
+        }
+        if (*(volatile int*)err != 0) ok = 0;
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+struct KahanS {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+template <int NT, int CH>
+__global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
+    constexpr int NW = NT / 32;
+    constexpr int M = CH * 4;   // columns owned per thread
+    constexpr int NRED = kStepNred;
+    constexpr int FG = NT / 64;
+    static_assert(NT % 64 == 0, "layout");
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int RING = A.ring;
+    unsigned char* ring = smem;
+    uint64_t* mbar = (uint64_t*)(smem + (size_t)RING * A.row_bytes);   // [RING] copy arrivals
+    uint64_t* mrow = mbar + RING;                                      // [NRED] row-sum publication
+    unsigned* rel_cnt = (unsigned*)(mrow + NRED);                      // [RING]
+    unsigned* iss_cnt = rel_cnt + RING;                                // [RING]
+    // 8 (2 RING + NRED) bytes of barriers and counters end on a 16-byte boundary, so the
+    // float4-read partials come first
+    float* red = (float*)(mrow + NRED + RING);                         // [NRED][2][NW] (16-aligned)
+    double* crow = (double*)(red + NRED * 2 * NW);                     // [max_rows] row references
+    double* redp = crow + A.max_rows;                                  // [FG][64]
+    double* redd = redp + FG * 64;                                     // [NW]
+    float* srow = (float*)(redd + NW);                                 // [max_rows]
+    __shared__ int s_flag, s_ok;
+    __shared__ float s_res;
+    __shared__ double s_max;
+
+    const int n = A.n;
+    const int G = gridDim.x;
+    const int b = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int r0 = (int)((int64_t)b * n / G);
+    const int r1 = (int)((int64_t)(b + 1) * n / G);
+    const int nrows = r1 - r0;
+    const int c0 = r0, c1 = r1;
+    const int NC = (n + 3) / 4;
+    const unsigned char* kbase = (const unsigned char*)A.K;
+    const size_t kpitch = (size_t)A.ldk * sizeof(float);
+
+    if (tid == 0) {
+        for (int s = 0; s < RING; ++s) mbar_init(&mbar[s], 1);
+        for (int s = 0; s < RING; ++s) rel_cnt[s] = iss_cnt[s] = 0;
+        for (int s = 0; s < NRED; ++s) mbar_init(&mrow[s], NW);
+        mbar_fence_init();
+        s_flag = 0;
+    }
+    __syncthreads();
+
+    uint32_t it = 0;      // consumption index of the current sweep's first row
+    uint32_t ofs = 0;     // index u holds local row (u - ofs) % nrows
+    uint32_t gbase = 0;   // row stages completed, over all sweeps
+    unsigned nbar = 0;
+    int rphase = 0;
+    auto issue_index = [&](uint32_t u) {   // one thread
+        const uint32_t slot = u % (uint32_t)RING;
+        const int q = (int)((u - ofs) % (uint32_t)nrows);
+        iss_cnt[slot] += 1;
+        mbar_arrive_expect_tx(&mbar[slot], A.row_bytes);
+        bulk_g2s(ring + (size_t)slot * A.row_bytes, kbase + (size_t)(r0 + q) * kpitch, A.row_bytes, &mbar[slot]);
+    };
+    auto release_index = [&](uint32_t u) {   // lane 0 after __syncwarp
+        const uint32_t slot = u % (uint32_t)RING;
+        const unsigned old = atom_add_acq_rel(&rel_cnt[slot], 1u);
+        if ((old + 1u) % (unsigned)NW == 0u) {
+            fence_proxy_async_smem();
+            issue_index(u + (uint32_t)RING);
+        }
+    };
+    auto wait_copies = [&]() {   // tid 0: the last copy issued into every slot
+        for (int s = 0; s < RING; ++s) {
+            const unsigned k = iss_cnt[s];
+            if (k > 0u && !mbar_wait(&mbar[s], (k - 1u) & 1u, A.err, kWaitTimeoutNs)) break;
+        }
+    };
+    auto drain = [&]() {
+        __syncthreads();
+        if (tid == 0) wait_copies();
+        __syncthreads();
+    };
+    auto gsync = [&]() -> bool {
+        ++nbar;
+        return step_grid_sync(A.bar, nbar * (unsigned)G, A.err, &s_ok);
+    };
+
+    int cidx[CH];
+    int nval[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+        cidx[k] = tid + k * NT;
+        nval[k] = cidx[k] < NC ? min(4, n - cidx[k] * 4) : 0;
+    }
+    float S[M], cf[M];
+
+    // ---- K rows of this stripe for step p (V holds the step's starting column potentials) ----
+    auto prep = [&](double p) {
+        const float pf = (float)p;
+        double* vsm = (double*)ring;   // the ring is idle: stage V there
+        for (int j = tid; j < n; j += NT) vsm[j] = A.V[j];
+        __syncthreads();
+        for (int q = 0; q < nrows; ++q) {
+            const int64_t row = r0 + q;
+            // reference C ~ max_j (p log2 w - V_j), FP32 estimate (only a scale)
+            float mloc = -INFINITY;
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                if (nval[k] == 0) continue;
+                int w[4];
+                load_w4(A, row, cidx[k] * 4, nval[k], w);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (e < nval[k] && w[e] > 0)
+                        mloc = fmaxf(mloc, fmaf(pf, lg2_approx((float)w[e]), -(float)vsm[cidx[k] * 4 + e]));
+            }
+            mloc = warp_max(mloc);
+            if (lane == 0) redd[wid] = (double)mloc;
+            __syncthreads();
+            if (tid == 0) {
+                double m = -INFINITY;
+                for (int x = 0; x < NW; ++x) m = fmax(m, redd[x]);
+                if (!(m > -INFINITY)) { atomicCAS(A.err, 0, kErrNonfinite); m = 0.0; }
+                s_max = m;
+                crow[q] = m;
+            }
+            __syncthreads();
+            const double m = s_max;
+            float* krow = A.K + row * A.ldk;
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                if (cidx[k] >= (int)(A.ldk / 4)) continue;
+                float kv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                if (nval[k] > 0) {
+                    int w[4];
+                    load_w4(A, row, cidx[k] * 4, nval[k], w);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (e < nval[k] && w[e] > 0) {
+                            // exponent in FP64 (exact table log2), then one rounding to FP32
+                            const double x = fma(p, wlog2(A.tab, w[e]), -(vsm[cidx[k] * 4 + e] + m));
+                            kv[e] = ex2_approx((float)x);
+                        }
+                    }
+                }
+                *(float4*)(krow + cidx[k] * 4) = make_float4(kv[0], kv[1], kv[2], kv[3]);
+            }
+        }
+        fence_proxy_async_all();   // K rows are read back, and the V scratch overwritten, by bulk copies
+        __syncthreads();
+    };
+
+    for (int k = A.k0; k < A.n_p; ++k) {
+        const double p = A.P[k];
+        if (k > A.k0) {
+            // copies prefetched at the end of the previous step hold old K rows: let them land
+            // before the ring is reused as scratch and the rows are rewritten
+            __syncthreads();
+            if (tid == 0) wait_copies();
+            __syncthreads();
+        }
+        if (s_flag) { drain(); return; }
+        for (int j = c0 + tid; j < c1; j += NT) {
+            A.Vs[j] = A.V[j];
+            A.Cf[j] = 1.0f;
+        }
+        prep(p);
+        if (nrows > 0) {
+            if (k == A.k0) {
+                if (tid == 0)
+                    for (uint32_t u = 0; u < (uint32_t)RING; ++u) issue_index(u);
+            } else {
+                // the stale prefetches [it, it + RING) are skipped: every warp releases
+                // them, which refills their slots with the new rows
+                ofs += (uint32_t)RING;
+                __syncwarp();
+                if (lane == 0)
+                    for (uint32_t u = it; u < it + (uint32_t)RING; ++u) release_index(u);
+                it += (uint32_t)RING;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) cf[m] = (m % 4) < nval[m / 4] ? 1.0f : 0.0f;
+        int sweeps = 0;
+        float resid = INFINITY;
+        bool done = false;
+        while (!done) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) S[m] = 0.0f;
+            // ---------------- row pass ----------------
+            // stage g = local rows 2g, 2g+1.  produce(g): partial row sums, published on
+            // mrow[g % NRED]; consume(g): wait for every warp's partials, accumulate the
+            // normalised rows into the column sums, release the slots.
+            const int nst = (nrows + 1) / 2;
+            auto row_partial = [&](const unsigned char* rowp) -> float {
+                float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+                for (int kk = 0; kk < CH; ++kk) {
+                    if (nval[kk] == 0) continue;   // chunk beyond the row: not in the slot
+                    const float4 kv = *(const float4*)(rowp + (size_t)cidx[kk] * 16);
+                    a0 = fmaf(kv.x, cf[4 * kk], a0);
+                    a1 = fmaf(kv.y, cf[4 * kk + 1], a1);
+                    a0 = fmaf(kv.z, cf[4 * kk + 2], a0);
+                    a1 = fmaf(kv.w, cf[4 * kk + 3], a1);
+                }
+                return a0 + a1;
+            };
+            auto produce = [&](int g) {
+                const int q0 = 2 * g;
+                const bool two = q0 + 1 < nrows;
+                const uint32_t u0 = it + q0;
+                bool ok = mbar_wait(&mbar[u0 % RING], (u0 / RING) & 1u, A.err, kWaitTimeoutNs);
+                if (two) ok = mbar_wait(&mbar[(u0 + 1) % RING], ((u0 + 1) / RING) & 1u, A.err, kWaitTimeoutNs) && ok;
+                if (!ok) s_flag = 1;
+                const float sp0 = row_partial(ring + (size_t)(u0 % RING) * A.row_bytes);
+                const float sp1 = two ? row_partial(ring + (size_t)((u0 + 1) % RING) * A.row_bytes) : 0.0f;
+                const float w0 = warp_sum(sp0);
+                const float w1 = warp_sum(sp1);
+                if (lane == 0) {
+                    const uint32_t gs = gbase + g;
+                    red[((gs % NRED) * 2) * NW + wid] = w0;
+                    red[((gs % NRED) * 2 + 1) * NW + wid] = w1;
+                    mbar_arrive(&mrow[gs % NRED]);
+                }
+            };
+            auto consume = [&](int g) -> bool {
+                const int q0 = 2 * g;
+                const bool two = q0 + 1 < nrows;
+                const uint32_t u0 = it + q0;
+                const uint32_t gs = gbase + g;
+                if (!mbar_wait(&mrow[gs % NRED], (gs / NRED) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
+                if (s_flag) return false;
+                float ss[2];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float4* rv = (const float4*)(red + ((gs % NRED) * 2 + r) * NW);
+                    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll
+                    for (int x = 0; x < NW / 4; ++x) {
+                        const float4 q4 = rv[x];
+                        a0 += q4.x;
+                        a1 += q4.y;
+                        a2 += q4.z;
+                        a3 += q4.w;
+                    }
+                    ss[r] = (a0 + a1) + (a2 + a3);
+                }
+                if (!(ss[0] >= 0x1p-120f && ss[0] <= 0x1p120f) || (two && !(ss[1] >= 0x1p-120f && ss[1] <= 0x1p120f))) {
+                    if (tid == 0) atomicCAS(A.err, 0, kErrNonfinite);
+                    s_flag = 1;
+                    return false;
+                }
+                if (tid == 0) {
+                    srow[q0] = ss[0];
+                    if (two) srow[q0 + 1] = ss[1];
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    if (r == 1 && !two) break;
+                    const float inv = rcp_approx(ss[r]);
+                    const unsigned char* rowp = ring + (size_t)((u0 + r) % RING) * A.row_bytes;
+#pragma unroll
+                    for (int kk = 0; kk < CH; ++kk) {
+                        if (nval[kk] == 0) continue;
+                        const float4 kv = *(const float4*)(rowp + (size_t)cidx[kk] * 16);
+                        S[4 * kk] = fmaf(kv.x, inv, S[4 * kk]);
+                        S[4 * kk + 1] = fmaf(kv.y, inv, S[4 * kk + 1]);
+                        S[4 * kk + 2] = fmaf(kv.z, inv, S[4 * kk + 2]);
+                        S[4 * kk + 3] = fmaf(kv.w, inv, S[4 * kk + 3]);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    release_index(u0);
+                    if (two) release_index(u0 + 1);
+                }
+                return true;
+            };
+            if (nst > 0) produce(0);
+            for (int g = 0; g < nst; ++g) {
+                if (g + 1 < nst) produce(g + 1);
+                if (!consume(g)) break;
+            }
+            __syncthreads();
+            if (s_flag) { drain(); return; }
+            it += (uint32_t)nrows;
+            gbase += (uint32_t)nst;
+            float* pb = A.part + (size_t)b * A.npad;
+#pragma unroll
+            for (int kk = 0; kk < CH; ++kk) {
+                if (nval[kk] > 0)
+                    *(float4*)(pb + (size_t)cidx[kk] * 4) =
+                        make_float4(S[4 * kk] * cf[4 * kk], S[4 * kk + 1] * cf[4 * kk + 1],
+                                    S[4 * kk + 2] * cf[4 * kk + 2], S[4 * kk + 3] * cf[4 * kk + 3]);
+            }
+            ++sweeps;
+            if (!gsync()) { drain(); return; }
+            // ---------------- column finalisation of columns [c0, c1) ----------------
+            float* rmax_word = A.rmax + ((sweeps + rphase) & 1);
+            float rmax = 0.0f;
+            for (int cb = c0; cb < c1; cb += 64) {
+                const int j = cb + (tid & 63);
+                const int grp = tid >> 6;
+                KahanS acc;
+                if (j < c1) {
+                    const float* pj = A.part + j;
+                    for (int g0 = grp; g0 < G; g0 += FG * 16) {
+                        float a[16];
+#pragma unroll
+                        for (int x = 0; x < 16; ++x) {
+                            const int g = g0 + x * FG;
+                            a[x] = g < G ? __ldcg(pj + (size_t)g * A.npad) : 0.0f;
+                        }
+#pragma unroll
+                        for (int x = 0; x < 16; ++x) acc.add(a[x]);
+                    }
+                }
+                redp[grp * 64 + (tid & 63)] = (double)acc.s - (double)acc.c;
+                __syncthreads();
+                if (tid < 64 && j < c1) {
+                    double Sj = 0.0;
+#pragma unroll
+                    for (int x = 0; x < FG; ++x) Sj += redp[x * 64 + tid];
+                    if (!(Sj > 0.0) || !isfinite(Sj)) atomicCAS(A.err, 0, kErrNonfinite);
+                    const double d = Sj - 1.0;
+                    rmax = fmaxf(rmax, (float)fabs(d));
+                    double lg;
+                    if (fabs(d) < 1e-3) {
+                        // log2(1 + d) by its series in FP64 (|d| < 1e-3: five terms reach 1e-17)
+                        lg = d * (1.0 + d * (-0.5 + d * (1.0 / 3.0 + d * (-0.25 + d * 0.2)))) * kLog2e;
+                    } else {
+                        lg = log2(Sj);
+                    }
+                    const double v = A.V[j] + lg;
+                    A.V[j] = v;
+                    A.Cf[j] = ex2_approx((float)(A.Vs[j] - v));
+                }
+                __syncthreads();
+            }
+            if (wid < 2) {
+                rmax = warp_max(rmax);
+                if (lane == 0 && rmax > 0.0f) atomicMax((unsigned*)rmax_word, __float_as_uint(rmax));
+            }
+            if (!gsync()) { drain(); return; }
+            // ---------------- decision (identical in every block) ----------------
+            if (tid == 0) {
+                s_res = __uint_as_float(ld_acquire((const unsigned*)rmax_word));
+                if (b == 0) A.rmax[((sweeps + rphase) + 1) & 1] = 0.0f;
+            }
+            __syncthreads();
+            resid = s_res;
+            done = (resid <= A.tol) || (sweeps >= A.max_sweeps);
+            if (!done) {
+#pragma unroll
+                for (int kk = 0; kk < CH; ++kk)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        cf[4 * kk + e] = e < nval[kk] ? __ldcg(A.Cf + cidx[kk] * 4 + e) : 0.0f;
+            }
+        }
+        rphase += sweeps;
+        for (int q = tid; q < nrows; q += NT) A.U[r0 + q] = crow[q] + log2((double)srow[q]);
+        if (b == 0 && tid == 0) {
+            A.sweeps_out[k] = sweeps;
+            A.resid_out[k] = resid;
+        }
+        if (k + 1 < A.n_p) {
+            const double f = A.keep_v ? 1.0 : A.P[k + 1] / p;
+            for (int j = c0 + tid; j < c1; j += NT) A.V[j] *= f;
+            if (!gsync()) { drain(); return; }
+        }
+    }
+    drain();
+}
+
+struct StepCfg {
+    int nt, ch, ring;
+};
+
+size_t step_smem_bytes(int nt, int ring, unsigned row_bytes, int max_rows) {
+    const int nw = nt / 32;
+    const int fg = nt / 64;
+    return (size_t)ring * row_bytes + 8 * (size_t)(ring + kStepNred + ring) +
+           8 * (size_t)(max_rows + fg * 64 + nw) + 4 * (size_t)(kStepNred * 2 * nw + max_rows) + 1024;
+}
+
+int step_max_rows(const sa_ctx* ctx, int n) {
+    int gmin = std::max(1, std::min(ctx->num_sms, n / 8));
+    if (ctx->max_grid > 0) gmin = std::max(1, std::min(gmin, ctx->max_grid));
+    return (n + gmin - 1) / gmin + 1;
+}
+
+StepCfg pick_step(const sa_ctx* ctx, int n) {
+    const int nc = (n + 3) / 4;
+    StepCfg c{0, 0, 0};
+    if (nc <= 128) c = {128, 1, 0};
+    else if (nc <= 256) c = {256, 1, 0};
+    else if (nc <= 512) c = {512, 1, 0};
+    else if (nc <= 1024) c = {512, 2, 0};
+    else if (nc <= 2048) c = {512, 4, 0};
+    else if (nc <= 3072) c = {512, 6, 0};
+    else return c;
+    const unsigned row_bytes = (unsigned)align_up((size_t)n * 4, 16);
+    const int max_rows = step_max_rows(ctx, n);
+    // the ring doubles as scratch for V (8 n bytes) during the per-step evaluation
+    for (int ring = 8; ring >= 4; --ring) {
+        if ((size_t)ring * row_bytes < (size_t)n * 8) break;
+        if (step_smem_bytes(c.nt, ring, row_bytes, max_rows) <= ctx->smem_optin) {
+            c.ring = ring;
+            return c;
+        }
+    }
+    c.nt = 0;
+    return c;
+}
+
+template <int NT, int CH>
+sa_status launch_step(sa_ctx* ctx, const StepArgs& args, size_t smem, int* grid_out) {
+    auto kern = step_kernel<NT, CH>;
+    SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+    if (per_sm < 1) {
+        set_error("step sweep: kernel does not fit on an SM (smem %zu)", smem);
+        return SA_E_UNSUPPORTED;
+    }
+    int G = ctx->num_sms * per_sm;
+    const int gmax_rows = args.n / 8 > 0 ? args.n / 8 : 1;
+    if (G > gmax_rows) G = gmax_rows;
+    if (*grid_out > 0 && *grid_out < G) G = *grid_out;
+    if ((args.n + G - 1) / G > args.max_rows) {
+        set_error("step sweep: grid of %d blocks leaves stripes longer than %d rows", G, args.max_rows);
+        return SA_E_UNSUPPORTED;
+    }
+    *grid_out = G;
+    StepArgs a = args;
+    void* params[] = {&a};
+    SA_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(NT), params, smem, ctx->stream));
+    count_launch();
+    return SA_OK;
+}
+
+}  // namespace
+
+bool step_supported(const sa_ctx* ctx, const sa_matrix* a) {
+    const int sz = wbytes(a->wtype);
+    if (((uintptr_t)a->w & 15) != 0) return false;
+    if (((size_t)a->ld * sz) % 16 != 0) return false;
+    return pick_step(ctx, a->n).nt > 0;
+}
+
+size_t step_workspace_bytes(const sa_ctx* ctx, const sa_matrix* a, int n_p) {
+    const int n = a->n;
+    const size_t ldk = align_up((size_t)n, 4);
+    const int G_max = ctx->num_sms * 2;
+    const size_t npad = align_up((size_t)n, 32);
+    return (size_t)n * ldk * 4 + (size_t)G_max * npad * 4 + (size_t)kTab * 8 + 2 * align_up((size_t)n * 8, 256) +
+           align_up((size_t)n * 4, 256) + (size_t)n_p * 16 + 16384;
+}
+
+sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double* U, double* V,
+                     sa_scale_info* info) {
+    const int n = a->n;
+    const StepCfg cfg = pick_step(ctx, n);
+    if (cfg.nt == 0) {
+        set_error("step sweep: n=%d not supported", n);
+        return SA_E_UNSUPPORTED;
+    }
+    cudaStream_t st = ctx->stream;
+    const int G_max = ctx->num_sms * 2;
+    const int npad = (int)align_up((size_t)n, 32);
+    const int64_t ldk = (int64_t)align_up((size_t)n, 4);
+    sa_status rc = ctx->ws.reserve(step_workspace_bytes(ctx, a, o->n_p));
+    if (rc) return rc;
+    Carve cv(ctx->ws.ptr);
+    float* K = cv.take<float>((size_t)n * ldk);
+    float* part = cv.take<float>((size_t)G_max * npad);
+    double* tab = cv.take<double>(kTab);
+    double* Vs = cv.take<double>(n);
+    float* Cf = cv.take<float>(n);
+    float* rmax = cv.take<float>(2);
+    double* P = cv.take<double>(o->n_p);
+    double* resid_out = cv.take<double>(o->n_p);
+    int* sweeps_out = cv.take<int>(o->n_p);
+    unsigned* bar = cv.take<unsigned>(2);
+    int* err = cv.take<int>(1);
+    log2_table_kernel<<<kTab / 256, 256, 0, st>>>(tab);
+    count_launch();
+    SA_CUDA(cudaMemcpyAsync(P, o->p, o->n_p * sizeof(double), cudaMemcpyHostToDevice, st));
+    SA_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+    SA_CUDA(cudaMemsetAsync(rmax, 0, 2 * sizeof(float), st));
+    SA_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    SA_CUDA(cudaMemsetAsync(sweeps_out, 0, o->n_p * sizeof(int), st));
+    const int k0 = o->resume_from > 0 ? o->resume_from : 0;
+    if (k0 == 0) {
+        SA_CUDA(cudaMemsetAsync(U, 0, n * sizeof(double), st));
+        SA_CUDA(cudaMemsetAsync(V, 0, n * sizeof(double), st));
+    } else if (!o->warm_keep_v) {
+        launch_scale_vec(V, n, o->p[k0] / o->p[k0 - 1], st);
+    }
+    StepArgs args{};
+    args.w = a->w;
+    args.n = n;
+    args.ld = a->ld;
+    args.i16 = a->wtype == SA_I16;
+    args.K = K;
+    args.ldk = ldk;
+    args.row_bytes = (unsigned)align_up((size_t)n * 4, 16);
+    args.ring = cfg.ring;
+    args.tab = tab;
+    args.P = P;
+    args.k0 = k0;
+    args.n_p = o->n_p;
+    args.tol = o->tol;
+    args.max_sweeps = o->max_sweeps_per_p;
+    args.keep_v = o->warm_keep_v;
+    args.U = U;
+    args.V = V;
+    args.Vs = Vs;
+    args.Cf = Cf;
+    args.part = part;
+    args.npad = npad;
+    args.rmax = rmax;
+    args.bar = bar;
+    args.err = err;
+    args.sweeps_out = sweeps_out;
+    args.resid_out = resid_out;
+    args.max_rows = step_max_rows(ctx, n);
+    const size_t smem = step_smem_bytes(cfg.nt, cfg.ring, args.row_bytes, args.max_rows);
+    int G = ctx->max_grid > 0 ? std::min(G_max, ctx->max_grid) : G_max;
+    cudaEvent_t ev0, ev1;
+    SA_CUDA(cudaEventCreate(&ev0));
+    SA_CUDA(cudaEventCreate(&ev1));
+    SA_CUDA(cudaEventRecord(ev0, st));
+    if (cfg.nt == 128) rc = launch_step<128, 1>(ctx, args, smem, &G);
+    else if (cfg.nt == 256) rc = launch_step<256, 1>(ctx, args, smem, &G);
+    else if (cfg.ch == 1) rc = launch_step<512, 1>(ctx, args, smem, &G);
+    else if (cfg.ch == 2) rc = launch_step<512, 2>(ctx, args, smem, &G);
+    else if (cfg.ch == 4) rc = launch_step<512, 4>(ctx, args, smem, &G);
+    else rc = launch_step<512, 6>(ctx, args, smem, &G);
+    if (rc) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); return rc; }
+    SA_CUDA(cudaEventRecord(ev1, st));
+    sa_status prc = ctx->pinned.reserve(4096 + (size_t)o->n_p * 16);
+    if (prc) return prc;
+    char* hp = (char*)ctx->pinned.ptr;
+    int* h_err = (int*)hp;
+    int* h_sw = (int*)(hp + 64);
+    double* h_rs = (double*)(hp + 64 + align_up((size_t)o->n_p * 4, 64));
+    SA_CUDA(cudaMemcpyAsync(h_err, err, 4, cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaMemcpyAsync(h_sw, sweeps_out, o->n_p * 4, cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaMemcpyAsync(h_rs, resid_out, o->n_p * 8, cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaStreamSynchronize(st));
+    float kms = 0.0f;
+    SA_CUDA(cudaEventElapsedTime(&kms, ev0, ev1));
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    int64_t total = 0;
+    int conv = 1;
+    for (int k = k0; k < o->n_p; ++k) {
+        total += h_sw[k];
+        if (!(h_rs[k] <= o->tol)) conv = 0;
+    }
+    if (info) {
+        info->sweeps_total = total;
+        info->residual = h_rs[o->n_p - 1];
+        info->p_final = o->p[o->n_p - 1];
+        info->converged = conv;
+        info->steps_done = o->n_p - k0;
+        info->fallback_rows = 0;
+        info->kernel_used = SA_KERNEL_STEP;
+        info->kernel_ms = kms;
+    }
+    if (*h_err == kErrTimeout) {
+        set_error("step sweep: a bounded device wait timed out (grid of %d blocks)", G);
+        return SA_E_TIMEOUT;
+    }
+    if (*h_err == kErrNonfinite) {
+        set_error("step sweep: a row or column sum left the FP32 range (matrix without support?)");
+        return SA_E_NONFINITE;
+    }
+    return conv ? SA_OK : SA_E_NOT_CONVERGED;
+}
+
+}  // namespace sa

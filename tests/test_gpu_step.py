@@ -1,0 +1,159 @@
+"""Parity of the per-step FP32 matrix path (SA_KERNEL_STEP) with the FP64 oracle.
+
+Tolerance: at the start of every p step the kernel forms each exponent
+p*log2(w) - C_i - V_j in FP64 (exact table of log2 w) and rounds it once to FP32 before
+one SFU exp2, so every entry of the step matrix K carries a relative error of at most
+2^-24 * |exponent| * ln 2 + 2^-22 (the SFU exp2 bound); the largest entries of a row have
+exponents near 0.  Within the step only FP32 sums (relative error of a few 2^-24 each) and
+the column factors c_j = 2^(Vs_j - V_j) (one SFU exp2 each) enter.  So, unlike the
+single-read kernel whose FP32 log2 error is multiplied by p, the FP64-recomputed row and
+column sums of the result stay within a bound that does not depend on p:
+STEP_SUM_BOUND = 1e-6 (the stopping tol) + 1e-6 (arithmetic).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1104_3830_gb300 import api
+from paper_1104_3830_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+STEP_SUM_BOUND = 2e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1104_3830_gb300 import build
+    build.build()
+    c = api.sa_create(0)
+    yield c
+    c.close()
+
+
+def fp64_sum_err(b, p, u, v):
+    r, c = oracle.sums(b, p, u, v)
+    return max(np.abs(r - 1).max(), np.abs(c - 1).max())
+
+
+@pytest.mark.parametrize("n,dtype,seed", [(256, np.int32, 0), (1000, np.int16, 1), (777, np.int32, 2),
+                                          (8, np.int16, 3), (1, np.int32, 4), (130, np.int16, 5),
+                                          (2049, np.int16, 6)])
+def test_low_p_matches_oracle_elementwise(ctx, n, dtype, seed):
+    """Ragged widths (n % 4 != 0, a single row, several column chunks per thread)."""
+    w = W.uniform(n, 1, 1000, 900 + seed, dtype=dtype)
+    ps = [1.0, 2.0, 4.0, 8.0]
+    d = api.to_device(w)
+    u, v, info = api.sa_scale(ctx, d, ps, 1e-6, 20000, kernel="step")
+    assert info["status"] == 0 and info["kernel_used"] == 3, info
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    b = oracle.log_weights(w.astype(np.int64))
+    uo, vo, swo, rso, sto = oracle.sinkhorn(b, ps, 1e-6, 20000)
+    assert sto == 0
+    xg = oracle.xmatrix(b, ps[-1], u, v)
+    xo = oracle.xmatrix(b, ps[-1], uo, vo)
+    # both sides stop within tol of bistochastic: entries agree to a few tol
+    assert np.all(np.abs(xg - xo) <= 8e-6 * np.maximum(xo, 1.0 / max(n, 1)) + 1e-9), np.max(np.abs(xg - xo))
+    assert fp64_sum_err(b, ps[-1], u, v) < STEP_SUM_BOUND
+
+
+def test_c1_schedule_error_does_not_grow_with_p(ctx):
+    """n = 256, int32 weights in [1, 1000], p = 1, ..., 256: the FP64-recomputed sums of the
+    step path stay within a p-independent bound, and its u_i + v_j match the oracle's."""
+    w, ps = W.c1()
+    d = api.to_device(w)
+    b = oracle.log_weights(w.astype(np.int64))
+    u, v, info = api.sa_scale(ctx, d, ps, 1e-6, 20000, kernel="step")
+    assert info["status"] == 0 and info["residual"] <= 1e-6, info
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    err = fp64_sum_err(b, ps[-1], u, v)
+    assert err < STEP_SUM_BOUND, err
+    er, ec = api.sa_verify(ctx, d, ps[-1], torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda())
+    assert abs(max(er, ec) - err) < 1e-9
+    uo, vo, swo, rso, sto = oracle.sinkhorn(b, ps, 1e-6, 20000)
+    xo = oracle.xmatrix(b, ps[-1], uo, vo)
+    big = xo > 1e-3
+    s_g = (u[:, None] + v[None, :])[big]
+    s_o = (uo[:, None] + vo[None, :])[big]
+    # x = exp(p b - u - v): agreement of x within a few tol means u + v within a few tol
+    assert np.max(np.abs(s_g - s_o)) < 1e-4
+
+
+def test_planted_high_p_sums(ctx):
+    """Planted n = 512 int16 instance up to p = 512: the step path's FP64 sums stay within
+    the p-independent bound (the single-read path's would be about 1.3e-7 * p)."""
+    w, pi, _ = W.planted(512, W.BASE_SEED + 40)
+    ps = [2.0 ** k for k in range(10)]
+    d = api.to_device(w)
+    u, v, info = api.sa_scale(ctx, d, ps, 1e-6, 5000, kernel="step")
+    assert info["status"] in (0, -4), info
+    b = oracle.log_weights(w.astype(np.int64))
+    err = fp64_sum_err(b, ps[-1], u.cpu().numpy(), v.cpu().numpy())
+    assert err < max(STEP_SUM_BOUND, 2 * info["residual"] + 1e-6), (err, info["residual"])
+
+
+def test_step_and_fused_agree_at_low_p(ctx):
+    w = W.uniform(512, 1, 1000, 77, dtype=np.int16)
+    ps = [1.0, 2.0, 4.0, 8.0]
+    d = api.to_device(w)
+    us, vs, _ = api.sa_scale(ctx, d, ps, 1e-6, kernel="step")
+    uf, vf, _ = api.sa_scale(ctx, d, ps, 1e-6, kernel="fused")
+    b = oracle.log_weights(w.astype(np.int64))
+    xs = oracle.xmatrix(b, 8.0, us.cpu().numpy(), vs.cpu().numpy())
+    xf = oracle.xmatrix(b, 8.0, uf.cpu().numpy(), vf.cpu().numpy())
+    assert np.max(np.abs(xs - xf)) < 2e-5
+
+
+def test_resume_equals_full_run(ctx):
+    w = W.uniform(400, 1, 1000, 80, dtype=np.int16)
+    ps = [1.0, 2.0, 4.0, 8.0, 16.0]
+    d = api.to_device(w)
+    u1, v1, _ = api.sa_scale(ctx, d, ps, 1e-6, kernel="step")
+    u2, v2, _ = api.sa_scale(ctx, d, ps[:3], 1e-6, kernel="step")
+    u3, v3, info = api.sa_scale(ctx, d, ps, 1e-6, resume_from=3, u=u2, v=v2, kernel="step")
+    assert info["steps_done"] == 2 and info["kernel_used"] == 3
+    b = oracle.log_weights(w.astype(np.int64))
+    x1 = oracle.xmatrix(b, 16.0, u1.cpu().numpy(), v1.cpu().numpy())
+    x3 = oracle.xmatrix(b, 16.0, u3.cpu().numpy(), v3.cpu().numpy())
+    assert np.max(np.abs(x1 - x3)) < 2e-5
+
+
+def test_auto_picks_step_for_mixed(ctx):
+    w = W.uniform(300, 1, 1000, 83, dtype=np.int16)
+    d = api.to_device(w)
+    _, _, info = api.sa_scale(ctx, d, [1.0, 2.0], 1e-6)
+    assert info["kernel_used"] == 3
+    _, _, info = api.sa_scale(ctx, d, [1.0, 2.0], 1e-6, prec="fp32")
+    assert info["kernel_used"] in (1, 2)
+
+
+def test_zero_row_is_nonfinite(ctx):
+    w = W.uniform(256, 1, 1000, 81, dtype=np.int16)
+    w[17, :] = 0
+    d = api.to_device(w)
+    with pytest.raises(api.SaError) as e:
+        api.sa_scale(ctx, d, [1.0, 2.0], 1e-6, 50, kernel="step")
+    assert e.value.status == -6
+    # the context stays usable
+    w2 = W.uniform(256, 1, 1000, 84, dtype=np.int16)
+    _, _, info = api.sa_scale(ctx, api.to_device(w2), [1.0, 2.0], 1e-6, kernel="step")
+    assert info["status"] == 0
+
+
+def test_largest_supported_width(ctx):
+    """n = 12288 (six chunks of four columns per thread, the widest configuration): FP64
+    sums by the library's own verification, the property that holds at any size; one
+    column more is rejected."""
+    n = 12288
+    w = W.uniform(n, 1, 1000, 85, dtype=np.int16)
+    d = api.to_device(w)
+    u, v, info = api.sa_scale(ctx, d, [1.0, 2.0], 1e-6, 2000, kernel="step")
+    assert info["status"] == 0 and info["kernel_used"] == 3, info
+    er, ec = api.sa_verify(ctx, d, 2.0, u, v)
+    assert max(er, ec) < STEP_SUM_BOUND, (er, ec)
+    with pytest.raises(api.SaError):
+        api.sa_scale(ctx, api.to_device(W.uniform(12292, 1, 10, 86, dtype=np.int16)), [1.0], 1e-6, 10,
+                     kernel="step")
