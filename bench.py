@@ -45,29 +45,31 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-# DRAM bytes per sweep of the fused kernel (dram__bytes.sum from one ncu capture of the
-# p = 1, 2 case of the planted n=8192 int16 instance, per sweep), valid only for the kernel
-# source it was taken on: any change to the kernel makes the figure unknown (null).
-TRAFFIC_SOURCE = "ncu capture, planted n=8192 int16, p=1,2 (6 sweeps), scaled per sweep"
-_TRAFFIC = {(8192, 2): 146.6e6}
-_TRAFFIC_SRC_SHA256 = {
-    "paper_1104_3830_gb300/csrc/sweep_fused.cu": "d1dcdbec1f63cfa05cc957fb78fc37e575de7385961ea5596cdca59bd7eef491",
-    "paper_1104_3830_gb300/csrc/common.cuh": "e16bf96e14128dd20b644d1aca4ec0085d06a37a1d9f040b585c32c72d919518",
+# DRAM bytes per sweep (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture,
+# divided by the sweeps of the captured launch), valid only for the kernel source the
+# capture was taken on: after any change to these files the figure is unknown (null).
+_TRAFFIC = {
+    # step kernel: planted n=8192 int16, p=256 from a cold start, 200 sweeps + 1 evaluation of K
+    (3, 8192, 2): (55.159e9 / 200, "ncu capture, planted n=8192 int16, p=256, 200 sweeps (one launch)",
+                   {"paper_1104_3830_gb300/csrc/sweep_step.cu":
+                    "3fe7148797c47861dcc7c301468f1403e404f6aba7f238e973c4eedcdd7f097f",
+                    "paper_1104_3830_gb300/csrc/common.cuh":
+                    "79cb5c1e43464590274462aa3183e66801bebb3f3d089a1451133303777195fd"}),
 }
 
 
-KERNEL_NAMES = {1: "fused_kernel (single-read persistent sweep, SFU exp2/log2 per element)",
-                2: "row_lse_kernel + col_partial_kernel (plain sweep, host loop)",
-                3: "step_kernel (persistent sweep over the per-step FP32 matrix)"}
-
-
-def fused_traffic_per_sweep(n, wbytes):
+def measured_traffic(kernel_used, n, wbytes):
+    """(bytes per sweep, source) if a capture of this kernel source and size exists."""
     import hashlib
-    for rel, want in _TRAFFIC_SRC_SHA256.items():
+    ent = _TRAFFIC.get((kernel_used, n, wbytes))
+    if ent is None:
+        return None, None
+    per_sweep, source, files = ent
+    for rel, want in files.items():
         with open(os.path.join(ROOT, rel), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != want:
-                return None
-    return _TRAFFIC.get((n, wbytes))
+                return None, None
+    return per_sweep, source
 
 
 def workload(name):
@@ -87,6 +89,10 @@ def workload(name):
     if name == "profile8192":
         w, ps, pi, _ = W.c2()
         return w, ps[:2], {"workload": "planted n=8192 int16, p=1,2 only (profiling case)"}
+    if name == "profile8192p256":
+        w, ps, pi, _ = W.c2()
+        return w, [256.0], {"workload": "planted n=8192 int16, p=256 from a cold start (profiling case; "
+                                        "use --max-sweeps to fix the sweep count)"}
     if name == "small":
         w = W.uniform(2048, 1, 10000, 5, dtype=np.int16)
         return w, [2.0 ** k for k in range(8)], {"workload": "uniform n=2048 int16 (profiling case)"}
@@ -461,11 +467,10 @@ def main():
     alg_bytes = sweeps_per_step * n * n * w.dtype.itemsize
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
     read_per_sweep = (n * ((n + 3) // 4 * 4) * 4) if used == 3 else (n * n * w.dtype.itemsize * (2 if used == 2 else 1))
-    traffic = fused_traffic_per_sweep(n, w.dtype.itemsize) if used == 1 else None
+    traffic, tsrc = measured_traffic(used, n, w.dtype.itemsize)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic * sweeps_per_step if traffic else None,
-                "traffic_per_sweep": traffic, "traffic_source": TRAFFIC_SOURCE if traffic else
-                "none for this kernel source or size",
+                "traffic_per_sweep": traffic, "traffic_source": tsrc or "none for this kernel source or size",
                 "kernel": KERNEL_NAMES.get(used, "?"),
                 "bytes_read_per_sweep": read_per_sweep,
                 "frac_of_bytes_read": read_per_sweep * sweeps_per_step / (kernel_ms / 1e3) / 1e9 / peak,

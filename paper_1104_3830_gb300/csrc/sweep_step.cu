@@ -28,6 +28,10 @@
 #include "common.cuh"
 #include "sa_internal.h"
 
+#ifndef SA_STEP_STAMP
+#define SA_STEP_STAMP(slot)   // phase timing hook (no-op in the library build)
+#endif
+
 namespace sa {
 
 namespace {
@@ -328,6 +332,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
         float resid = INFINITY;
         bool done = false;
         while (!done) {
+            SA_STEP_STAMP(0);
 #pragma unroll
             for (int m = 0; m < M; ++m) S[m] = 0.0f;
             // ---------------- row pass ----------------
@@ -425,6 +430,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 if (!consume(g)) break;
             }
             __syncthreads();
+            SA_STEP_STAMP(1);
             if (s_flag) { drain(); return; }
             it += (uint32_t)nrows;
             gbase += (uint32_t)nst;
@@ -438,6 +444,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
             }
             ++sweeps;
             if (!gsync()) { drain(); return; }
+            SA_STEP_STAMP(2);
             // ---------------- column finalisation of columns [c0, c1) ----------------
             float* rmax_word = A.rmax + ((sweeps + rphase) & 1);
             float rmax = 0.0f;
@@ -485,6 +492,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 if (lane == 0 && rmax > 0.0f) atomicMax((unsigned*)rmax_word, __float_as_uint(rmax));
             }
             if (!gsync()) { drain(); return; }
+            SA_STEP_STAMP(3);
             // ---------------- decision (identical in every block) ----------------
             if (tid == 0) {
                 s_res = __uint_as_float(ld_acquire((const unsigned*)rmax_word));
@@ -500,6 +508,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                     for (int e = 0; e < 4; ++e)
                         cf[4 * kk + e] = e < nval[kk] ? __ldcg(A.Cf + cidx[kk] * 4 + e) : 0.0f;
             }
+            SA_STEP_STAMP(4);
         }
         rphase += sweeps;
         for (int q = tid; q < nrows; q += NT) A.U[r0 + q] = crow[q] + log2((double)srow[q]);
