@@ -108,6 +108,10 @@ typedef struct {
     int32_t kernel_used;      /* sa_kernel actually used */
     double kernel_ms;         /* device time of the sweep kernels (CUDA events on the
                                  context stream), excluding set-up and unit conversion */
+    int32_t sparse_epochs;    /* STEP: evaluations of K whose sweeps ran on the entries
+                                 >= 2^-70 of their row only (0 for the other kernels) */
+    int32_t reanchors;        /* STEP: re-evaluations of K within a p step because the
+                                 column factors spread beyond 2^20 in a sparse epoch */
 } sa_scale_info;
 
 /* Reduced instance B in CSR (Eq. matrixred).  Arrays are host memory owned by the

@@ -46,7 +46,8 @@ class sa_scale_opts(ctypes.Structure):
 class sa_scale_info(ctypes.Structure):
     _fields_ = [("sweeps_total", ctypes.c_int64), ("residual", ctypes.c_double), ("p_final", ctypes.c_double),
                 ("converged", ctypes.c_int32), ("steps_done", ctypes.c_int32), ("fallback_rows", ctypes.c_int32),
-                ("kernel_used", ctypes.c_int32), ("kernel_ms", ctypes.c_double)]
+                ("kernel_used", ctypes.c_int32), ("kernel_ms", ctypes.c_double),
+                ("sparse_epochs", ctypes.c_int32), ("reanchors", ctypes.c_int32)]
 
 
 class sa_csr(ctypes.Structure):

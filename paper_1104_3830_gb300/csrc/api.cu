@@ -196,6 +196,7 @@ sa_status sa_create(sa_ctx** ctx, int device, void* cuda_stream) {
         const int v = atoi(wv);
         if (v == 256 || v == 512) c->fused_nt = v;
     }
+    if (const char* e = getenv("SA_STEP_SPARSE")) c->step_sparse = atoi(e) != 0;
     if (!prop.cooperativeLaunch) { delete c; set_error("device lacks cooperative launch"); return SA_E_UNSUPPORTED; }
     *ctx = c;
     return SA_OK;

@@ -61,6 +61,7 @@ struct sa_ctx {
     int max_grid = 0;        // cap on the fused kernel's grid (0: all SMs); set by the server
     int fused_nt = 512;      // threads per block of the fused kernel when 512 < chunks <= 1024
                              // (256 or 512; SA_FUSED_NT in the environment overrides)
+    int step_sparse = 0;     // step kernel: allow sparse epochs (SA_STEP_SPARSE=1 enables)
     sa::Workspace ws;        // scratch for sweeps, prune, certify
     sa::Workspace input;     // device copy of host inputs (sa_assign_host)
     sa::PinnedBuf pinned;    // staging for small device->host results

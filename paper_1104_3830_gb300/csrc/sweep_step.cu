@@ -36,7 +36,8 @@ namespace sa {
 
 namespace {
 
-constexpr int kStepNred = 4;   // row-sum publication buffers
+constexpr int kStepNred = 4;      // row-sum publication buffers
+constexpr int kStepMaxRing = 16;  // ring slots at most (sparse epochs use short slots)
 
 struct StepArgs {
     const void* w;
@@ -46,7 +47,18 @@ struct StepArgs {
     float* K;              // n x ldk, FP32
     int64_t ldk;           // floats, multiple of 4
     unsigned row_bytes;    // bytes copied per K row (multiple of 16)
-    int ring;              // ring slots (>= 4)
+    int ring;              // ring slots of a dense epoch (>= 4)
+    unsigned region_bytes; // shared-memory region for the ring (and sparse c, S)
+    uint2* rec;            // (column, value bits) records of K >= theta, rec_cap_row per row
+    int64_t rec_cap_row;   // record capacity per row (even)
+    unsigned long long* stats;   // [2][4]: records, longest row, overflow (per epoch parity)
+    unsigned* crange;      // [2][2]: max and min column factor of a sweep (float bits)
+    int* counters;         // [2]: sparse epochs, re-anchors
+    int sparse_ok;         // build records and allow sparse epochs
+    unsigned sparse_row_cap;            // longest row (records) a sparse epoch's ring holds
+    unsigned long long sparse_max_total; // most records for a sparse epoch
+    float theta;           // entries of K below theta are dropped in sparse epochs
+    float reanchor_ratio;  // re-evaluate K when max c / min c exceeds this
     const double* tab;     // log2 k for k = 0..kTab-1 (tab[0] = -inf)
     const double* P;       // schedule
     int k0, n_p;
@@ -153,27 +165,30 @@ struct KahanS {
 template <int NT, int CH>
 __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     constexpr int NW = NT / 32;
-    constexpr int M = CH * 4;   // columns owned per thread
+    constexpr int M = CH * 4;   // columns owned per thread (dense mode)
     constexpr int NRED = kStepNred;
+    constexpr int MAXR = kStepMaxRing;
     constexpr int FG = NT / 64;
     static_assert(NT % 64 == 0, "layout");
     extern __shared__ __align__(128) unsigned char smem[];
-    const int RING = A.ring;
-    unsigned char* ring = smem;
-    uint64_t* mbar = (uint64_t*)(smem + (size_t)RING * A.row_bytes);   // [RING] copy arrivals
-    uint64_t* mrow = mbar + RING;                                      // [NRED] row-sum publication
-    unsigned* rel_cnt = (unsigned*)(mrow + NRED);                      // [RING]
-    unsigned* iss_cnt = rel_cnt + RING;                                // [RING]
-    // 8 (2 RING + NRED) bytes of barriers and counters end on a 16-byte boundary, so the
-    // float4-read partials come first
-    float* red = (float*)(mrow + NRED + RING);                         // [NRED][2][NW] (16-aligned)
-    double* crow = (double*)(red + NRED * 2 * NW);                     // [max_rows] row references
-    double* redp = crow + A.max_rows;                                  // [FG][64]
-    double* redd = redp + FG * 64;                                     // [NW]
-    float* srow = (float*)(redd + NW);                                 // [max_rows]
-    __shared__ int s_flag, s_ok;
+    // [region: dense ring | or sparse c, S and ring] [barriers] [scratch]
+    unsigned char* region = smem;
+    uint64_t* mbar = (uint64_t*)(smem + A.region_bytes);   // [MAXR] copy arrivals
+    uint64_t* mrow = mbar + MAXR;                           // [NRED] row-sum publication
+    unsigned* rel_cnt = (unsigned*)(mrow + NRED);           // [MAXR] warp releases per slot
+    unsigned* iss_cnt = rel_cnt + MAXR;                     // [MAXR] copies issued per slot
+    // 8 (2 MAXR + NRED) bytes of barriers and counters end on a 16-byte boundary
+    float* red = (float*)(iss_cnt + MAXR);                  // [NRED][2][NW] (16-aligned)
+    double* crow = (double*)(red + NRED * 2 * NW);          // [max_rows] row references
+    double* redp = crow + A.max_rows;                       // [FG][64]
+    double* redd = redp + FG * 64;                          // [NW]
+    float* srow = (float*)(redd + NW);                      // [max_rows] row sums
+    unsigned* rowoff = (unsigned*)(srow + A.max_rows);      // [max_rows] record offsets
+    unsigned* rowlen = rowoff + A.max_rows;                 // [max_rows] padded record counts
+    __shared__ int s_flag, s_ok, s_mode, s_reanchor;
     __shared__ float s_res;
     __shared__ double s_max;
+    __shared__ unsigned s_maxlen;
 
     const int n = A.n;
     const int G = gridDim.x;
@@ -186,38 +201,53 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     const int NC = (n + 3) / 4;
     const unsigned char* kbase = (const unsigned char*)A.K;
     const size_t kpitch = (size_t)A.ldk * sizeof(float);
+    uint2* recb = A.rec + (size_t)r0 * A.rec_cap_row;        // this block's records
+    const size_t rec_cap = (size_t)nrows * A.rec_cap_row;
+    const size_t cs_bytes = ((size_t)n * 8 + 15) & ~(size_t)15;   // sparse: c and S
+    float* c_s = (float*)region;
+    float* S_s = c_s + n;
 
     if (tid == 0) {
-        for (int s = 0; s < RING; ++s) mbar_init(&mbar[s], 1);
-        for (int s = 0; s < RING; ++s) rel_cnt[s] = iss_cnt[s] = 0;
+        for (int s = 0; s < MAXR; ++s) rel_cnt[s] = iss_cnt[s] = 0u;
         for (int s = 0; s < NRED; ++s) mbar_init(&mrow[s], NW);
         mbar_fence_init();
         s_flag = 0;
     }
     __syncthreads();
 
-    uint32_t it = 0;      // consumption index of the current sweep's first row
-    uint32_t ofs = 0;     // index u holds local row (u - ofs) % nrows
-    uint32_t gbase = 0;   // row stages completed, over all sweeps
+    // ring geometry of the current epoch (one evaluation of K and the sweeps that use it)
+    int sparse = 0;
+    int ring_n = 4;
+    unsigned slot_bytes = A.row_bytes;
+    unsigned char* sbase = region;
+    uint32_t it = 0;      // consumption index of the current sweep's first row (per epoch)
+    uint32_t gbase = 0;   // row stages completed, over the whole launch
     unsigned nbar = 0;
     int rphase = 0;
+    unsigned epoch = 0;
     auto issue_index = [&](uint32_t u) {   // one thread
-        const uint32_t slot = u % (uint32_t)RING;
-        const int q = (int)((u - ofs) % (uint32_t)nrows);
+        const uint32_t slot = u % (uint32_t)ring_n;
+        const int q = (int)(u % (uint32_t)nrows);
         iss_cnt[slot] += 1;
-        mbar_arrive_expect_tx(&mbar[slot], A.row_bytes);
-        bulk_g2s(ring + (size_t)slot * A.row_bytes, kbase + (size_t)(r0 + q) * kpitch, A.row_bytes, &mbar[slot]);
+        if (sparse) {
+            const unsigned bytes = rowlen[q] * 8u;
+            mbar_arrive_expect_tx(&mbar[slot], bytes);
+            bulk_g2s(sbase + (size_t)slot * slot_bytes, recb + rowoff[q], bytes, &mbar[slot]);
+        } else {
+            mbar_arrive_expect_tx(&mbar[slot], A.row_bytes);
+            bulk_g2s(sbase + (size_t)slot * slot_bytes, kbase + (size_t)(r0 + q) * kpitch, A.row_bytes, &mbar[slot]);
+        }
     };
     auto release_index = [&](uint32_t u) {   // lane 0 after __syncwarp
-        const uint32_t slot = u % (uint32_t)RING;
+        const uint32_t slot = u % (uint32_t)ring_n;
         const unsigned old = atom_add_acq_rel(&rel_cnt[slot], 1u);
         if ((old + 1u) % (unsigned)NW == 0u) {
             fence_proxy_async_smem();
-            issue_index(u + (uint32_t)RING);
+            issue_index(u + (uint32_t)ring_n);
         }
     };
     auto wait_copies = [&]() {   // tid 0: the last copy issued into every slot
-        for (int s = 0; s < RING; ++s) {
+        for (int s = 0; s < MAXR; ++s) {
             const unsigned k = iss_cnt[s];
             if (k > 0u && !mbar_wait(&mbar[s], (k - 1u) & 1u, A.err, kWaitTimeoutNs)) break;
         }
@@ -241,12 +271,18 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     }
     float S[M], cf[M];
 
-    // ---- K rows of this stripe for step p (V holds the step's starting column potentials) ----
+    // ---- one evaluation of this stripe's rows of K for p (V: the epoch's starting column
+    //      potentials), dense rows in global memory plus, when enabled, the entries
+    //      >= theta as (column, value) records ----
     auto prep = [&](double p) {
         const float pf = (float)p;
-        double* vsm = (double*)ring;   // the ring is idle: stage V there
+        double* vsm = (double*)region;   // the region is idle: stage V there
         for (int j = tid; j < n; j += NT) vsm[j] = A.V[j];
+        if (tid == 0) s_maxlen = 0u;
         __syncthreads();
+        unsigned* wcnt = (unsigned*)red;   // [NW] per-warp kept counts (scratch)
+        size_t roff = 0;                   // records written so far (block-relative)
+        bool overflow = false;
         for (int q = 0; q < nrows; ++q) {
             const int64_t row = r0 + q;
             // reference C ~ max_j (p log2 w - V_j), FP32 estimate (only a scale)
@@ -274,9 +310,9 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
             __syncthreads();
             const double m = s_max;
             float* krow = A.K + row * A.ldk;
+            float kvs[M];
 #pragma unroll
             for (int k = 0; k < CH; ++k) {
-                if (cidx[k] >= (int)(A.ldk / 4)) continue;
                 float kv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                 if (nval[k] > 0) {
                     int w[4];
@@ -290,225 +326,363 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                         }
                     }
                 }
-                *(float4*)(krow + cidx[k] * 4) = make_float4(kv[0], kv[1], kv[2], kv[3]);
+                if (cidx[k] < NC) *(float4*)(krow + cidx[k] * 4) = make_float4(kv[0], kv[1], kv[2], kv[3]);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) kvs[4 * k + e] = kv[e];
+            }
+            if (A.sparse_ok) {
+                // compaction of the entries >= theta: warp scan of the per-thread counts
+                unsigned c = 0;
+#pragma unroll
+                for (int x = 0; x < M; ++x) c += kvs[x] >= A.theta ? 1u : 0u;
+                unsigned incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (lane == 31) wcnt[wid] = incl;
+                __syncthreads();
+                unsigned wbase = 0, tot = 0;
+                for (int x = 0; x < NW; ++x) {
+                    const unsigned t = wcnt[x];
+                    if (x < wid) wbase += t;
+                    tot += t;
+                }
+                const unsigned padded = tot < 2u ? 2u : tot + (tot & 1u);
+                const bool fits = !overflow && roff + padded <= rec_cap;
+                if (fits) {
+                    size_t o = roff + wbase + incl - c;
+#pragma unroll
+                    for (int x = 0; x < M; ++x)
+                        if (kvs[x] >= A.theta)
+                            recb[o++] = make_uint2((unsigned)(cidx[x / 4] * 4 + (x % 4)), __float_as_uint(kvs[x]));
+                    if (tid == 0)
+                        for (unsigned e = tot; e < padded; ++e) recb[roff + e] = make_uint2(0u, 0u);
+                }
+                if (tid == 0) {
+                    rowoff[q] = (unsigned)roff;
+                    rowlen[q] = padded;
+                    if (padded > s_maxlen) s_maxlen = padded;
+                }
+                if (fits) roff += padded;
+                else overflow = true;
+                __syncthreads();   // wcnt is reused by the next row
             }
         }
-        fence_proxy_async_all();   // K rows are read back, and the V scratch overwritten, by bulk copies
+        if (A.sparse_ok && tid == 0) {
+            unsigned long long* st = A.stats + 4 * (epoch & 1u);
+            atomicAdd(st + 0, (unsigned long long)roff);
+            atomicMax(st + 1, (unsigned long long)s_maxlen);
+            if (overflow) atomicMax(st + 2, 1ull);
+        }
+        fence_proxy_async_all();   // K rows are read back, and the region overwritten, by bulk copies
         __syncthreads();
     };
 
     for (int k = A.k0; k < A.n_p; ++k) {
         const double p = A.P[k];
-        if (k > A.k0) {
-            // copies prefetched at the end of the previous step hold old K rows: let them land
-            // before the ring is reused as scratch and the rows are rewritten
+        int sweeps = 0;
+        float resid = INFINITY;
+        int step_reanchors = 0;   // after two re-anchors the step finishes dense
+        for (;;) {   // epochs of step k: one evaluation of K, then sweeps until done or re-anchor
+            // every copy of the previous epoch has landed; reset the ring
             __syncthreads();
             if (tid == 0) wait_copies();
             __syncthreads();
-        }
-        if (s_flag) { drain(); return; }
-        for (int j = c0 + tid; j < c1; j += NT) {
-            A.Vs[j] = A.V[j];
-            A.Cf[j] = 1.0f;
-        }
-        prep(p);
-        if (nrows > 0) {
-            if (k == A.k0) {
-                if (tid == 0)
-                    for (uint32_t u = 0; u < (uint32_t)RING; ++u) issue_index(u);
-            } else {
-                // the stale prefetches [it, it + RING) are skipped: every warp releases
-                // them, which refills their slots with the new rows
-                ofs += (uint32_t)RING;
-                __syncwarp();
-                if (lane == 0)
-                    for (uint32_t u = it; u < it + (uint32_t)RING; ++u) release_index(u);
-                it += (uint32_t)RING;
+            if (s_flag) { drain(); return; }
+            if (tid == 0) {
+                for (int s = 0; s < MAXR; ++s) {
+                    if (epoch > 0u) mbar_inval(&mbar[s]);   // initialised by the previous epoch
+                    mbar_init(&mbar[s], 1);
+                    rel_cnt[s] = iss_cnt[s] = 0u;
+                }
+                mbar_fence_init();
             }
-        }
-#pragma unroll
-        for (int m = 0; m < M; ++m) cf[m] = (m % 4) < nval[m / 4] ? 1.0f : 0.0f;
-        int sweeps = 0;
-        float resid = INFINITY;
-        bool done = false;
-        while (!done) {
-            SA_STEP_STAMP(0);
-#pragma unroll
-            for (int m = 0; m < M; ++m) S[m] = 0.0f;
-            // ---------------- row pass ----------------
-            // stage g = local rows 2g, 2g+1.  produce(g): partial row sums, published on
-            // mrow[g % NRED]; consume(g): wait for every warp's partials, accumulate the
-            // normalised rows into the column sums, release the slots.
-            const int nst = (nrows + 1) / 2;
-            auto row_partial = [&](const unsigned char* rowp) -> float {
-                float a0 = 0.0f, a1 = 0.0f;
-#pragma unroll
-                for (int kk = 0; kk < CH; ++kk) {
-                    if (nval[kk] == 0) continue;   // chunk beyond the row: not in the slot
-                    const float4 kv = *(const float4*)(rowp + (size_t)cidx[kk] * 16);
-                    a0 = fmaf(kv.x, cf[4 * kk], a0);
-                    a1 = fmaf(kv.y, cf[4 * kk + 1], a1);
-                    a0 = fmaf(kv.z, cf[4 * kk + 2], a0);
-                    a1 = fmaf(kv.w, cf[4 * kk + 3], a1);
-                }
-                return a0 + a1;
-            };
-            auto produce = [&](int g) {
-                const int q0 = 2 * g;
-                const bool two = q0 + 1 < nrows;
-                const uint32_t u0 = it + q0;
-                bool ok = mbar_wait(&mbar[u0 % RING], (u0 / RING) & 1u, A.err, kWaitTimeoutNs);
-                if (two) ok = mbar_wait(&mbar[(u0 + 1) % RING], ((u0 + 1) / RING) & 1u, A.err, kWaitTimeoutNs) && ok;
-                if (!ok) s_flag = 1;
-                const float sp0 = row_partial(ring + (size_t)(u0 % RING) * A.row_bytes);
-                const float sp1 = two ? row_partial(ring + (size_t)((u0 + 1) % RING) * A.row_bytes) : 0.0f;
-                const float w0 = warp_sum(sp0);
-                const float w1 = warp_sum(sp1);
-                if (lane == 0) {
-                    const uint32_t gs = gbase + g;
-                    red[((gs % NRED) * 2) * NW + wid] = w0;
-                    red[((gs % NRED) * 2 + 1) * NW + wid] = w1;
-                    mbar_arrive(&mrow[gs % NRED]);
-                }
-            };
-            auto consume = [&](int g) -> bool {
-                const int q0 = 2 * g;
-                const bool two = q0 + 1 < nrows;
-                const uint32_t u0 = it + q0;
-                const uint32_t gs = gbase + g;
-                if (!mbar_wait(&mrow[gs % NRED], (gs / NRED) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
-                if (s_flag) return false;
-                float ss[2];
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const float4* rv = (const float4*)(red + ((gs % NRED) * 2 + r) * NW);
-                    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-#pragma unroll
-                    for (int x = 0; x < NW / 4; ++x) {
-                        const float4 q4 = rv[x];
-                        a0 += q4.x;
-                        a1 += q4.y;
-                        a2 += q4.z;
-                        a3 += q4.w;
+            for (int j = c0 + tid; j < c1; j += NT) {
+                A.Vs[j] = A.V[j];
+                A.Cf[j] = 1.0f;
+            }
+            prep(p);
+            if (!gsync()) { drain(); return; }
+            // mode of this epoch, identical in every block
+            if (tid == 0) {
+                int sp = 0;
+                if (A.sparse_ok) {
+                    const volatile unsigned long long* st = A.stats + 4 * (epoch & 1u);
+                    sp = st[2] == 0ull && st[0] <= A.sparse_max_total && st[1] <= (unsigned long long)A.sparse_row_cap &&
+                         step_reanchors < 2;
+                    if (b == 0) {
+                        unsigned long long* nx = A.stats + 4 * ((epoch + 1u) & 1u);
+                        nx[0] = nx[1] = nx[2] = 0ull;
                     }
-                    ss[r] = (a0 + a1) + (a2 + a3);
+                    if (b == 0 && sp) atomicAdd(A.counters + 0, 1);
                 }
-                if (!(ss[0] >= 0x1p-120f && ss[0] <= 0x1p120f) || (two && !(ss[1] >= 0x1p-120f && ss[1] <= 0x1p120f))) {
-                    if (tid == 0) atomicCAS(A.err, 0, kErrNonfinite);
-                    s_flag = 1;
-                    return false;
+                s_mode = sp;
+            }
+            __syncthreads();
+            sparse = s_mode;
+            ++epoch;
+            it = 0;
+            if (sparse) {
+                slot_bytes = s_maxlen * 8u;
+                sbase = region + cs_bytes;
+                ring_n = (int)min((size_t)MAXR, ((size_t)A.region_bytes - cs_bytes) / slot_bytes);
+                for (int j = tid; j < n; j += NT) {
+                    c_s[j] = 1.0f;
+                    S_s[j] = 0.0f;
                 }
-                if (tid == 0) {
-                    srow[q0] = ss[0];
-                    if (two) srow[q0 + 1] = ss[1];
-                }
+            } else {
+                slot_bytes = A.row_bytes;
+                sbase = region;
+                ring_n = A.ring;
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    if (r == 1 && !two) break;
-                    const float inv = rcp_approx(ss[r]);
-                    const unsigned char* rowp = ring + (size_t)((u0 + r) % RING) * A.row_bytes;
+                for (int m = 0; m < M; ++m) cf[m] = (m % 4) < nval[m / 4] ? 1.0f : 0.0f;
+            }
+            __syncthreads();
+            if (tid == 0 && nrows > 0)
+                for (uint32_t u = 0; u < (uint32_t)ring_n; ++u) issue_index(u);
+            bool done = false, reanchor = false;
+            while (!done && !reanchor) {
+                SA_STEP_STAMP(0);
+#pragma unroll
+                for (int m = 0; m < M; ++m) S[m] = 0.0f;
+                // ---------------- row pass ----------------
+                // stage g = local rows 2g, 2g+1.  produce(g): partial row sums, published on
+                // mrow[g % NRED]; consume(g): wait for every warp's partials, accumulate the
+                // normalised rows into the column sums, release the slots.
+                const int nst = (nrows + 1) / 2;
+                auto slot_of = [&](uint32_t u) -> const unsigned char* {
+                    return sbase + (size_t)(u % (uint32_t)ring_n) * slot_bytes;
+                };
+                auto row_partial = [&](uint32_t u) -> float {
+                    const unsigned char* rowp = slot_of(u);
+                    float a0 = 0.0f, a1 = 0.0f;
+                    if (sparse) {
+                        const uint2* rp = (const uint2*)rowp;
+                        const unsigned len = rowlen[u % (uint32_t)nrows];
+                        for (unsigned e = tid; e < len; e += NT) {
+                            const uint2 r = rp[e];
+                            a0 = fmaf(__uint_as_float(r.y), c_s[r.x], a0);
+                        }
+                        return a0;
+                    }
 #pragma unroll
                     for (int kk = 0; kk < CH; ++kk) {
-                        if (nval[kk] == 0) continue;
+                        if (nval[kk] == 0) continue;   // chunk beyond the row: not in the slot
                         const float4 kv = *(const float4*)(rowp + (size_t)cidx[kk] * 16);
-                        S[4 * kk] = fmaf(kv.x, inv, S[4 * kk]);
-                        S[4 * kk + 1] = fmaf(kv.y, inv, S[4 * kk + 1]);
-                        S[4 * kk + 2] = fmaf(kv.z, inv, S[4 * kk + 2]);
-                        S[4 * kk + 3] = fmaf(kv.w, inv, S[4 * kk + 3]);
+                        a0 = fmaf(kv.x, cf[4 * kk], a0);
+                        a1 = fmaf(kv.y, cf[4 * kk + 1], a1);
+                        a0 = fmaf(kv.z, cf[4 * kk + 2], a0);
+                        a1 = fmaf(kv.w, cf[4 * kk + 3], a1);
                     }
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    release_index(u0);
-                    if (two) release_index(u0 + 1);
-                }
-                return true;
-            };
-            if (nst > 0) produce(0);
-            for (int g = 0; g < nst; ++g) {
-                if (g + 1 < nst) produce(g + 1);
-                if (!consume(g)) break;
-            }
-            __syncthreads();
-            SA_STEP_STAMP(1);
-            if (s_flag) { drain(); return; }
-            it += (uint32_t)nrows;
-            gbase += (uint32_t)nst;
-            float* pb = A.part + (size_t)b * A.npad;
+                    return a0 + a1;
+                };
+                auto produce = [&](int g) {
+                    const int q0 = 2 * g;
+                    const bool two = q0 + 1 < nrows;
+                    const uint32_t u0 = it + q0;
+                    const uint32_t rn = (uint32_t)ring_n;
+                    bool ok = mbar_wait(&mbar[u0 % rn], (u0 / rn) & 1u, A.err, kWaitTimeoutNs);
+                    if (two) ok = mbar_wait(&mbar[(u0 + 1) % rn], ((u0 + 1) / rn) & 1u, A.err, kWaitTimeoutNs) && ok;
+                    if (!ok) s_flag = 1;
+                    const float sp0 = row_partial(u0);
+                    const float sp1 = two ? row_partial(u0 + 1) : 0.0f;
+                    const float w0 = warp_sum(sp0);
+                    const float w1 = warp_sum(sp1);
+                    if (lane == 0) {
+                        const uint32_t gs = gbase + g;
+                        red[((gs % NRED) * 2) * NW + wid] = w0;
+                        red[((gs % NRED) * 2 + 1) * NW + wid] = w1;
+                        mbar_arrive(&mrow[gs % NRED]);
+                    }
+                };
+                auto consume = [&](int g) -> bool {
+                    const int q0 = 2 * g;
+                    const bool two = q0 + 1 < nrows;
+                    const uint32_t u0 = it + q0;
+                    const uint32_t gs = gbase + g;
+                    if (!mbar_wait(&mrow[gs % NRED], (gs / NRED) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
+                    if (s_flag) return false;
+                    float ss[2];
 #pragma unroll
-            for (int kk = 0; kk < CH; ++kk) {
-                if (nval[kk] > 0)
-                    *(float4*)(pb + (size_t)cidx[kk] * 4) =
-                        make_float4(S[4 * kk] * cf[4 * kk], S[4 * kk + 1] * cf[4 * kk + 1],
-                                    S[4 * kk + 2] * cf[4 * kk + 2], S[4 * kk + 3] * cf[4 * kk + 3]);
-            }
-            ++sweeps;
-            if (!gsync()) { drain(); return; }
-            SA_STEP_STAMP(2);
-            // ---------------- column finalisation of columns [c0, c1) ----------------
-            float* rmax_word = A.rmax + ((sweeps + rphase) & 1);
-            float rmax = 0.0f;
-            for (int cb = c0; cb < c1; cb += 64) {
-                const int j = cb + (tid & 63);
-                const int grp = tid >> 6;
-                KahanS acc;
-                if (j < c1) {
-                    const float* pj = A.part + j;
-                    for (int g0 = grp; g0 < G; g0 += FG * 16) {
-                        float a[16];
+                    for (int r = 0; r < 2; ++r) {
+                        const float4* rv = (const float4*)(red + ((gs % NRED) * 2 + r) * NW);
+                        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
 #pragma unroll
-                        for (int x = 0; x < 16; ++x) {
-                            const int g = g0 + x * FG;
-                            a[x] = g < G ? __ldcg(pj + (size_t)g * A.npad) : 0.0f;
+                        for (int x = 0; x < NW / 4; ++x) {
+                            const float4 q4 = rv[x];
+                            a0 += q4.x;
+                            a1 += q4.y;
+                            a2 += q4.z;
+                            a3 += q4.w;
+                        }
+                        ss[r] = (a0 + a1) + (a2 + a3);
+                    }
+                    if (!(ss[0] >= 0x1p-120f && ss[0] <= 0x1p120f) || (two && !(ss[1] >= 0x1p-120f && ss[1] <= 0x1p120f))) {
+                        if (tid == 0) atomicCAS(A.err, 0, kErrNonfinite);
+                        s_flag = 1;
+                        return false;
+                    }
+                    if (tid == 0) {
+                        srow[q0] = ss[0];
+                        if (two) srow[q0 + 1] = ss[1];
+                    }
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        if (r == 1 && !two) break;
+                        const float inv = rcp_approx(ss[r]);
+                        const unsigned char* rowp = slot_of(u0 + r);
+                        if (sparse) {
+                            const uint2* rp = (const uint2*)rowp;
+                            const unsigned len = rowlen[q0 + r];
+                            for (unsigned e = tid; e < len; e += NT) {
+                                const uint2 rr = rp[e];
+                                atomicAdd(&S_s[rr.x], __uint_as_float(rr.y) * inv);
+                            }
+                            continue;
                         }
 #pragma unroll
-                        for (int x = 0; x < 16; ++x) acc.add(a[x]);
+                        for (int kk = 0; kk < CH; ++kk) {
+                            if (nval[kk] == 0) continue;
+                            const float4 kv = *(const float4*)(rowp + (size_t)cidx[kk] * 16);
+                            S[4 * kk] = fmaf(kv.x, inv, S[4 * kk]);
+                            S[4 * kk + 1] = fmaf(kv.y, inv, S[4 * kk + 1]);
+                            S[4 * kk + 2] = fmaf(kv.z, inv, S[4 * kk + 2]);
+                            S[4 * kk + 3] = fmaf(kv.w, inv, S[4 * kk + 3]);
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        release_index(u0);
+                        if (two) release_index(u0 + 1);
+                    }
+                    return true;
+                };
+                if (nst > 0) produce(0);
+                for (int g = 0; g < nst; ++g) {
+                    if (g + 1 < nst) produce(g + 1);
+                    if (!consume(g)) break;
+                }
+                __syncthreads();
+                SA_STEP_STAMP(1);
+                if (s_flag) { drain(); return; }
+                it += (uint32_t)nrows;
+                gbase += (uint32_t)nst;
+                float* pb = A.part + (size_t)b * A.npad;
+                if (sparse) {
+                    for (int j = tid; j < n; j += NT) {
+                        pb[j] = S_s[j] * c_s[j];
+                        S_s[j] = 0.0f;
+                    }
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < CH; ++kk) {
+                        if (nval[kk] > 0)
+                            *(float4*)(pb + (size_t)cidx[kk] * 4) =
+                                make_float4(S[4 * kk] * cf[4 * kk], S[4 * kk + 1] * cf[4 * kk + 1],
+                                            S[4 * kk + 2] * cf[4 * kk + 2], S[4 * kk + 3] * cf[4 * kk + 3]);
                     }
                 }
-                redp[grp * 64 + (tid & 63)] = (double)acc.s - (double)acc.c;
-                __syncthreads();
-                if (tid < 64 && j < c1) {
-                    double Sj = 0.0;
+                ++sweeps;
+                if (!gsync()) { drain(); return; }
+                SA_STEP_STAMP(2);
+                // ---------------- column finalisation of columns [c0, c1) ----------------
+                const int par = (sweeps + rphase) & 1;
+                float* rmax_word = A.rmax + par;
+                float rmax = 0.0f, cmx = 0.0f, cmn = INFINITY;
+                for (int cb = c0; cb < c1; cb += 64) {
+                    const int j = cb + (tid & 63);
+                    const int grp = tid >> 6;
+                    KahanS acc;
+                    if (j < c1) {
+                        const float* pj = A.part + j;
+                        for (int g0 = grp; g0 < G; g0 += FG * 16) {
+                            float a[16];
 #pragma unroll
-                    for (int x = 0; x < FG; ++x) Sj += redp[x * 64 + tid];
-                    if (!(Sj > 0.0) || !isfinite(Sj)) atomicCAS(A.err, 0, kErrNonfinite);
-                    const double d = Sj - 1.0;
-                    rmax = fmaxf(rmax, (float)fabs(d));
-                    double lg;
-                    if (fabs(d) < 1e-3) {
-                        // log2(1 + d) by its series in FP64 (|d| < 1e-3: five terms reach 1e-17)
-                        lg = d * (1.0 + d * (-0.5 + d * (1.0 / 3.0 + d * (-0.25 + d * 0.2)))) * kLog2e;
+                            for (int x = 0; x < 16; ++x) {
+                                const int g = g0 + x * FG;
+                                a[x] = g < G ? __ldcg(pj + (size_t)g * A.npad) : 0.0f;
+                            }
+#pragma unroll
+                            for (int x = 0; x < 16; ++x) acc.add(a[x]);
+                        }
+                    }
+                    redp[grp * 64 + (tid & 63)] = (double)acc.s - (double)acc.c;
+                    __syncthreads();
+                    if (tid < 64 && j < c1) {
+                        double Sj = 0.0;
+#pragma unroll
+                        for (int x = 0; x < FG; ++x) Sj += redp[x * 64 + tid];
+                        if (!(Sj > 0.0) || !isfinite(Sj)) atomicCAS(A.err, 0, kErrNonfinite);
+                        const double d = Sj - 1.0;
+                        rmax = fmaxf(rmax, (float)fabs(d));
+                        double lg;
+                        if (fabs(d) < 1e-3) {
+                            // log2(1 + d) by its series in FP64 (|d| < 1e-3: five terms reach 1e-17)
+                            lg = d * (1.0 + d * (-0.5 + d * (1.0 / 3.0 + d * (-0.25 + d * 0.2)))) * kLog2e;
+                        } else {
+                            lg = log2(Sj);
+                        }
+                        const double v = A.V[j] + lg;
+                        A.V[j] = v;
+                        const float cnew = ex2_approx((float)(A.Vs[j] - v));
+                        A.Cf[j] = cnew;
+                        cmx = fmaxf(cmx, cnew);
+                        cmn = fminf(cmn, cnew);
+                    }
+                    __syncthreads();
+                }
+                if (wid < 2) {
+                    rmax = warp_max(rmax);
+                    if (lane == 0 && rmax > 0.0f) atomicMax((unsigned*)rmax_word, __float_as_uint(rmax));
+                    if (sparse) {
+                        cmx = warp_max(cmx);
+                        cmn = -warp_max(-cmn);
+                        // positive floats order like their bit patterns
+                        if (lane == 0 && cmx > 0.0f) atomicMax(A.crange + 2 * par, __float_as_uint(cmx));
+                        if (lane == 0 && cmn < INFINITY) atomicMin(A.crange + 2 * par + 1, __float_as_uint(cmn));
+                    }
+                }
+                if (!gsync()) { drain(); return; }
+                SA_STEP_STAMP(3);
+                // ---------------- decision (identical in every block) ----------------
+                if (tid == 0) {
+                    s_res = __uint_as_float(ld_acquire((const unsigned*)rmax_word));
+                    int ra = 0;
+                    if (sparse) {
+                        const float hi = __uint_as_float(ld_acquire(A.crange + 2 * par));
+                        const float lo = __uint_as_float(ld_acquire(A.crange + 2 * par + 1));
+                        ra = !(hi <= A.reanchor_ratio * lo);
+                    }
+                    s_reanchor = ra;
+                    if (b == 0) {
+                        A.rmax[par ^ 1] = 0.0f;
+                        A.crange[2 * (par ^ 1)] = 0u;
+                        A.crange[2 * (par ^ 1) + 1] = 0x7f800000u;
+                    }
+                }
+                __syncthreads();
+                resid = s_res;
+                done = (resid <= A.tol) || (sweeps >= A.max_sweeps);
+                reanchor = !done && s_reanchor;
+                if (!done && !reanchor) {
+                    if (sparse) {
+                        for (int j = tid; j < n; j += NT) c_s[j] = __ldcg(A.Cf + j);
+                        __syncthreads();
                     } else {
-                        lg = log2(Sj);
+#pragma unroll
+                        for (int kk = 0; kk < CH; ++kk)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                cf[4 * kk + e] = e < nval[kk] ? __ldcg(A.Cf + cidx[kk] * 4 + e) : 0.0f;
                     }
-                    const double v = A.V[j] + lg;
-                    A.V[j] = v;
-                    A.Cf[j] = ex2_approx((float)(A.Vs[j] - v));
                 }
-                __syncthreads();
+                SA_STEP_STAMP(4);
             }
-            if (wid < 2) {
-                rmax = warp_max(rmax);
-                if (lane == 0 && rmax > 0.0f) atomicMax((unsigned*)rmax_word, __float_as_uint(rmax));
-            }
-            if (!gsync()) { drain(); return; }
-            SA_STEP_STAMP(3);
-            // ---------------- decision (identical in every block) ----------------
-            if (tid == 0) {
-                s_res = __uint_as_float(ld_acquire((const unsigned*)rmax_word));
-                if (b == 0) A.rmax[((sweeps + rphase) + 1) & 1] = 0.0f;
-            }
-            __syncthreads();
-            resid = s_res;
-            done = (resid <= A.tol) || (sweeps >= A.max_sweeps);
-            if (!done) {
-#pragma unroll
-                for (int kk = 0; kk < CH; ++kk)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        cf[4 * kk + e] = e < nval[kk] ? __ldcg(A.Cf + cidx[kk] * 4 + e) : 0.0f;
-            }
-            SA_STEP_STAMP(4);
+            if (!reanchor) break;
+            ++step_reanchors;
+            if (b == 0 && tid == 0) atomicAdd(A.counters + 1, 1);
         }
         rphase += sweeps;
         for (int q = tid; q < nrows; q += NT) A.U[r0 + q] = crow[q] + log2((double)srow[q]);
@@ -529,11 +703,11 @@ struct StepCfg {
     int nt, ch, ring;
 };
 
-size_t step_smem_bytes(int nt, int ring, unsigned row_bytes, int max_rows) {
+size_t step_smem_bytes(int nt, size_t region_bytes, int max_rows) {
     const int nw = nt / 32;
     const int fg = nt / 64;
-    return (size_t)ring * row_bytes + 8 * (size_t)(ring + kStepNred + ring) +
-           8 * (size_t)(max_rows + fg * 64 + nw) + 4 * (size_t)(kStepNred * 2 * nw + max_rows) + 1024;
+    return region_bytes + 8 * (size_t)(2 * kStepMaxRing + kStepNred) + 4 * (size_t)(kStepNred * 2 * nw) +
+           8 * (size_t)(max_rows + fg * 64 + nw) + 4 * (size_t)max_rows + 8 * (size_t)max_rows + 1024;
 }
 
 int step_max_rows(const sa_ctx* ctx, int n) {
@@ -557,7 +731,7 @@ StepCfg pick_step(const sa_ctx* ctx, int n) {
     // the ring doubles as scratch for V (8 n bytes) during the per-step evaluation
     for (int ring = 8; ring >= 4; --ring) {
         if ((size_t)ring * row_bytes < (size_t)n * 8) break;
-        if (step_smem_bytes(c.nt, ring, row_bytes, max_rows) <= ctx->smem_optin) {
+        if (step_smem_bytes(c.nt, (size_t)ring * row_bytes, max_rows) <= ctx->smem_optin) {
             c.ring = ring;
             return c;
         }
@@ -601,13 +775,17 @@ bool step_supported(const sa_ctx* ctx, const sa_matrix* a) {
     return pick_step(ctx, a->n).nt > 0;
 }
 
+// records per row reserved for sparse epochs: a quarter of the row (denser steps run dense)
+int64_t step_rec_cap_row(int n) { return (int64_t)align_up((size_t)n / 4 + 2, 2); }
+
 size_t step_workspace_bytes(const sa_ctx* ctx, const sa_matrix* a, int n_p) {
     const int n = a->n;
     const size_t ldk = align_up((size_t)n, 4);
     const int G_max = ctx->num_sms * 2;
     const size_t npad = align_up((size_t)n, 32);
-    return (size_t)n * ldk * 4 + (size_t)G_max * npad * 4 + (size_t)kTab * 8 + 2 * align_up((size_t)n * 8, 256) +
-           align_up((size_t)n * 4, 256) + (size_t)n_p * 16 + 16384;
+    const size_t recs = ctx->step_sparse ? (size_t)n * step_rec_cap_row(n) : 2;
+    return (size_t)n * ldk * 4 + recs * 8 + (size_t)G_max * npad * 4 + (size_t)kTab * 8 +
+           2 * align_up((size_t)n * 8, 256) + align_up((size_t)n * 4, 256) + (size_t)n_p * 16 + 32768;
 }
 
 sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double* U, double* V,
@@ -626,6 +804,8 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     if (rc) return rc;
     Carve cv(ctx->ws.ptr);
     float* K = cv.take<float>((size_t)n * ldk);
+    const int64_t rec_cap_row = ctx->step_sparse ? step_rec_cap_row(n) : 0;
+    uint2* rec = cv.take<uint2>(ctx->step_sparse ? (size_t)n * rec_cap_row : 2);
     float* part = cv.take<float>((size_t)G_max * npad);
     double* tab = cv.take<double>(kTab);
     double* Vs = cv.take<double>(n);
@@ -636,6 +816,9 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     int* sweeps_out = cv.take<int>(o->n_p);
     unsigned* bar = cv.take<unsigned>(2);
     int* err = cv.take<int>(1);
+    unsigned long long* stats = cv.take<unsigned long long>(8);
+    unsigned* crange = cv.take<unsigned>(4);
+    int* counters = cv.take<int>(2);
     log2_table_kernel<<<kTab / 256, 256, 0, st>>>(tab);
     count_launch();
     SA_CUDA(cudaMemcpyAsync(P, o->p, o->n_p * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -643,6 +826,13 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     SA_CUDA(cudaMemsetAsync(rmax, 0, 2 * sizeof(float), st));
     SA_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     SA_CUDA(cudaMemsetAsync(sweeps_out, 0, o->n_p * sizeof(int), st));
+    SA_CUDA(cudaMemsetAsync(stats, 0, 8 * sizeof(unsigned long long), st));
+    SA_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(int), st));
+    {
+        // crange words: max = 0, min = +inf (bits of positive floats order like the floats)
+        static const unsigned init[4] = {0u, 0x7f800000u, 0u, 0x7f800000u};
+        SA_CUDA(cudaMemcpyAsync(crange, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    }
     const int k0 = o->resume_from > 0 ? o->resume_from : 0;
     if (k0 == 0) {
         SA_CUDA(cudaMemsetAsync(U, 0, n * sizeof(double), st));
@@ -650,6 +840,8 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     } else if (!o->warm_keep_v) {
         launch_scale_vec(V, n, o->p[k0] / o->p[k0 - 1], st);
     }
+    const size_t region = (size_t)cfg.ring * align_up((size_t)n * 4, 16);
+    const size_t cs_bytes = align_up((size_t)n * 8, 16);
     StepArgs args{};
     args.w = a->w;
     args.n = n;
@@ -659,6 +851,20 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     args.ldk = ldk;
     args.row_bytes = (unsigned)align_up((size_t)n * 4, 16);
     args.ring = cfg.ring;
+    args.region_bytes = (unsigned)region;
+    args.rec = rec;
+    args.rec_cap_row = rec_cap_row;
+    args.stats = stats;
+    args.crange = crange;
+    args.counters = counters;
+    // a sparse epoch needs a ring of >= 4 slots of its longest row next to c and S
+    args.sparse_row_cap = region > cs_bytes ? (unsigned)(((region - cs_bytes) / (4 * 8)) & ~(size_t)1) : 0u;
+    args.sparse_ok = ctx->step_sparse && args.sparse_row_cap >= 2;
+    args.sparse_max_total = (unsigned long long)n * (unsigned long long)n / 4ull;
+    // dropped entries of a row sum to at most n * theta * (max c / min c) of its mass
+    // (the largest entry of K in a row is about 1): n * 2^-70 * 2^20 <= 2^-36 for n <= 2^14
+    args.theta = 0x1p-70f;
+    args.reanchor_ratio = 0x1p20f;
     args.tab = tab;
     args.P = P;
     args.k0 = k0;
@@ -678,7 +884,7 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     args.sweeps_out = sweeps_out;
     args.resid_out = resid_out;
     args.max_rows = step_max_rows(ctx, n);
-    const size_t smem = step_smem_bytes(cfg.nt, cfg.ring, args.row_bytes, args.max_rows);
+    const size_t smem = step_smem_bytes(cfg.nt, region, args.max_rows);
     int G = ctx->max_grid > 0 ? std::min(G_max, ctx->max_grid) : G_max;
     cudaEvent_t ev0, ev1;
     SA_CUDA(cudaEventCreate(&ev0));
@@ -696,9 +902,11 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     if (prc) return prc;
     char* hp = (char*)ctx->pinned.ptr;
     int* h_err = (int*)hp;
+    int* h_cnt = (int*)(hp + 16);
     int* h_sw = (int*)(hp + 64);
     double* h_rs = (double*)(hp + 64 + align_up((size_t)o->n_p * 4, 64));
     SA_CUDA(cudaMemcpyAsync(h_err, err, 4, cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaMemcpyAsync(h_cnt, counters, 8, cudaMemcpyDeviceToHost, st));
     SA_CUDA(cudaMemcpyAsync(h_sw, sweeps_out, o->n_p * 4, cudaMemcpyDeviceToHost, st));
     SA_CUDA(cudaMemcpyAsync(h_rs, resid_out, o->n_p * 8, cudaMemcpyDeviceToHost, st));
     SA_CUDA(cudaStreamSynchronize(st));
@@ -721,6 +929,8 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
         info->fallback_rows = 0;
         info->kernel_used = SA_KERNEL_STEP;
         info->kernel_ms = kms;
+        info->sparse_epochs = h_cnt[0];
+        info->reanchors = h_cnt[1];
     }
     if (*h_err == kErrTimeout) {
         set_error("step sweep: a bounded device wait timed out (grid of %d blocks)", G);

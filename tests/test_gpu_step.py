@@ -157,3 +157,48 @@ def test_largest_supported_width(ctx):
     with pytest.raises(api.SaError):
         api.sa_scale(ctx, api.to_device(W.uniform(12292, 1, 10, 86, dtype=np.int16)), [1.0], 1e-6, 10,
                      kernel="step")
+
+
+def _ctx_with(env):
+    import os
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        return api.sa_create(0)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+@pytest.mark.parametrize("n", [512, 2048])
+def test_sparse_epochs_match_dense(ctx, n):
+    """At high p most entries of the step matrix fall below 2^-70 of their row and the step
+    path sweeps only the rest.  Same potentials (as X) as the all-dense path within a few
+    tol, FP64 sums within the p-independent bound."""
+    w, pi, _ = W.planted(n, W.BASE_SEED + 41 + n)
+    ps = [2.0 ** k for k in range(10)]
+    d = api.to_device(w)
+    sp = _ctx_with({"SA_STEP_SPARSE": "1"})
+    dense = _ctx_with({"SA_STEP_SPARSE": "0"})
+    try:
+        us, vs, info_s = api.sa_scale(sp, d, ps, 1e-6, 3000, kernel="step")
+        ud, vd, info_d = api.sa_scale(dense, d, ps, 1e-6, 3000, kernel="step")
+    finally:
+        sp.close()
+        dense.close()
+    assert info_s["sparse_epochs"] > 0, info_s
+    assert info_d["sparse_epochs"] == 0, info_d
+    b = oracle.log_weights(w.astype(np.int64))
+    us, vs, ud, vd = us.cpu().numpy(), vs.cpu().numpy(), ud.cpu().numpy(), vd.cpu().numpy()
+    for (u, v, info) in ((us, vs, info_s), (ud, vd, info_d)):
+        err = fp64_sum_err(b, ps[-1], u, v)
+        assert err < max(STEP_SUM_BOUND, 2 * info["residual"] + 1e-6), (err, info)
+    xs = oracle.xmatrix(b, ps[-1], us, vs)
+    xd = oracle.xmatrix(b, ps[-1], ud, vd)
+    tol_x = 4 * max(info_s["residual"], info_d["residual"], 1e-6) + 1e-6
+    assert np.max(np.abs(xs - xd)) < tol_x, np.max(np.abs(xs - xd))
+    # the planted permutation carries the mass at p = 512
+    assert np.all(xs[np.arange(n), pi] > 0.5)
