@@ -37,7 +37,7 @@ namespace sa {
 namespace {
 
 constexpr int kStepNred = 4;      // row-sum publication buffers
-constexpr int kStepMaxRing = 16;  // ring slots at most (sparse epochs use short slots)
+constexpr int kStepMaxRing = 16;  // ring slots at most; a slot holds one stage (two rows)
 
 struct StepArgs {
     const void* w;
@@ -55,7 +55,7 @@ struct StepArgs {
     unsigned* crange;      // [2][2]: max and min column factor of a sweep (float bits)
     int* counters;         // [2]: sparse epochs, re-anchors
     int sparse_ok;         // build records and allow sparse epochs
-    unsigned sparse_row_cap;            // longest row (records) a sparse epoch's ring holds
+    unsigned sparse_row_cap;            // longest stage (records of two rows) a sparse ring holds
     unsigned long long sparse_max_total; // most records for a sparse epoch
     float theta;           // entries of K below theta are dropped in sparse epochs
     float reanchor_ratio;  // re-evaluate K when max c / min c exceeds this
@@ -162,7 +162,7 @@ struct KahanS {
     }
 };
 
-template <int NT, int CH>
+template <int NT, int CH, bool SP>
 __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     constexpr int NW = NT / 32;
     constexpr int M = CH * 4;   // columns owned per thread (dense mode)
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     uint64_t* mrow = mbar + MAXR;                           // [NRED] row-sum publication
     unsigned* rel_cnt = (unsigned*)(mrow + NRED);           // [MAXR] warp releases per slot
     unsigned* iss_cnt = rel_cnt + MAXR;                     // [MAXR] copies issued per slot
-    // 8 (2 MAXR + NRED) bytes of barriers and counters end on a 16-byte boundary
+    // 8 (MAXR + NRED) + 8 MAXR bytes of barriers and counters end on a 16-byte boundary
     float* red = (float*)(iss_cnt + MAXR);                  // [NRED][2][NW] (16-aligned)
     double* crow = (double*)(red + NRED * 2 * NW);          // [max_rows] row references
     double* redp = crow + A.max_rows;                       // [FG][64]
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     __shared__ int s_flag, s_ok, s_mode, s_reanchor;
     __shared__ float s_res;
     __shared__ double s_max;
-    __shared__ unsigned s_maxlen;
+    __shared__ unsigned s_maxlen;   // longest stage (records of two rows) of this stripe
 
     const int n = A.n;
     const int G = gridDim.x;
@@ -220,30 +220,39 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     int ring_n = 4;
     unsigned slot_bytes = A.row_bytes;
     unsigned char* sbase = region;
-    uint32_t it = 0;      // consumption index of the current sweep's first row (per epoch)
+    uint32_t its = 0;     // ring index of the current sweep's first stage (per epoch)
     uint32_t gbase = 0;   // row stages completed, over the whole launch
     unsigned nbar = 0;
     int rphase = 0;
     unsigned epoch = 0;
-    auto issue_index = [&](uint32_t u) {   // one thread
-        const uint32_t slot = u % (uint32_t)ring_n;
-        const int q = (int)(u % (uint32_t)nrows);
-        iss_cnt[slot] += 1;
-        if (sparse) {
-            const unsigned bytes = rowlen[q] * 8u;
-            mbar_arrive_expect_tx(&mbar[slot], bytes);
-            bulk_g2s(sbase + (size_t)slot * slot_bytes, recb + rowoff[q], bytes, &mbar[slot]);
+    // The ring holds stages (local rows 2g and 2g+1, contiguous in global memory: K rows, or
+    // the records of the two rows) in fixed slots: ring index v is stage v % nst of its sweep,
+    // in slot v % ring_n.  The warp whose release completes a slot's count refills it with
+    // ring index v + ring_n: no thread waits to issue a copy.
+    const int nst = (nrows + 1) / 2;
+    auto issue_index = [&](uint32_t v) {   // one thread
+        const uint32_t slot = v % (uint32_t)ring_n;
+        const int q0 = 2 * (int)(v % (uint32_t)nst);
+        const int nr = min(2, nrows - q0);
+        const void* src;
+        unsigned bytes;
+        if (SP && sparse) {
+            src = recb + rowoff[q0];
+            bytes = (rowlen[q0] + (nr > 1 ? rowlen[q0 + 1] : 0u)) * 8u;
         } else {
-            mbar_arrive_expect_tx(&mbar[slot], A.row_bytes);
-            bulk_g2s(sbase + (size_t)slot * slot_bytes, kbase + (size_t)(r0 + q) * kpitch, A.row_bytes, &mbar[slot]);
+            src = kbase + (size_t)(r0 + q0) * kpitch;
+            bytes = (unsigned)nr * A.row_bytes;
         }
+        iss_cnt[slot] += 1;
+        mbar_arrive_expect_tx(&mbar[slot], bytes);
+        bulk_g2s(sbase + (size_t)slot * slot_bytes, src, bytes, &mbar[slot]);
     };
-    auto release_index = [&](uint32_t u) {   // lane 0 after __syncwarp
-        const uint32_t slot = u % (uint32_t)ring_n;
+    auto release_index = [&](uint32_t v) {   // lane 0 after __syncwarp
+        const uint32_t slot = v % (uint32_t)ring_n;
         const unsigned old = atom_add_acq_rel(&rel_cnt[slot], 1u);
         if ((old + 1u) % (unsigned)NW == 0u) {
             fence_proxy_async_smem();
-            issue_index(u + (uint32_t)ring_n);
+            issue_index(v + (uint32_t)ring_n);
         }
     };
     auto wait_copies = [&]() {   // tid 0: the last copy issued into every slot
@@ -330,7 +339,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) kvs[4 * k + e] = kv[e];
             }
-            if (A.sparse_ok) {
+            if (SP && A.sparse_ok) {
                 // compaction of the entries >= theta: warp scan of the per-thread counts
                 unsigned c = 0;
 #pragma unroll
@@ -363,14 +372,16 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 if (tid == 0) {
                     rowoff[q] = (unsigned)roff;
                     rowlen[q] = padded;
-                    if (padded > s_maxlen) s_maxlen = padded;
+                    // stage records: rows 2g and 2g+1 are contiguous
+                    const unsigned stage = (q & 1) ? rowlen[q - 1] + padded : padded;
+                    if (stage > s_maxlen) s_maxlen = stage;
                 }
                 if (fits) roff += padded;
                 else overflow = true;
                 __syncthreads();   // wcnt is reused by the next row
             }
         }
-        if (A.sparse_ok && tid == 0) {
+        if (SP && A.sparse_ok && tid == 0) {
             unsigned long long* st = A.stats + 4 * (epoch & 1u);
             atomicAdd(st + 0, (unsigned long long)roff);
             atomicMax(st + 1, (unsigned long long)s_maxlen);
@@ -408,7 +419,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
             // mode of this epoch, identical in every block
             if (tid == 0) {
                 int sp = 0;
-                if (A.sparse_ok) {
+                if (SP && A.sparse_ok) {
                     const volatile unsigned long long* st = A.stats + 4 * (epoch & 1u);
                     sp = st[2] == 0ull && st[0] <= A.sparse_max_total && st[1] <= (unsigned long long)A.sparse_row_cap &&
                          step_reanchors < 2;
@@ -423,25 +434,25 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
             __syncthreads();
             sparse = s_mode;
             ++epoch;
-            it = 0;
-            if (sparse) {
-                slot_bytes = s_maxlen * 8u;
-                sbase = region + cs_bytes;
-                ring_n = (int)min((size_t)MAXR, ((size_t)A.region_bytes - cs_bytes) / slot_bytes);
+            its = 0;
+            if (SP && sparse) {
                 for (int j = tid; j < n; j += NT) {
                     c_s[j] = 1.0f;
                     S_s[j] = 0.0f;
                 }
+                slot_bytes = s_maxlen * 8u;
+                sbase = region + cs_bytes;
+                ring_n = (int)min((size_t)MAXR, ((size_t)A.region_bytes - cs_bytes) / slot_bytes);
             } else {
-                slot_bytes = A.row_bytes;
+                slot_bytes = 2u * A.row_bytes;
                 sbase = region;
-                ring_n = A.ring;
+                ring_n = A.ring / 2;
 #pragma unroll
                 for (int m = 0; m < M; ++m) cf[m] = (m % 4) < nval[m / 4] ? 1.0f : 0.0f;
             }
             __syncthreads();
             if (tid == 0 && nrows > 0)
-                for (uint32_t u = 0; u < (uint32_t)ring_n; ++u) issue_index(u);
+                for (uint32_t v = 0; v < (uint32_t)ring_n; ++v) issue_index(v);
             bool done = false, reanchor = false;
             while (!done && !reanchor) {
                 SA_STEP_STAMP(0);
@@ -451,16 +462,17 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 // stage g = local rows 2g, 2g+1.  produce(g): partial row sums, published on
                 // mrow[g % NRED]; consume(g): wait for every warp's partials, accumulate the
                 // normalised rows into the column sums, release the slots.
-                const int nst = (nrows + 1) / 2;
-                auto slot_of = [&](uint32_t u) -> const unsigned char* {
-                    return sbase + (size_t)(u % (uint32_t)ring_n) * slot_bytes;
+                // row r (0, 1) of the stage at ring index v
+                auto row_of = [&](uint32_t v, int q0, int r) -> const unsigned char* {
+                    const unsigned char* base = sbase + (size_t)(v % (uint32_t)ring_n) * slot_bytes;
+                    if (r == 0) return base;
+                    return base + ((SP && sparse) ? rowlen[q0] * 8u : A.row_bytes);
                 };
-                auto row_partial = [&](uint32_t u) -> float {
-                    const unsigned char* rowp = slot_of(u);
+                auto row_partial = [&](const unsigned char* rowp, int q) -> float {
                     float a0 = 0.0f, a1 = 0.0f;
-                    if (sparse) {
+                    if (SP && sparse) {
                         const uint2* rp = (const uint2*)rowp;
-                        const unsigned len = rowlen[u % (uint32_t)nrows];
+                        const unsigned len = rowlen[q];
                         for (unsigned e = tid; e < len; e += NT) {
                             const uint2 r = rp[e];
                             a0 = fmaf(__uint_as_float(r.y), c_s[r.x], a0);
@@ -481,13 +493,11 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 auto produce = [&](int g) {
                     const int q0 = 2 * g;
                     const bool two = q0 + 1 < nrows;
-                    const uint32_t u0 = it + q0;
+                    const uint32_t v = its + g;
                     const uint32_t rn = (uint32_t)ring_n;
-                    bool ok = mbar_wait(&mbar[u0 % rn], (u0 / rn) & 1u, A.err, kWaitTimeoutNs);
-                    if (two) ok = mbar_wait(&mbar[(u0 + 1) % rn], ((u0 + 1) / rn) & 1u, A.err, kWaitTimeoutNs) && ok;
-                    if (!ok) s_flag = 1;
-                    const float sp0 = row_partial(u0);
-                    const float sp1 = two ? row_partial(u0 + 1) : 0.0f;
+                    if (!mbar_wait(&mbar[v % rn], (v / rn) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
+                    const float sp0 = row_partial(row_of(v, q0, 0), q0);
+                    const float sp1 = two ? row_partial(row_of(v, q0, 1), q0 + 1) : 0.0f;
                     const float w0 = warp_sum(sp0);
                     const float w1 = warp_sum(sp1);
                     if (lane == 0) {
@@ -500,7 +510,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 auto consume = [&](int g) -> bool {
                     const int q0 = 2 * g;
                     const bool two = q0 + 1 < nrows;
-                    const uint32_t u0 = it + q0;
+                    const uint32_t v = its + g;
                     const uint32_t gs = gbase + g;
                     if (!mbar_wait(&mrow[gs % NRED], (gs / NRED) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
                     if (s_flag) return false;
@@ -532,8 +542,8 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                     for (int r = 0; r < 2; ++r) {
                         if (r == 1 && !two) break;
                         const float inv = rcp_approx(ss[r]);
-                        const unsigned char* rowp = slot_of(u0 + r);
-                        if (sparse) {
+                        const unsigned char* rowp = row_of(v, q0, r);
+                        if (SP && sparse) {
                             const uint2* rp = (const uint2*)rowp;
                             const unsigned len = rowlen[q0 + r];
                             for (unsigned e = tid; e < len; e += NT) {
@@ -553,10 +563,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                         }
                     }
                     __syncwarp();
-                    if (lane == 0) {
-                        release_index(u0);
-                        if (two) release_index(u0 + 1);
-                    }
+                    if (lane == 0) release_index(v);
                     return true;
                 };
                 if (nst > 0) produce(0);
@@ -567,10 +574,10 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 __syncthreads();
                 SA_STEP_STAMP(1);
                 if (s_flag) { drain(); return; }
-                it += (uint32_t)nrows;
+                its += (uint32_t)nst;
                 gbase += (uint32_t)nst;
                 float* pb = A.part + (size_t)b * A.npad;
-                if (sparse) {
+                if (SP && sparse) {
                     for (int j = tid; j < n; j += NT) {
                         pb[j] = S_s[j] * c_s[j];
                         S_s[j] = 0.0f;
@@ -636,7 +643,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 if (wid < 2) {
                     rmax = warp_max(rmax);
                     if (lane == 0 && rmax > 0.0f) atomicMax((unsigned*)rmax_word, __float_as_uint(rmax));
-                    if (sparse) {
+                    if (SP && sparse) {
                         cmx = warp_max(cmx);
                         cmn = -warp_max(-cmn);
                         // positive floats order like their bit patterns
@@ -650,7 +657,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 if (tid == 0) {
                     s_res = __uint_as_float(ld_acquire((const unsigned*)rmax_word));
                     int ra = 0;
-                    if (sparse) {
+                    if (SP && sparse) {
                         const float hi = __uint_as_float(ld_acquire(A.crange + 2 * par));
                         const float lo = __uint_as_float(ld_acquire(A.crange + 2 * par + 1));
                         ra = !(hi <= A.reanchor_ratio * lo);
@@ -667,7 +674,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 done = (resid <= A.tol) || (sweeps >= A.max_sweeps);
                 reanchor = !done && s_reanchor;
                 if (!done && !reanchor) {
-                    if (sparse) {
+                    if (SP && sparse) {
                         for (int j = tid; j < n; j += NT) c_s[j] = __ldcg(A.Cf + j);
                         __syncthreads();
                     } else {
@@ -706,7 +713,8 @@ struct StepCfg {
 size_t step_smem_bytes(int nt, size_t region_bytes, int max_rows) {
     const int nw = nt / 32;
     const int fg = nt / 64;
-    return region_bytes + 8 * (size_t)(2 * kStepMaxRing + kStepNred) + 4 * (size_t)(kStepNred * 2 * nw) +
+    return region_bytes + 8 * (size_t)(kStepMaxRing + kStepNred) + 8 * (size_t)kStepMaxRing +
+           4 * (size_t)(kStepNred * 2 * nw) +
            8 * (size_t)(max_rows + fg * 64 + nw) + 4 * (size_t)max_rows + 8 * (size_t)max_rows + 1024;
 }
 
@@ -742,7 +750,8 @@ StepCfg pick_step(const sa_ctx* ctx, int n) {
 
 template <int NT, int CH>
 sa_status launch_step(sa_ctx* ctx, const StepArgs& args, size_t smem, int* grid_out) {
-    auto kern = step_kernel<NT, CH>;
+    // the dense-only instantiation carries none of the sparse code
+    auto kern = args.sparse_ok ? step_kernel<NT, CH, true> : step_kernel<NT, CH, false>;
     SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
@@ -857,8 +866,9 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     args.stats = stats;
     args.crange = crange;
     args.counters = counters;
-    // a sparse epoch needs a ring of >= 4 slots of its longest row next to c and S
-    args.sparse_row_cap = region > cs_bytes ? (unsigned)(((region - cs_bytes) / (4 * 8)) & ~(size_t)1) : 0u;
+    // a sparse epoch's ring (next to c and S) needs >= 3 slots of its longest stage: two in
+    // use and one in flight
+    args.sparse_row_cap = region > cs_bytes ? (unsigned)(((region - cs_bytes) / (3 * 8)) & ~(size_t)1) : 0u;
     args.sparse_ok = ctx->step_sparse && args.sparse_row_cap >= 2;
     args.sparse_max_total = (unsigned long long)n * (unsigned long long)n / 4ull;
     // dropped entries of a row sum to at most n * theta * (max c / min c) of its mass
