@@ -71,7 +71,8 @@ typedef enum { SA_PREC_MIXED = 0, SA_PREC_FP32 = 1, SA_PREC_FP64 = 2 } sa_prec;
  *   K = 2^(p log2 w - C_i - V_j) once (FP64 exponent from an exact log2 table, one FP32
  *   rounding) into a workspace of n * ceil(n/4)*4 floats, and each sweep reads K once
  *   (4 bytes per element): no per-element SFU work in the sweeps and an error that does
- *   not grow with p.  Needs n <= 12288.
+ *   not grow with p.  Needs n <= 24576 (above 12288 the rows are read from global
+ *   memory, prefetched into L2, instead of through the shared-memory ring).
  * AUTO: STEP for SA_PREC_MIXED when it applies, else FUSED when it applies, else PLAIN;
  *   PLAIN for SA_PREC_FP64. */
 typedef enum { SA_KERNEL_AUTO = 0, SA_KERNEL_FUSED = 1, SA_KERNEL_PLAIN = 2, SA_KERNEL_STEP = 3 } sa_kernel;

@@ -238,7 +238,7 @@ sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, doub
         return SA_E_UNSUPPORTED;
     }
     if (kind == SA_KERNEL_STEP && (o->prec != SA_PREC_MIXED || !step_supported(ctx, a))) {
-        set_error("step kernel needs SA_PREC_MIXED, a 16-byte aligned base, ld*sizeof(w) %% 16 == 0 and n <= 12288");
+        set_error("step kernel needs SA_PREC_MIXED, a 16-byte aligned base, ld*sizeof(w) %% 16 == 0 and n <= 24576");
         return SA_E_UNSUPPORTED;
     }
     if (kind == SA_KERNEL_STEP) rc = scale_step(ctx, a, o, d_u, d_v, info);

@@ -38,6 +38,7 @@ namespace {
 
 constexpr int kStepNred = 4;      // row-sum publication buffers
 constexpr int kStepMaxRing = 16;  // ring slots at most; a slot holds one stage (two rows)
+constexpr int kStepPrefetch = 4;  // direct mode: stages prefetched into L2 ahead of use
 
 struct StepArgs {
     const void* w;
@@ -59,7 +60,7 @@ struct StepArgs {
     unsigned long long sparse_max_total; // most records for a sparse epoch
     float theta;           // entries of K below theta are dropped in sparse epochs
     float reanchor_ratio;  // re-evaluate K when max c / min c exceeds this
-    const double* tab;     // log2 k for k = 0..kTab-1 (tab[0] = -inf)
+    const float2* tab;     // log2 k for k = 0..kTab-1 as an unevaluated float pair (hi, lo)
     const double* P;       // schedule
     int k0, n_p;
     double tol;
@@ -81,9 +82,14 @@ struct StepArgs {
 
 constexpr int kTab = 32768;
 
-__global__ void log2_table_kernel(double* tab) {
+// log2 k split into hi = float(log2 k) and lo = float(log2 k - hi): 48 significant bits
+__global__ void log2_table_kernel(float2* tab) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < kTab) tab[k] = k > 0 ? log2((double)k) : -INFINITY;
+    if (k < kTab) {
+        const double l = k > 0 ? log2((double)k) : 0.0;
+        const float hi = (float)l;
+        tab[k] = make_float2(hi, (float)(l - (double)hi));
+    }
 }
 
 __device__ __forceinline__ void load_w4(const StepArgs& A, int64_t row, int j, int cnt, int w[4]) {
@@ -112,9 +118,20 @@ __device__ __forceinline__ void load_w4(const StepArgs& A, int64_t row, int j, i
     }
 }
 
-// exact log2 of a positive integer weight in FP64 (table for the int16 range)
-__device__ __forceinline__ double wlog2(const double* tab, int w) {
-    return w < kTab ? __ldg(tab + (w > 0 ? w : 0)) : log2((double)w);
+// log2 of a positive integer weight as a float pair (table for the int16 range)
+__device__ __forceinline__ float2 wlog2(const float2* tab, int w) {
+    if (w < kTab) return __ldg(tab + w);
+    const double l = log2((double)w);
+    const float hi = (float)l;
+    return make_float2(hi, (float)(l - (double)hi));
+}
+
+// s + err = a + b exactly (Knuth's two-sum; no FMA contraction is possible here)
+__device__ __forceinline__ float two_sum(float a, float b, float* err) {
+    const float s = a + b;
+    const float bb = s - a;
+    *err = (a - (s - bb)) + (b - bb);
+    return s;
 }
 
 __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
@@ -162,7 +179,10 @@ struct KahanS {
     }
 };
 
-template <int NT, int CH, bool SP>
+// SP: sparse epochs possible.  DIR: rows too wide for a shared-memory ring (n > 12288) are
+// read straight from global memory (prefetched into L2 a few stages ahead by bulk
+// prefetches) and re-read from L1/L2 for the column accumulation.
+template <int NT, int CH, bool SP, bool DIR>
 __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     constexpr int NW = NT / 32;
     constexpr int M = CH * 4;   // columns owned per thread (dense mode)
@@ -247,6 +267,11 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
         mbar_arrive_expect_tx(&mbar[slot], bytes);
         bulk_g2s(sbase + (size_t)slot * slot_bytes, src, bytes, &mbar[slot]);
     };
+    auto prefetch_stage = [&](int g) {   // one thread: the K rows of stage g into L2
+        const int q0 = 2 * g;
+        const int nr = min(2, nrows - q0);
+        if (nr > 0) bulk_prefetch_l2(kbase + (size_t)(r0 + q0) * kpitch, (unsigned)nr * A.row_bytes);
+    };
     auto release_index = [&](uint32_t v) {   // lane 0 after __syncwarp
         const uint32_t slot = v % (uint32_t)ring_n;
         const unsigned old = atom_add_acq_rel(&rel_cnt[slot], 1u);
@@ -285,8 +310,16 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     //      >= theta as (column, value) records ----
     auto prep = [&](double p) {
         const float pf = (float)p;
-        double* vsm = (double*)region;   // the region is idle: stage V there
-        for (int j = tid; j < n; j += NT) vsm[j] = A.V[j];
+        // the region is idle: stage V there as float pairs (hi, lo)
+        float2* vsm = (float2*)region;
+        for (int j = tid; j < n; j += NT) {
+            const double vj = A.V[j];
+            const float hi = (float)vj;
+            vsm[j] = make_float2(hi, (float)(vj - (double)hi));
+        }
+        // p = ph + pl (pl = 0 for any p with at most 24 significant bits)
+        const float ph = (float)p;
+        const float pl = (float)(p - (double)ph);
         if (tid == 0) s_maxlen = 0u;
         __syncthreads();
         unsigned* wcnt = (unsigned*)red;   // [NW] per-warp kept counts (scratch)
@@ -304,7 +337,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
                     if (e < nval[k] && w[e] > 0)
-                        mloc = fmaxf(mloc, fmaf(pf, lg2_approx((float)w[e]), -(float)vsm[cidx[k] * 4 + e]));
+                        mloc = fmaxf(mloc, fmaf(pf, lg2_approx((float)w[e]), -vsm[cidx[k] * 4 + e].x));
             }
             mloc = warp_max(mloc);
             if (lane == 0) redd[wid] = (double)mloc;
@@ -318,6 +351,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
             }
             __syncthreads();
             const double m = s_max;
+            const float mh = (float)m, ml = (float)(m - (double)mh);
             float* krow = A.K + row * A.ldk;
             float kvs[M];
 #pragma unroll
@@ -329,9 +363,18 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         if (e < nval[k] && w[e] > 0) {
-                            // exponent in FP64 (exact table log2), then one rounding to FP32
-                            const double x = fma(p, wlog2(A.tab, w[e]), -(vsm[cidx[k] * 4 + e] + m));
-                            kv[e] = ex2_approx((float)x);
+                            // x = p log2 w - V_j - m with 48-bit operands: the large leading
+                            // parts cancel exactly (two-product, two-sums), the small ones are
+                            // added after; x is then exact to about 2^-24 |x|
+                            const float2 lw = wlog2(A.tab, w[e]);
+                            const float2 vj = vsm[cidx[k] * 4 + e];
+                            const float t = ph * lw.x;
+                            const float te = fmaf(ph, lw.x, -t);
+                            float e1, e2;
+                            const float s1 = two_sum(t, -vj.x, &e1);
+                            const float s2 = two_sum(s1, -mh, &e2);
+                            const float rest = ((te + e1) + e2) + (fmaf(ph, lw.y, pl * lw.x) - vj.y - ml);
+                            kv[e] = ex2_approx(s2 + rest);
                         }
                     }
                 }
@@ -451,8 +494,10 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 for (int m = 0; m < M; ++m) cf[m] = (m % 4) < nval[m / 4] ? 1.0f : 0.0f;
             }
             __syncthreads();
-            if (tid == 0 && nrows > 0)
+            if (!DIR && tid == 0 && nrows > 0)
                 for (uint32_t v = 0; v < (uint32_t)ring_n; ++v) issue_index(v);
+            if (DIR && tid == 0)
+                for (int g = 0; g < min(kStepPrefetch, nst); ++g) prefetch_stage(g);
             bool done = false, reanchor = false;
             while (!done && !reanchor) {
                 SA_STEP_STAMP(0);
@@ -464,6 +509,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 // normalised rows into the column sums, release the slots.
                 // row r (0, 1) of the stage at ring index v
                 auto row_of = [&](uint32_t v, int q0, int r) -> const unsigned char* {
+                    if (DIR) return kbase + (size_t)(r0 + q0 + r) * kpitch;
                     const unsigned char* base = sbase + (size_t)(v % (uint32_t)ring_n) * slot_bytes;
                     if (r == 0) return base;
                     return base + ((SP && sparse) ? rowlen[q0] * 8u : A.row_bytes);
@@ -495,7 +541,13 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                     const bool two = q0 + 1 < nrows;
                     const uint32_t v = its + g;
                     const uint32_t rn = (uint32_t)ring_n;
-                    if (!mbar_wait(&mbar[v % rn], (v / rn) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
+                    if (DIR) {
+                        // rows of stage g + P into L2 while this stage is summed (the stage after
+                        // the last wraps to the next sweep's first)
+                        if (tid == 0) prefetch_stage((g + kStepPrefetch) % nst);
+                    } else if (!mbar_wait(&mbar[v % rn], (v / rn) & 1u, A.err, kWaitTimeoutNs)) {
+                        s_flag = 1;
+                    }
                     const float sp0 = row_partial(row_of(v, q0, 0), q0);
                     const float sp1 = two ? row_partial(row_of(v, q0, 1), q0 + 1) : 0.0f;
                     const float w0 = warp_sum(sp0);
@@ -562,8 +614,10 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                             S[4 * kk + 3] = fmaf(kv.w, inv, S[4 * kk + 3]);
                         }
                     }
-                    __syncwarp();
-                    if (lane == 0) release_index(v);
+                    if (!DIR) {
+                        __syncwarp();
+                        if (lane == 0) release_index(v);
+                    }
                     return true;
                 };
                 if (nst > 0) produce(0);
@@ -708,6 +762,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
 
 struct StepCfg {
     int nt, ch, ring;
+    bool direct;
 };
 
 size_t step_smem_bytes(int nt, size_t region_bytes, int max_rows) {
@@ -726,16 +781,25 @@ int step_max_rows(const sa_ctx* ctx, int n) {
 
 StepCfg pick_step(const sa_ctx* ctx, int n) {
     const int nc = (n + 3) / 4;
-    StepCfg c{0, 0, 0};
-    if (nc <= 128) c = {128, 1, 0};
-    else if (nc <= 256) c = {256, 1, 0};
-    else if (nc <= 512) c = {512, 1, 0};
-    else if (nc <= 1024) c = {512, 2, 0};
-    else if (nc <= 2048) c = {512, 4, 0};
-    else if (nc <= 3072) c = {512, 6, 0};
+    StepCfg c{0, 0, 0, false};
+    if (nc <= 128) c = {128, 1, 0, false};
+    else if (nc <= 256) c = {256, 1, 0, false};
+    else if (nc <= 512) c = {512, 1, 0, false};
+    else if (nc <= 1024) c = {512, 2, 0, false};
+    else if (nc <= 2048) c = {512, 4, 0, false};
+    else if (nc <= 3072) c = {512, 6, 0, false};
+    else if (nc <= 4096) c = {512, 8, 0, true};
+    else if (nc <= 5120) c = {512, 10, 0, true};
+    else if (nc <= 6144) c = {512, 12, 0, true};
     else return c;
     const unsigned row_bytes = (unsigned)align_up((size_t)n * 4, 16);
     const int max_rows = step_max_rows(ctx, n);
+    if (c.direct) {
+        // no ring: the region only stages V (8 n bytes) while K is evaluated
+        if (step_smem_bytes(c.nt, align_up((size_t)n * 8, 16), max_rows) <= ctx->smem_optin) return c;
+        c.nt = 0;
+        return c;
+    }
     // the ring doubles as scratch for V (8 n bytes) during the per-step evaluation
     for (int ring = 8; ring >= 4; --ring) {
         if ((size_t)ring * row_bytes < (size_t)n * 8) break;
@@ -748,10 +812,10 @@ StepCfg pick_step(const sa_ctx* ctx, int n) {
     return c;
 }
 
-template <int NT, int CH>
+template <int NT, int CH, bool DIR>
 sa_status launch_step(sa_ctx* ctx, const StepArgs& args, size_t smem, int* grid_out) {
     // the dense-only instantiation carries none of the sparse code
-    auto kern = args.sparse_ok ? step_kernel<NT, CH, true> : step_kernel<NT, CH, false>;
+    auto kern = (!DIR && args.sparse_ok) ? step_kernel<NT, CH, !DIR, DIR> : step_kernel<NT, CH, false, DIR>;
     SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
@@ -816,7 +880,7 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     const int64_t rec_cap_row = ctx->step_sparse ? step_rec_cap_row(n) : 0;
     uint2* rec = cv.take<uint2>(ctx->step_sparse ? (size_t)n * rec_cap_row : 2);
     float* part = cv.take<float>((size_t)G_max * npad);
-    double* tab = cv.take<double>(kTab);
+    float2* tab = cv.take<float2>(kTab);
     double* Vs = cv.take<double>(n);
     float* Cf = cv.take<float>(n);
     float* rmax = cv.take<float>(2);
@@ -849,7 +913,7 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     } else if (!o->warm_keep_v) {
         launch_scale_vec(V, n, o->p[k0] / o->p[k0 - 1], st);
     }
-    const size_t region = (size_t)cfg.ring * align_up((size_t)n * 4, 16);
+    const size_t region = cfg.direct ? align_up((size_t)n * 8, 16) : (size_t)cfg.ring * align_up((size_t)n * 4, 16);
     const size_t cs_bytes = align_up((size_t)n * 8, 16);
     StepArgs args{};
     args.w = a->w;
@@ -869,7 +933,7 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     // a sparse epoch's ring (next to c and S) needs >= 3 slots of its longest stage: two in
     // use and one in flight
     args.sparse_row_cap = region > cs_bytes ? (unsigned)(((region - cs_bytes) / (3 * 8)) & ~(size_t)1) : 0u;
-    args.sparse_ok = ctx->step_sparse && args.sparse_row_cap >= 2;
+    args.sparse_ok = ctx->step_sparse && !cfg.direct && args.sparse_row_cap >= 2;
     args.sparse_max_total = (unsigned long long)n * (unsigned long long)n / 4ull;
     // dropped entries of a row sum to at most n * theta * (max c / min c) of its mass
     // (the largest entry of K in a row is about 1): n * 2^-70 * 2^20 <= 2^-36 for n <= 2^14
@@ -900,12 +964,15 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     SA_CUDA(cudaEventCreate(&ev0));
     SA_CUDA(cudaEventCreate(&ev1));
     SA_CUDA(cudaEventRecord(ev0, st));
-    if (cfg.nt == 128) rc = launch_step<128, 1>(ctx, args, smem, &G);
-    else if (cfg.nt == 256) rc = launch_step<256, 1>(ctx, args, smem, &G);
-    else if (cfg.ch == 1) rc = launch_step<512, 1>(ctx, args, smem, &G);
-    else if (cfg.ch == 2) rc = launch_step<512, 2>(ctx, args, smem, &G);
-    else if (cfg.ch == 4) rc = launch_step<512, 4>(ctx, args, smem, &G);
-    else rc = launch_step<512, 6>(ctx, args, smem, &G);
+    if (cfg.nt == 128) rc = launch_step<128, 1, false>(ctx, args, smem, &G);
+    else if (cfg.nt == 256) rc = launch_step<256, 1, false>(ctx, args, smem, &G);
+    else if (cfg.ch == 1) rc = launch_step<512, 1, false>(ctx, args, smem, &G);
+    else if (cfg.ch == 2) rc = launch_step<512, 2, false>(ctx, args, smem, &G);
+    else if (cfg.ch == 4) rc = launch_step<512, 4, false>(ctx, args, smem, &G);
+    else if (cfg.ch == 6) rc = launch_step<512, 6, false>(ctx, args, smem, &G);
+    else if (cfg.ch == 8) rc = launch_step<512, 8, true>(ctx, args, smem, &G);
+    else if (cfg.ch == 10) rc = launch_step<512, 10, true>(ctx, args, smem, &G);
+    else rc = launch_step<512, 12, true>(ctx, args, smem, &G);
     if (rc) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); return rc; }
     SA_CUDA(cudaEventRecord(ev1, st));
     sa_status prc = ctx->pinned.reserve(4096 + (size_t)o->n_p * 16);

@@ -144,9 +144,8 @@ def test_zero_row_is_nonfinite(ctx):
 
 
 def test_largest_supported_width(ctx):
-    """n = 12288 (six chunks of four columns per thread, the widest configuration): FP64
-    sums by the library's own verification, the property that holds at any size; one
-    column more is rejected."""
+    """n = 12288 (six chunks of four columns per thread, the widest ring configuration):
+    FP64 sums by the library's own verification, the property that holds at any size."""
     n = 12288
     w = W.uniform(n, 1, 1000, 85, dtype=np.int16)
     d = api.to_device(w)
@@ -154,8 +153,29 @@ def test_largest_supported_width(ctx):
     assert info["status"] == 0 and info["kernel_used"] == 3, info
     er, ec = api.sa_verify(ctx, d, 2.0, u, v)
     assert max(er, ec) < STEP_SUM_BOUND, (er, ec)
+
+
+@pytest.mark.parametrize("n", [12290, 20000])
+def test_direct_rows_wide_instances(ctx, n):
+    """Rows wider than the ring (read from global memory with L2 prefetch): the n = 20000
+    int16 instance with weights in [1, 32767] over p = 1, 2, 4 and a ragged width; FP64 sums
+    by the library's verification, and the row sums of a few sampled rows recomputed by the
+    oracle."""
+    w = W.uniform(n, 1, 32767, 86, dtype=np.int16)
+    d = api.to_device(w)
+    ps = [1.0, 2.0, 4.0]
+    u, v, info = api.sa_scale(ctx, d, ps, 1e-6, 2000, kernel="step")
+    assert info["status"] == 0 and info["kernel_used"] == 3, info
+    er, ec = api.sa_verify(ctx, d, ps[-1], u, v)
+    assert max(er, ec) < STEP_SUM_BOUND, (er, ec)
+    uu, vv = u.cpu().numpy(), v.cpu().numpy()
+    rng = np.random.default_rng(0)
+    for i in rng.choice(n, 4, replace=False):
+        b = np.log(w[i].astype(np.float64))
+        s = np.exp(ps[-1] * b - uu[i] - vv).sum()
+        assert abs(s - 1.0) < STEP_SUM_BOUND + 1e-6, (i, s)
     with pytest.raises(api.SaError):
-        api.sa_scale(ctx, api.to_device(W.uniform(12292, 1, 10, 86, dtype=np.int16)), [1.0], 1e-6, 10,
+        api.sa_scale(ctx, api.to_device(W.uniform(24580, 1, 10, 87, dtype=np.int16)), [1.0], 1e-6, 10,
                      kernel="step")
 
 
