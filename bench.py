@@ -300,6 +300,79 @@ def run_batch(args):
     ctx.close()
 
 
+def run_precision(args):
+    """Precision form: the dense n = 20000 int16 instance (weights uniform in [1, 32767],
+    p = 1, 2, ..., 256) scaled by the mixed-precision path (per-step FP32 matrix, FP64
+    potentials), the all-FP32 path (FP32 potentials) and the all-FP64 path on the same input;
+    sweeps/s of the scaling and the error of each result: FP64 row/column sums of X(p) over
+    the whole matrix, and FP64 row sums of sampled rows recomputed here from the definition
+    x_ij = exp(p log w_ij - u_i - v_j)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1104_3830_gb300 import _lib as L
+    from paper_1104_3830_gb300 import api
+    from paper_1104_3830_gb300 import workloads as W
+    w, ps = W.c3()
+    n = w.shape[0]
+    stream = torch.cuda.current_stream()
+    ctx = api.sa_create(0, stream.cuda_stream)
+    d = api.to_device(w)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(7)
+    rows = rng.choice(n, 16, replace=False)
+    launches0 = L.lib().sa_kernel_launches()
+    paths = {}
+    with ClockSampler(0) as clk:
+        for name, prec in (("mixed", "mixed"), ("fp32", "fp32"), ("fp64", "fp64")):
+            reps = 1 if prec == "fp64" else max(1, args.steps)
+            for _ in range(1 if prec == "fp64" else args.warmup):
+                api.sa_scale(ctx, d, ps, 1e-6, args.max_sweeps, prec=prec)
+            times, infos = [], []
+            for _ in range(reps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                u, v, info = api.sa_scale(ctx, d, ps, 1e-6, args.max_sweeps, prec=prec)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+                infos.append(info)
+            info = infos[-1]
+            er, ec = api.sa_verify(ctx, d, ps[-1], u, v)
+            uu, vv = u.cpu().numpy(), v.cpu().numpy()
+            row_err = 0.0
+            for i in rows:
+                s_ = np.exp(ps[-1] * np.log(w[i].astype(np.float64)) - uu[i] - vv).sum()
+                row_err = max(row_err, abs(s_ - 1.0))
+            ms = statistics.mean(times)
+            paths[name] = {"sweeps": int(info["sweeps_total"]), "ms": ms,
+                           "sweeps_per_s": info["sweeps_total"] / (ms / 1e3),
+                           "kernel": KERNEL_NAMES.get(info["kernel_used"], "?"),
+                           "kernel_ms": info["kernel_ms"], "converged": int(info["converged"]),
+                           "fp64_row_sum_err": er, "fp64_col_sum_err": ec,
+                           "sampled_rows_err": row_err}
+    launches = L.lib().sa_kernel_launches() - launches0
+    peak, peak_kind = load_peaks()
+    m = paths["mixed"]
+    achieved = m["sweeps"] * n * n * 2 / (m["ms"] / 1e3) / 1e9
+    line = {"metric": METRIC, "value": m["sweeps_per_s"], "unit": "sweeps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (exp/sum), f64 potentials", "data": "synthetic",
+            "config": {"workload": "uniform n=20000 int16 w in [1,32767], p=1..256 (x2), tol 1e-6, scaling only "
+                                   "(mixed / all-FP32 / all-FP64 paths on the same input)",
+                       "l2": "flushed before every timed run (256 MiB write); the matrix (800 MB) exceeds L2",
+                       "sampled_rows": [int(i) for i in rows]},
+            "paths": paths,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": m["kernel"], "peak_source": f"{peak_kind} hbm_gbs",
+                         "note": "whole scaling call incl. the per-step evaluation of K, 3 sweeps per step"},
+            "e2e": None, "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serve(args):
     """Serving form: Poisson request stream of dense instances, n log-uniform in
     [32, 4096], through the continuous-batching server (sa_submit/sa_poll) and through a
@@ -314,7 +387,8 @@ def run_serve(args):
     seed = W.BASE_SEED + 4
     pool_n = W.loguniform_sizes(args.serve_pool, 32, 4096, seed)
     pool = [W.c5_request(seed, q, int(n), args.serve_dist) for q, n in enumerate(pool_n)]
-    arrivals = W.poisson_arrivals(args.serve_rate, args.serve_seconds, seed)
+    # the first serve_requests arrivals of the Poisson stream, served by both systems
+    arrivals = W.poisson_arrivals(args.serve_rate, args.serve_seconds, seed)[: args.serve_requests]
     ps = [2.0 ** q for q in range(9)]
     o = L.make_opts(ps, 1e-6, args.max_sweeps)
     lib = L.lib()
@@ -350,9 +424,9 @@ def run_serve(args):
                 "instances_per_s": len(lat) / span, "requests": len(lat)}
 
     ours = serve_run(arrivals)
-    # plain FIFO: one request at a time on the plain kernels, same arrivals (bounded sample)
+    # plain FIFO: one request at a time on the plain kernels, the same arrivals
     ctx = api.sa_create(0)
-    arr_f = arrivals[: args.fifo_requests]
+    arr_f = arrivals
     lat = []
     t0 = time.perf_counter()
     free_at = 0.0
@@ -371,9 +445,10 @@ def run_serve(args):
     line = {"metric": METRIC, "value": ours["instances_per_s"], "unit": "instances/s", "n_gpus": 1,
             "steps": 1, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (exp/sum), f64 potentials", "data": "synthetic",
-            "config": {"workload": f"Poisson {args.serve_rate}/s for {args.serve_seconds}s, n log-uniform [32,4096], "
-                                   f"{args.serve_dist} weights, 40 GB budget, p=1..256 (x2)",
-                       "offered_per_s": len(arrivals) / args.serve_seconds, "pool": len(pool)},
+            "config": {"workload": f"first {len(arrivals)} requests of a Poisson {args.serve_rate}/s stream, "
+                                   f"n log-uniform [32,4096], {args.serve_dist} weights, 40 GB budget, p=1..256 (x2); "
+                                   "the same requests and arrival times for both systems",
+                       "offered_per_s": args.serve_rate, "pool": len(pool)},
             "serve": ours, "plain_fifo": fifo}
     print(json.dumps(line), flush=True)
 
@@ -396,7 +471,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-pool", type=int, default=96)
     ap.add_argument("--serve-dist", default="uniform", choices=["uniform", "zipf"])
-    ap.add_argument("--fifo-requests", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=300)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -404,6 +479,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "precision20000":
+        return run_precision(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
