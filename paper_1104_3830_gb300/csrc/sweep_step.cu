@@ -60,7 +60,6 @@ struct StepArgs {
     unsigned long long sparse_max_total; // most records for a sparse epoch
     float theta;           // entries of K below theta are dropped in sparse epochs
     float reanchor_ratio;  // re-evaluate K when max c / min c exceeds this
-    const float2* tab;     // log2 k for k = 0..kTab-1 as an unevaluated float pair (hi, lo)
     const double* P;       // schedule
     int k0, n_p;
     double tol;
@@ -80,17 +79,7 @@ struct StepArgs {
     int max_rows;
 };
 
-constexpr int kTab = 32768;
-
-// log2 k split into hi = float(log2 k) and lo = float(log2 k - hi): 48 significant bits
-__global__ void log2_table_kernel(float2* tab) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < kTab) {
-        const double l = k > 0 ? log2((double)k) : 0.0;
-        const float hi = (float)l;
-        tab[k] = make_float2(hi, (float)(l - (double)hi));
-    }
-}
+constexpr int kTab = 32768;   // weights below this take the shared-table logarithm
 
 __device__ __forceinline__ void load_w4(const StepArgs& A, int64_t row, int j, int cnt, int w[4]) {
     if (A.i16) {
@@ -118,20 +107,53 @@ __device__ __forceinline__ void load_w4(const StepArgs& A, int64_t row, int j, i
     }
 }
 
-// log2 of a positive integer weight as a float pair (table for the int16 range)
-__device__ __forceinline__ float2 wlog2(const float2* tab, int w) {
-    if (w < kTab) return __ldg(tab + w);
-    const double l = log2((double)w);
-    const float hi = (float)l;
-    return make_float2(hi, (float)(l - (double)hi));
-}
-
 // s + err = a + b exactly (Knuth's two-sum; no FMA contraction is possible here)
 __device__ __forceinline__ float two_sum(float a, float b, float* err) {
     const float s = a + b;
     const float bb = s - a;
     *err = (a - (s - bb)) + (b - bb);
     return s;
+}
+
+// Shared table for log2 of a weight: entry j (the top 8 mantissa bits of m in [1, 2)) holds
+// g_j = 1 / (1 + (j + 0.5)/256) rounded to 9 significant bits and -log2(g_j) as a float pair.
+__device__ __forceinline__ float4 log2_tab_entry(int j) {
+    const double c = 1.0 + (j + 0.5) / 256.0;
+    const double g = ldexp(rint(ldexp(1.0 / c, 8)), -8);   // 9 significant bits (value in (0.5, 1))
+    const double t = -log2(g);
+    const float th = (float)t;
+    return make_float4((float)g, th, (float)(t - (double)th), 0.0f);
+}
+
+// log2 w (0 < w < 2^15) as an unevaluated float pair, accurate to about 2^-40: with
+// w = 2^e m, m g_j is exact (15 + 9 significant bits), so r = m g_j - 1 is exact and
+// |r| < 2^-8; log2 w = e + (-log2 g_j) + log2(1 + r), the last from its series with the
+// leading product r log2(e) split exactly.
+__device__ __forceinline__ float2 log2_pair(int w, const float4* tab) {
+    const unsigned bits = __float_as_uint((float)w);
+    const int e = (int)(bits >> 23) - 127;
+    const float4 t = tab[(bits >> 15) & 0xFFu];
+    const float m = __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
+    const float r = fmaf(m, t.x, -1.0f);
+    const float l2eh = 1.4426950216293335f, l2el = 1.925963033500011e-08f;   // log2(e) as a pair
+    const float ph = r * l2eh;
+    const float pe = fmaf(r, l2eh, -ph);
+    // ln(1 + r) / r - 1 = -r/2 + r^2/3 - r^3/4 + r^4/5 - r^5/6 (next term below 2^-48)
+    const float poly = r * (-0.5f + r * (0.333333343f + r * (-0.25f + r * (0.2f + r * -0.166666672f))));
+    const float small = fmaf(r, l2el, pe) + ph * poly;
+    float e1, e2;
+    const float s1 = two_sum((float)e, t.y, &e1);
+    const float s2 = two_sum(s1, ph, &e2);
+    return make_float2(s2, ((e1 + e2) + t.z) + small);
+}
+
+// log2 of a positive integer weight as a float pair (shared table + series for the int16
+// range; FP64 above it)
+__device__ __forceinline__ float2 wlog2(const float4* stab, int w) {
+    if (w < kTab) return log2_pair(w, stab);
+    const double l = log2((double)w);
+    const float hi = (float)l;
+    return make_float2(hi, (float)(l - (double)hi));
 }
 
 __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
@@ -206,8 +228,8 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     unsigned* rowoff = (unsigned*)(srow + A.max_rows);      // [max_rows] record offsets
     unsigned* rowlen = rowoff + A.max_rows;                 // [max_rows] padded record counts
     __shared__ int s_flag, s_ok, s_mode, s_reanchor;
+    __shared__ float4 s_l2tab[256];
     __shared__ float s_res;
-    __shared__ double s_max;
     __shared__ unsigned s_maxlen;   // longest stage (records of two rows) of this stripe
 
     const int n = A.n;
@@ -227,6 +249,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     float* c_s = (float*)region;
     float* S_s = c_s + n;
 
+    for (int j = tid; j < 256; j += NT) s_l2tab[j] = log2_tab_entry(j);
     if (tid == 0) {
         for (int s = 0; s < MAXR; ++s) rel_cnt[s] = iss_cnt[s] = 0u;
         for (int s = 0; s < NRED; ++s) mbar_init(&mrow[s], NW);
@@ -325,57 +348,65 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
         unsigned* wcnt = (unsigned*)red;   // [NW] per-warp kept counts (scratch)
         size_t roff = 0;                   // records written so far (block-relative)
         bool overflow = false;
-        for (int q = 0; q < nrows; ++q) {
-            const int64_t row = r0 + q;
-            // reference C ~ max_j (p log2 w - V_j), FP32 estimate (only a scale)
-            float mloc = -INFINITY;
+        // the weights of row q + 1 are loaded while row q is evaluated
+        int wv[M], wn[M];
+        auto load_row = [&](int q, int* dst) {
 #pragma unroll
             for (int k = 0; k < CH; ++k) {
-                if (nval[k] == 0) continue;
-                int w[4];
-                load_w4(A, row, cidx[k] * 4, nval[k], w);
+                int w4[4] = {0, 0, 0, 0};
+                if (q < nrows && nval[k] > 0) load_w4(A, r0 + q, cidx[k] * 4, nval[k], w4);
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (e < nval[k] && w[e] > 0)
-                        mloc = fmaxf(mloc, fmaf(pf, lg2_approx((float)w[e]), -vsm[cidx[k] * 4 + e].x));
+                for (int e = 0; e < 4; ++e) dst[4 * k + e] = w4[e];
             }
+        };
+        load_row(0, wn);
+        for (int q = 0; q < nrows; ++q) {
+            const int64_t row = r0 + q;
+#pragma unroll
+            for (int x = 0; x < M; ++x) wv[x] = wn[x];
+            load_row(q + 1, wn);
+            // reference C ~ max_j (p log2 w - V_j), an FP32 estimate (only a scale; C itself
+            // enters the row potential exactly)
+            float mloc = -INFINITY;
+#pragma unroll
+            for (int x = 0; x < M; ++x)
+                if ((x % 4) < nval[x / 4] && wv[x] > 0)
+                    mloc = fmaxf(mloc, fmaf(pf, lg2_approx((float)wv[x]), -vsm[cidx[x / 4] * 4 + (x % 4)].x));
             mloc = warp_max(mloc);
-            if (lane == 0) redd[wid] = (double)mloc;
+            float* smx = (float*)redd;
+            if (lane == 0) smx[wid] = mloc;
             __syncthreads();
-            if (tid == 0) {
-                double m = -INFINITY;
-                for (int x = 0; x < NW; ++x) m = fmax(m, redd[x]);
-                if (!(m > -INFINITY)) { atomicCAS(A.err, 0, kErrNonfinite); m = 0.0; }
-                s_max = m;
-                crow[q] = m;
+            float mf = -INFINITY;
+#pragma unroll
+            for (int x = 0; x < NW; ++x) mf = fmaxf(mf, smx[x]);
+            if (!(mf > -INFINITY)) {
+                if (tid == 0) atomicCAS(A.err, 0, kErrNonfinite);
+                mf = 0.0f;
             }
-            __syncthreads();
-            const double m = s_max;
-            const float mh = (float)m, ml = (float)(m - (double)mh);
+            if (tid == 0) crow[q] = (double)mf;
+            __syncthreads();   // smx is rewritten by the next row
+            const float mh = mf, ml = 0.0f;
             float* krow = A.K + row * A.ldk;
             float kvs[M];
 #pragma unroll
             for (int k = 0; k < CH; ++k) {
                 float kv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                if (nval[k] > 0) {
-                    int w[4];
-                    load_w4(A, row, cidx[k] * 4, nval[k], w);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if (e < nval[k] && w[e] > 0) {
-                            // x = p log2 w - V_j - m with 48-bit operands: the large leading
-                            // parts cancel exactly (two-product, two-sums), the small ones are
-                            // added after; x is then exact to about 2^-24 |x|
-                            const float2 lw = wlog2(A.tab, w[e]);
-                            const float2 vj = vsm[cidx[k] * 4 + e];
-                            const float t = ph * lw.x;
-                            const float te = fmaf(ph, lw.x, -t);
-                            float e1, e2;
-                            const float s1 = two_sum(t, -vj.x, &e1);
-                            const float s2 = two_sum(s1, -mh, &e2);
-                            const float rest = ((te + e1) + e2) + (fmaf(ph, lw.y, pl * lw.x) - vj.y - ml);
-                            kv[e] = ex2_approx(s2 + rest);
-                        }
+                for (int e = 0; e < 4; ++e) {
+                    const int x = 4 * k + e;
+                    if (e < nval[k] && wv[x] > 0) {
+                        // x = p log2 w - V_j - m with 48-bit operands: the large leading
+                        // parts cancel exactly (two-product, two-sums), the small ones are
+                        // added after; x is then exact to about 2^-24 |x|
+                        const float2 lw = wlog2(s_l2tab, wv[x]);
+                        const float2 vj = vsm[cidx[k] * 4 + e];
+                        const float t = ph * lw.x;
+                        const float te = fmaf(ph, lw.x, -t);
+                        float e1, e2;
+                        const float s1 = two_sum(t, -vj.x, &e1);
+                        const float s2 = two_sum(s1, -mh, &e2);
+                        const float rest = ((te + e1) + e2) + (fmaf(ph, lw.y, pl * lw.x) - vj.y - ml);
+                        kv[e] = ex2_approx(s2 + rest);
                     }
                 }
                 if (cidx[k] < NC) *(float4*)(krow + cidx[k] * 4) = make_float4(kv[0], kv[1], kv[2], kv[3]);
@@ -770,7 +801,7 @@ size_t step_smem_bytes(int nt, size_t region_bytes, int max_rows) {
     const int fg = nt / 64;
     return region_bytes + 8 * (size_t)(kStepMaxRing + kStepNred) + 8 * (size_t)kStepMaxRing +
            4 * (size_t)(kStepNred * 2 * nw) +
-           8 * (size_t)(max_rows + fg * 64 + nw) + 4 * (size_t)max_rows + 8 * (size_t)max_rows + 1024;
+           8 * (size_t)(max_rows + fg * 64 + nw) + 4 * (size_t)max_rows + 8 * (size_t)max_rows + 4096 + 1024;
 }
 
 int step_max_rows(const sa_ctx* ctx, int n) {
@@ -857,7 +888,7 @@ size_t step_workspace_bytes(const sa_ctx* ctx, const sa_matrix* a, int n_p) {
     const int G_max = ctx->num_sms * 2;
     const size_t npad = align_up((size_t)n, 32);
     const size_t recs = ctx->step_sparse ? (size_t)n * step_rec_cap_row(n) : 2;
-    return (size_t)n * ldk * 4 + recs * 8 + (size_t)G_max * npad * 4 + (size_t)kTab * 8 +
+    return (size_t)n * ldk * 4 + recs * 8 + (size_t)G_max * npad * 4 +
            2 * align_up((size_t)n * 8, 256) + align_up((size_t)n * 4, 256) + (size_t)n_p * 16 + 32768;
 }
 
@@ -880,7 +911,6 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     const int64_t rec_cap_row = ctx->step_sparse ? step_rec_cap_row(n) : 0;
     uint2* rec = cv.take<uint2>(ctx->step_sparse ? (size_t)n * rec_cap_row : 2);
     float* part = cv.take<float>((size_t)G_max * npad);
-    float2* tab = cv.take<float2>(kTab);
     double* Vs = cv.take<double>(n);
     float* Cf = cv.take<float>(n);
     float* rmax = cv.take<float>(2);
@@ -892,8 +922,6 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     unsigned long long* stats = cv.take<unsigned long long>(8);
     unsigned* crange = cv.take<unsigned>(4);
     int* counters = cv.take<int>(2);
-    log2_table_kernel<<<kTab / 256, 256, 0, st>>>(tab);
-    count_launch();
     SA_CUDA(cudaMemcpyAsync(P, o->p, o->n_p * sizeof(double), cudaMemcpyHostToDevice, st));
     SA_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
     SA_CUDA(cudaMemsetAsync(rmax, 0, 2 * sizeof(float), st));
@@ -939,7 +967,6 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     // (the largest entry of K in a row is about 1): n * 2^-70 * 2^20 <= 2^-36 for n <= 2^14
     args.theta = 0x1p-70f;
     args.reanchor_ratio = 0x1p20f;
-    args.tab = tab;
     args.P = P;
     args.k0 = k0;
     args.n_p = o->n_p;
