@@ -253,6 +253,45 @@ typedef struct {
 sa_status sa_assign(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* opts, double t,
                     sa_assign_result* res);
 
+/* ---- Algorithm 1 with adaptive p (Sec. 4.2, Algorithm 1) ----------------------------- */
+
+/* Options of the preprocessing loop: prescale A to [1, e] (Sec. 4.1.1), then for
+ * p = p0, p0 + dp, ...: scale A^(p) to an eps-bistochastic X, prune B = {x_ij >= t}
+ * (Eq. matrixred), solve B exactly and evaluate gamma (Eq. optratio); stop at the first p
+ * with gamma <= opt_ratio.  p is on the prescaled scale; the raw-weight equivalent is
+ * p / log(max w / min w) when max/min > e (the identity X(A^(m)/c, p) = X(A, p m)). */
+typedef struct {
+    double opt_ratio;         /* required gamma, > 1 (the paper uses about 2) */
+    double p0;                /* first p (the paper: 100) */
+    double dp;                /* increase of p per round (the paper: 50) */
+    int32_t max_rounds;       /* SA_E_NOT_CONVERGED after this many rounds without success */
+    double eps;               /* eps of the eps-bistochastic stop; <= 0: 1/n (the paper's) */
+    double t;                 /* pruning threshold; <= 0: 1/n (the paper's) */
+    int32_t max_sweeps_per_p; /* cap of the scaling at each p */
+    sa_prec prec;
+    sa_kernel kernel;
+} sa_alg1_opts;
+
+typedef struct {
+    int32_t* perm;            /* caller-owned host int32[n]: an optimal permutation of the final B */
+    double sum_log_w;         /* sum_i log w_{i perm(i)} */
+    double gamma;             /* Eq. optratio at the final p (<= opt_ratio on success) */
+    double p_final;           /* final p on the prescaled scale */
+    double p_raw;             /* the same p applied to the raw weights */
+    int32_t rounds;           /* values of p tried */
+    int64_t sweeps_total;     /* scaling sweeps over all rounds */
+    int64_t nnz;              /* entries of the final B (row and column maxima always kept) */
+} sa_alg1_result;
+
+/*
+ * sa_algorithm1: the paper's preprocessing algorithm on a device matrix.  Each round
+ * warm-starts the scaling from the previous round's potentials (scaled by the ratio of the
+ * p values).  A round whose B holds no permutation counts as gamma = +inf.  Returns SA_OK
+ * with gamma <= opt_ratio, or SA_E_NOT_CONVERGED after max_rounds (res filled with the
+ * last round).  Unlike sa_assign the result is only certified to within gamma.
+ */
+sa_status sa_algorithm1(sa_ctx* ctx, const sa_matrix* a, const sa_alg1_opts* opts, sa_alg1_result* res);
+
 /*
  * sa_assign_host: sa_assign on a HOST matrix (n x ld weights): copies it into a
  * context-owned device buffer on the context stream first.  For end-to-end timing.

@@ -286,3 +286,51 @@ def preprocess(w, p_sched, tol=1e-6, max_sweeps=20000, t=None, guard=True):
     return {"u": u, "v": v, "sweeps": sw, "resid": rs, "status": st, "mask": mask,
             "perm": perm, "solve_status": st_h, "log_w_B": log_w_b, "log_ub": ub,
             "gamma": gamma(ub, log_w_b) if st_h == 0 else np.inf}
+
+
+def algorithm1(w, opt_ratio=2.0, p0=100.0, dp=50.0, max_rounds=20, eps=None, t=None, max_sweeps=20000,
+               guard=True):
+    """Algorithm 1 of the paper with adaptive p: prescale (Sec. 4.1.1), then for p = p0,
+    p0 + dp, ... scale to an eps-bistochastic X (eps = 1/n by default), prune at t (1/n),
+    solve B exactly and stop when gamma (Eq. optratio) <= opt_ratio.  p is on the prescaled
+    scale; the scaling runs on the raw log weights at p * m (the prescaling identity), with
+    each round warm-started from the last (potentials scaled by the ratio of the p values).
+
+    Returns a dict with perm, log_w_B, gamma, p_final, p_raw, rounds, sweeps, status
+    (0 success, 1 max_rounds reached)."""
+    b = log_weights(w)
+    n = b.shape[0]
+    wpos = np.asarray(w)[np.asarray(w) > 0]
+    ratio = float(wpos.max()) / float(wpos.min())
+    m = 1.0 / np.log(ratio) if ratio > np.e else 1.0
+    eps = 1.0 / n if eps is None else eps
+    t = 1.0 / n if t is None else t
+    u = v = None
+    p, p_prev = p0, None
+    sweeps = 0
+    out = None
+    for r in range(max_rounds):
+        p_raw = p * m
+        if u is None:
+            u, v, sw, rs, st = sinkhorn(b, [p_raw], eps, max_sweeps)
+            sweeps += int(sw.sum())
+        else:
+            f = p_raw / p_prev
+            u, v, sw, rs, st = sinkhorn_from(b, p_raw, u * f, v * f, eps, max_sweeps)
+            sweeps += sw
+        mask = prune_mask(b, p_raw, u, v, t, guard)
+        perm, al, be, st_h = hungarian(np.where(mask, b, -np.inf))
+        if st_h == 0:
+            log_w_b = float(sum(b[i, perm[i]] for i in range(n)))
+            g = gamma(log_ub(b, p_raw, v), log_w_b)
+        else:
+            log_w_b, g = -np.inf, np.inf
+        out = {"perm": perm, "log_w_B": log_w_b, "gamma": g, "p_final": p, "p_raw": p_raw, "rounds": r + 1,
+               "sweeps": sweeps, "nnz": int(mask.sum()), "status": 1}
+        if g <= opt_ratio:
+            out["status"] = 0
+            return out
+        p_prev = p_raw
+        p += dp
+    return out
+

@@ -63,6 +63,18 @@ class sa_assign_result(ctypes.Structure):
                 ("ms_solve", ctypes.c_double), ("ms_certify", ctypes.c_double)]
 
 
+class sa_alg1_opts(ctypes.Structure):
+    _fields_ = [("opt_ratio", ctypes.c_double), ("p0", ctypes.c_double), ("dp", ctypes.c_double),
+                ("max_rounds", ctypes.c_int32), ("eps", ctypes.c_double), ("t", ctypes.c_double),
+                ("max_sweeps_per_p", ctypes.c_int32), ("prec", ctypes.c_int), ("kernel", ctypes.c_int)]
+
+
+class sa_alg1_result(ctypes.Structure):
+    _fields_ = [("perm", ctypes.POINTER(ctypes.c_int32)), ("sum_log_w", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("p_final", ctypes.c_double), ("p_raw", ctypes.c_double), ("rounds", ctypes.c_int32),
+                ("sweeps_total", ctypes.c_int64), ("nnz", ctypes.c_int64)]
+
+
 class sa_result(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("perm", ctypes.POINTER(ctypes.c_int32)), ("sum_log_w", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("sweeps", ctypes.c_int64), ("status", ctypes.c_int32),
@@ -96,6 +108,8 @@ SIGNATURES = {
     "sa_assign_host": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int32, ctypes.c_int64,
                                       ctypes.POINTER(sa_scale_opts), ctypes.c_double,
                                       ctypes.POINTER(sa_assign_result)]),
+    "sa_algorithm1": (ctypes.c_int, [_VP, ctypes.POINTER(sa_matrix), ctypes.POINTER(sa_alg1_opts),
+                                     ctypes.POINTER(sa_alg1_result)]),
     "sa_narrow_i32_to_i16": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, ctypes.c_int64, ctypes.c_int32, _I64P]),
     "sa_batch_scale": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, ctypes.c_int,
                                       ctypes.POINTER(sa_scale_opts), _VP, _VP, _I32P, _I32P]),

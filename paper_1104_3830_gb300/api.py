@@ -193,6 +193,23 @@ def sa_assign(ctx: Context, w, p, tol=1e-6, max_sweeps=20000, prec="mixed", kern
     return _result_dict(r, perm)
 
 
+def sa_algorithm1(ctx: Context, w, opt_ratio=2.0, p0=100.0, dp=50.0, max_rounds=20, eps=0.0, t=0.0,
+                  max_sweeps=20000, prec="mixed", kernel="auto", allow_not_converged=False):
+    """The paper's preprocessing loop with adaptive p (prescaled scale); returns a dict."""
+    m = matrix(w)
+    n = w.size(0)
+    perm = np.full(n, -1, dtype=np.int32)
+    r = L.sa_alg1_result()
+    r.perm = perm.ctypes.data_as(L._I32P)
+    o = L.sa_alg1_opts(float(opt_ratio), float(p0), float(dp), int(max_rounds), float(eps), float(t), int(max_sweeps),
+                       L.PREC[prec], L.KERNEL[kernel])
+    st = lib().sa_algorithm1(ctx.handle, ctypes.byref(m), ctypes.byref(o), ctypes.byref(r))
+    if not (allow_not_converged and st == L.SA_E_NOT_CONVERGED):
+        check(st)
+    return {"status": st, "perm": perm, "sum_log_w": r.sum_log_w, "gamma": r.gamma, "p_final": r.p_final,
+            "p_raw": r.p_raw, "rounds": r.rounds, "sweeps_total": r.sweeps_total, "nnz": r.nnz}
+
+
 def sa_assign_host(ctx: Context, w_host: np.ndarray, p, tol=1e-6, max_sweeps=20000, prec="mixed", kernel="auto",
                    t=0.0):
     """sa_assign on a host (numpy, ideally pinned) matrix: the copy is part of the call."""

@@ -386,6 +386,79 @@ sa_status sa_assign(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, dou
     return SA_OK;
 }
 
+sa_status sa_algorithm1(sa_ctx* ctx, const sa_matrix* a, const sa_alg1_opts* o, sa_alg1_result* res) {
+    if (!ctx || !o || !res || !res->perm) { set_error("null context, options or result"); return SA_E_INVALID; }
+    sa_status rc = check_matrix(a);
+    if (rc) return rc;
+    if (!(o->opt_ratio > 1.0) || !(o->p0 > 0) || !(o->dp > 0) || o->max_rounds <= 0 || o->max_sweeps_per_p <= 0) {
+        set_error("algorithm 1 needs opt_ratio > 1, p0 > 0, dp > 0, max_rounds > 0 and max_sweeps_per_p > 0");
+        return SA_E_INVALID;
+    }
+    DeviceGuard g(ctx->device);
+    const int n = a->n;
+    int64_t wmin = 0, wmax = 0;
+    if ((rc = weights_minmax(ctx, a, &wmin, &wmax))) return rc;
+    // prescaling (Sec. 4.1.1): A^(m)/c has entries in [1, e]; X at p on that scale is X of A at p m
+    const double ratio = (double)wmax / (double)wmin;
+    const double m = ratio > std::exp(1.0) ? 1.0 / std::log(ratio) : 1.0;
+    const double eps = o->eps > 0 ? o->eps : 1.0 / n;
+    const double t = o->t > 0 ? o->t : 1.0 / n;
+    double* d_uv = nullptr;
+    SA_CUDA(cudaMallocAsync((void**)&d_uv, 2 * sizeof(double) * n, ctx->stream));
+    double* d_u = d_uv;
+    double* d_v = d_uv + n;
+    std::vector<double> alpha(n), beta(n);
+    std::vector<int32_t> perm(n);
+    res->rounds = 0;
+    res->sweeps_total = 0;
+    res->gamma = INFINITY;
+    double p = o->p0, p_prev_raw = 0.0;
+    sa_status out = SA_E_NOT_CONVERGED;
+    for (int r = 0; r < o->max_rounds; ++r, p += o->dp) {
+        const double p_raw = p * m;
+        double sched[2] = {p_prev_raw, p_raw};
+        sa_scale_opts so{};
+        so.p = r == 0 ? sched + 1 : sched;
+        so.n_p = r == 0 ? 1 : 2;
+        so.tol = eps;
+        so.max_sweeps_per_p = o->max_sweeps_per_p;
+        so.prec = o->prec;
+        so.kernel = o->kernel;
+        so.warm_keep_v = 0;
+        so.resume_from = r == 0 ? 0 : 1;   // warm start: (u, v) * p_raw / p_prev_raw
+        sa_scale_info info{};
+        rc = sa_scale(ctx, a, &so, d_u, d_v, &info);
+        if (rc != SA_OK && rc != SA_E_NOT_CONVERGED) { out = rc; break; }
+        res->sweeps_total += info.sweeps_total;
+        res->rounds = r + 1;
+        res->p_final = p;
+        res->p_raw = p_raw;
+        p_prev_raw = p_raw;
+        sa_csr B{};
+        double log_ub = 0.0;
+        rc = prune_device(ctx, a, p_raw, d_u, d_v, t, 1, &B, &log_ub);
+        if (rc) { out = rc; break; }
+        double sum = 0.0;
+        rc = solve_csr(B, perm.data(), &sum, alpha.data(), beta.data());
+        const int64_t nnz = B.nnz;
+        sa_csr_free(&B);
+        if (rc != SA_OK && rc != SA_E_NO_PERFECT_MATCHING) { out = rc; break; }
+        const double gam = rc == SA_OK ? std::exp(log_ub - sum) : INFINITY;
+        if (rc == SA_OK) {
+            std::copy(perm.begin(), perm.end(), res->perm);
+            res->sum_log_w = sum;
+            res->nnz = nnz;
+        }
+        res->gamma = gam;
+        if (gam <= o->opt_ratio) { out = SA_OK; break; }
+    }
+    cudaFreeAsync(d_uv, ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sa_algorithm1");
+    if (out == SA_E_NOT_CONVERGED) set_error("gamma above opt_ratio after %d rounds (last %g)", o->max_rounds, res->gamma);
+    return out;
+}
+
 sa_status sa_assign_host(sa_ctx* ctx, const void* host_w, sa_wtype wtype, int32_t n, int64_t ld,
                          const sa_scale_opts* o, double t, sa_assign_result* res) {
     if (!ctx || !host_w || n <= 0 || ld < n) { set_error("bad host matrix"); return SA_E_INVALID; }

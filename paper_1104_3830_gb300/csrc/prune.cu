@@ -313,6 +313,28 @@ __global__ void verify_cols_combine(int n, int nchunks, const double* part, doub
     err[j] = fabs(s - 1.0);
 }
 
+// smallest positive and largest weight of the matrix (zeros are absent entries)
+__global__ void minmax_kernel(const void* w, int i16, int n, int64_t ld, unsigned long long* out) {
+    unsigned mn = 0xffffffffu, mx = 0u;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)n * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        const int x = i16 ? (int)((const int16_t*)w)[(int64_t)i * ld + j] : ((const int32_t*)w)[(int64_t)i * ld + j];
+        if (x > 0) {
+            mn = min(mn, (unsigned)x);
+            mx = max(mx, (unsigned)x);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(out, (unsigned long long)mn);
+        atomicMax(out + 1, (unsigned long long)mx);
+    }
+}
+
 __global__ void max_reduce_kernel(const double* x, int n, double* out) {
     double m = 0.0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) m = fmax(m, x[k]);
@@ -524,6 +546,26 @@ sa_status verify_device(sa_ctx* ctx, const sa_matrix* a, double p, const double*
     SA_CUDA(cudaGetLastError());
     if (max_row_err) *max_row_err = h[0];
     if (max_col_err) *max_col_err = h[1];
+    return SA_OK;
+}
+
+sa_status weights_minmax(sa_ctx* ctx, const sa_matrix* a, int64_t* wmin, int64_t* wmax) {
+    cudaStream_t st = ctx->stream;
+    sa_status rc = ctx->ws.reserve(256);
+    if (rc) return rc;
+    unsigned long long* d = (unsigned long long*)ctx->ws.ptr;
+    const unsigned long long init[2] = {~0ull, 0ull};
+    SA_CUDA(cudaMemcpyAsync(d, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    const int64_t total = (int64_t)a->n * a->n;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 8);
+    minmax_kernel<<<blocks, 256, 0, st>>>(a->w, a->wtype == SA_I16, a->n, a->ld, d);
+    count_launch();
+    unsigned long long h[2];
+    SA_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaStreamSynchronize(st));
+    if (h[1] == 0ull) { set_error("matrix has no positive entry"); return SA_E_NO_PERFECT_MATCHING; }
+    *wmin = (int64_t)h[0];
+    *wmax = (int64_t)h[1];
     return SA_OK;
 }
 

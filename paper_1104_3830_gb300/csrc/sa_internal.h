@@ -120,6 +120,9 @@ sa_status verify_device(sa_ctx* ctx, const sa_matrix* a, double p, const double*
                         const double* d_v, double* d_rows, double* d_cols, double* max_row_err,
                         double* max_col_err);
 
+// smallest positive and largest weight (prune.cu)
+sa_status weights_minmax(sa_ctx* ctx, const sa_matrix* a, int64_t* wmin, int64_t* wmax);
+
 sa_status narrow_device(sa_ctx* ctx, const int32_t* src, int64_t lds, int16_t* dst, int64_t ldd,
                         int n, int64_t* n_bad);
 

@@ -292,3 +292,40 @@ def test_prune_threshold_and_guard():
     assert np.array_equal(mg, (x >= 0.9) | (x == x.max(axis=1, keepdims=True)) | (x == x.max(axis=0, keepdims=True)))
     rp, col = oracle.prune_csr(m)
     assert rp[-1] == m.sum() and all(np.array_equal(np.nonzero(m[i])[0], col[rp[i]:rp[i + 1]]) for i in range(50))
+
+
+# ---- Algorithm 1 with adaptive p (Sec. 4.2) -----------------------------------------
+
+def test_algorithm1_gamma_bounds_the_brute_force_optimum():
+    """On small instances the returned permutation of B is within the factor gamma of the
+    optimum of A found by enumeration (Prop. aoc), and gamma <= opt_ratio on success."""
+    for seed in range(4):
+        w = W.uniform(7, 1, 50, 700 + seed, dtype=np.int32)
+        r = oracle.algorithm1(w, opt_ratio=1.5, p0=5.0, dp=5.0, max_rounds=40, eps=1e-9)
+        assert r["status"] == 0 and r["gamma"] <= 1.5
+        b = oracle.log_weights(w.astype(np.int64))
+        perm_bf, best = oracle.bruteforce(b)[:2]
+        assert best - 1e-12 <= best
+        assert -1e-12 <= best - r["log_w_B"] <= np.log(r["gamma"]) + 1e-9
+        assert sorted(r["perm"]) == list(range(7))
+
+
+def test_algorithm1_planted_stops_in_one_round():
+    """A planted strict row maximum: the first p already isolates the plant, and the certified
+    ratio is within the requested bound (gamma tends to 1 only as p grows)."""
+    w, pi, _ = W.planted(64, W.BASE_SEED + 90)
+    r = oracle.algorithm1(w, opt_ratio=2.0)
+    assert r["status"] == 0 and r["rounds"] == 1
+    assert np.array_equal(r["perm"], pi)
+    assert 1.0 <= r["gamma"] <= 2.0
+
+
+def test_algorithm1_prescaling_scale():
+    """p is on the prescaled scale: p_raw = p / ln(max/min) when max/min > e, p otherwise."""
+    w = W.uniform(16, 1, 1000, 91, dtype=np.int32)
+    r = oracle.algorithm1(w, opt_ratio=1e9, p0=100.0)
+    ratio = w.max() / w[w > 0].min()
+    assert abs(r["p_raw"] - 100.0 / np.log(ratio)) < 1e-12
+    w2 = (np.ones((16, 16)) * 2 + np.eye(16)).astype(np.int32)   # max/min = 1.5 < e
+    r2 = oracle.algorithm1(w2, opt_ratio=1e9, p0=100.0)
+    assert r2["p_raw"] == 100.0
