@@ -50,17 +50,12 @@ def load_peaks():
 # capture was taken on: after any change to these files the figure is unknown (null).
 _TRAFFIC = {
     # step kernel: planted n=8192 int16, p=256 from a cold start, 200 sweeps + 1 evaluation of K
-    (3, 8192, 2): (55.159e9 / 200, "ncu capture, planted n=8192 int16, p=256, 200 sweeps (one launch)",
+    (3, 8192, 2): (55.163e9 / 200, "ncu capture, planted n=8192 int16, p=256, 200 sweeps (one launch)",
                    {"paper_1104_3830_gb300/csrc/sweep_step.cu":
-                    "3fe7148797c47861dcc7c301468f1403e404f6aba7f238e973c4eedcdd7f097f",
+                    "1c881b89f5f8b2e693d096369ebd91441a13d7e1cc5b79d7fbfecff60f3e44a9",
                     "paper_1104_3830_gb300/csrc/common.cuh":
-                    "79cb5c1e43464590274462aa3183e66801bebb3f3d089a1451133303777195fd"}),
+                    "a6671f98cbd36384cd1797923d09a590dde55eb3479341ec323ebc1b9836442c"}),
 }
-
-
-KERNEL_NAMES = {1: "fused_kernel (single-read persistent sweep, SFU exp2/log2 per element)",
-                2: "row_lse_kernel + col_partial_kernel (plain sweep, host loop)",
-                3: "step_kernel (persistent sweep over the per-step FP32 matrix)"}
 
 
 def measured_traffic(kernel_used, n, wbytes):
