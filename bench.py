@@ -58,6 +58,11 @@ _TRAFFIC = {
 }
 
 
+KERNEL_NAMES = {1: "fused_kernel (single-read persistent sweep, SFU exp2/log2 per element)",
+                2: "row_lse_kernel + col_partial_kernel (plain sweep, host loop)",
+                3: "step_kernel (persistent sweep over the per-step FP32 matrix)"}
+
+
 def measured_traffic(kernel_used, n, wbytes):
     """(bytes per sweep, source) if a capture of this kernel source and size exists."""
     import hashlib

@@ -1,0 +1,40 @@
+"""Host-side pieces of bench.py (no GPU): the module imports, every name the JSON line
+uses is defined, the traffic table is consistent, and the workloads have the stated
+shapes."""
+import importlib.util
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    argv = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        spec.loader.exec_module(mod)
+    finally:
+        sys.argv = argv
+    return mod
+
+
+def test_bench_names_and_tables():
+    b = _bench()
+    assert set(b.KERNEL_NAMES) == {1, 2, 3}
+    per_sweep, src = b.measured_traffic(3, 8192, 2)
+    # either the capture matches the current kernel source or the figure is withheld
+    assert (per_sweep is None and src is None) or (per_sweep > 268e6 and "ncu" in src)
+    assert b.measured_traffic(1, 12345, 2) == (None, None)
+    assert b.load_peaks()[0] > 0
+
+
+def test_bench_workload_shapes():
+    b = _bench()
+    w, ps, cfg = b.workload("uniform256")
+    assert w.shape == (256, 256) and w.dtype == np.int32 and ps[-1] == 256.0 and "workload" in cfg
+    w, ps, cfg = b.workload("small")
+    assert w.shape == (2048, 2048) and w.dtype == np.int16
