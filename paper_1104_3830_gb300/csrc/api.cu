@@ -197,6 +197,7 @@ sa_status sa_create(sa_ctx** ctx, int device, void* cuda_stream) {
         if (v == 256 || v == 512) c->fused_nt = v;
     }
     if (const char* e = getenv("SA_STEP_SPARSE")) c->step_sparse = atoi(e) != 0;
+    if (const char* e = getenv("SA_MAX_GRID")) c->max_grid = std::max(0, atoi(e));
     if (!prop.cooperativeLaunch) { delete c; set_error("device lacks cooperative launch"); return SA_E_UNSUPPORTED; }
     *ctx = c;
     return SA_OK;

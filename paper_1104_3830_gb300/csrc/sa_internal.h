@@ -58,7 +58,8 @@ struct sa_ctx {
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     size_t smem_optin = 0;
-    int max_grid = 0;        // cap on the fused kernel's grid (0: all SMs); set by the server
+    int max_grid = 0;        // cap on the persistent kernels' grid (0: all SMs); set by the
+                             // server, or SA_MAX_GRID in the environment
     int fused_nt = 512;      // threads per block of the fused kernel when 512 < chunks <= 1024
                              // (256 or 512; SA_FUSED_NT in the environment overrides)
     int step_sparse = 0;     // step kernel: allow sparse epochs (SA_STEP_SPARSE=1 enables)
