@@ -145,11 +145,11 @@ static sa_status csr_union(const sa_csr& a, const sa_csr& b, sa_csr* out) {
 }
 
 static sa_status solve_csr(const sa_csr& b, int32_t* perm, double* sum_log_w, double* alpha,
-                           double* beta) {
+                           double* beta, const double* price0 = nullptr) {
     std::vector<double> lw((size_t)std::max<int64_t>(b.nnz, 1));
     for (int64_t e = 0; e < b.nnz; ++e)
         lw[e] = b.w[e] > 0 ? std::log((double)b.w[e]) : -std::numeric_limits<double>::infinity();
-    sa_status rc = sparse_assign(b.n, b.row_ptr, b.col, lw.data(), perm, alpha, beta);
+    sa_status rc = sparse_assign(b.n, b.row_ptr, b.col, lw.data(), perm, alpha, beta, price0);
     if (rc) return rc;
     if (sum_log_w) {
         double s = 0.0;
@@ -329,6 +329,11 @@ sa_status sa_assign(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, dou
     sa_csr B{};
     double log_ub = 0.0;
     std::vector<double> alpha(n), beta(n);
+    // starting prices of the exact solve: -v/p (natural log), dual feasible since x <= 1
+    std::vector<double> price(n);
+    SA_CUDA(cudaMemcpyAsync(price.data(), d_v, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    SA_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int j = 0; j < n; ++j) price[j] = -price[j] / p;
     res->reprunes = 0;
     res->repairs = 0;
     res->ms_prune = res->ms_solve = res->ms_certify = 0.0;
@@ -342,7 +347,7 @@ sa_status sa_assign(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, dou
         res->ms_prune += a1 - a0;
         if (rc) { cudaFreeAsync(d_uv, ctx->stream); return rc; }
         if (!have_first) res->nnz_first = B.nnz;
-        rc = solve_csr(B, res->perm, &res->sum_log_w, alpha.data(), beta.data());
+        rc = solve_csr(B, res->perm, &res->sum_log_w, alpha.data(), beta.data(), price.data());
         res->ms_solve += now_ms() - a1;
         if (rc == SA_OK) break;
         sa_csr_free(&B);
@@ -374,7 +379,8 @@ sa_status sa_assign(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, dou
         B = merged;
         res->repairs++;
         double s0 = now_ms();
-        rc = solve_csr(B, res->perm, &res->sum_log_w, alpha.data(), beta.data());
+        for (int j = 0; j < n; ++j) price[j] = -beta[j];   // the last optimal duals
+        rc = solve_csr(B, res->perm, &res->sum_log_w, alpha.data(), beta.data(), price.data());
         res->ms_solve += now_ms() - s0;
         if (rc) { sa_csr_free(&B); cudaFreeAsync(d_uv, ctx->stream); return rc; }
         if (iter > 64) { set_error("duality repair did not settle"); sa_csr_free(&B); cudaFreeAsync(d_uv, ctx->stream); return SA_E_NOT_CONVERGED; }
@@ -440,7 +446,11 @@ sa_status sa_algorithm1(sa_ctx* ctx, const sa_matrix* a, const sa_alg1_opts* o, 
         rc = prune_device(ctx, a, p_raw, d_u, d_v, t, 1, &B, &log_ub);
         if (rc) { out = rc; break; }
         double sum = 0.0;
-        rc = solve_csr(B, perm.data(), &sum, alpha.data(), beta.data());
+        std::vector<double> price(n);   // warm start: -v/p of this round's scaling
+        SA_CUDA(cudaMemcpyAsync(price.data(), d_v, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+        SA_CUDA(cudaStreamSynchronize(ctx->stream));
+        for (int j = 0; j < n; ++j) price[j] = -price[j] / p_raw;
+        rc = solve_csr(B, perm.data(), &sum, alpha.data(), beta.data(), price.data());
         const int64_t nnz = B.nnz;
         sa_csr_free(&B);
         if (rc != SA_OK && rc != SA_E_NO_PERFECT_MATCHING) { out = rc; break; }

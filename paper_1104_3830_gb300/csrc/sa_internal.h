@@ -129,9 +129,10 @@ sa_status narrow_device(sa_ctx* ctx, const int32_t* src, int64_t lds, int16_t* d
 
 // ---- host exact solver (solve.cpp) ----------------------------------------------------
 // Max sum of logw over perfect matchings of a CSR bipartite graph (rows -> cols).
+// price0 (may be null): starting column prices of the minimisation form (-beta_j).
 // Returns SA_OK / SA_E_NO_PERFECT_MATCHING.
 sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const double* logw,
-                        int32_t* perm, double* alpha, double* beta);
+                        int32_t* perm, double* alpha, double* beta, const double* price0 = nullptr);
 
 // csr helpers (api.cu)
 sa_status csr_alloc(sa_csr* c, int n, int64_t nnz);

@@ -3,8 +3,11 @@
 //
 // Minimisation form: cost c_e = -log w_e on each kept entry.  Column prices v_j are kept
 // such that every assigned row i sits on a column of least reduced cost c_ij - v_j
-// (Jonker-Volgenant invariant).  Start: v_j = min_i c_ij and a greedy assignment on
-// zero-reduced-cost entries.  Each free row then runs Dijkstra over columns with a binary
+// (Jonker-Volgenant invariant).  Start: v_j = min_i c_ij, or caller-supplied prices (any
+// prices keep the invariant once every row takes its least-reduced-cost column; near
+// optimal ones -- the scaling's -v/p, dual feasible because x_ij(p) <= 1 -- leave few
+// conflicts and short augmenting paths), and a greedy assignment on each row's
+// least-reduced-cost column.  Each free row then runs Dijkstra over columns with a binary
 // heap until it reaches a free column; the prices of the columns finalised before the
 // target are lowered by (d_target - d_j) and the path is flipped.  At the end
 // u_i = c_{i,sigma(i)} - v_{sigma(i)} and (alpha, beta) = (-u, -v) are optimal LP duals
@@ -20,7 +23,7 @@
 namespace sa {
 
 sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const double* logw,
-                        int32_t* perm, double* alpha, double* beta) {
+                        int32_t* perm, double* alpha, double* beta, const double* price0) {
     const double INF = std::numeric_limits<double>::infinity();
     std::vector<double> v(n, INF);
     for (int i = 0; i < n; ++i)
@@ -34,6 +37,9 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
             set_error("reduced instance: column %d has no allowed entry", j);
             return SA_E_NO_PERFECT_MATCHING;
         }
+    if (price0)
+        for (int j = 0; j < n; ++j)
+            if (std::isfinite(price0[j])) v[j] = price0[j];
     std::vector<int32_t> rmatch(n, -1), cmatch(n, -1);
     // greedy assignment on least-reduced-cost columns
     for (int i = 0; i < n; ++i) {
@@ -49,6 +55,52 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
             return SA_E_NO_PERFECT_MATCHING;
         }
         if (cmatch[bj] < 0) { cmatch[bj] = i; rmatch[i] = bj; }
+    }
+    // Augmenting row reduction (Jonker and Volgenant, 1987): a free row takes its least
+    // reduced-cost column j1; when that is strictly below the second least, the price of j1
+    // drops by the difference, so j1 stays the row's least after the change and the row
+    // displaced from j1 (if any) is tried next.  Prices only drop, which keeps every
+    // assigned row on a least-reduced-cost column.  Two passes, each bounded in work.
+    {
+        std::vector<int32_t> freel;
+        for (int pass = 0; pass < 2; ++pass) {
+            freel.clear();
+            for (int i = 0; i < n; ++i)
+                if (rmatch[i] < 0) freel.push_back(i);
+            size_t k = 0;
+            int64_t budget = 8 * (int64_t)n + 64;
+            while (k < freel.size() && budget-- > 0) {
+                const int i = freel[k++];
+                double u1 = INF, u2 = INF;
+                int j1 = -1, j2 = -1;
+                for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                    if (!(logw[e] > -INF)) continue;
+                    const int j = col[e];
+                    const double h = -logw[e] - v[j];
+                    if (h < u1) {
+                        u2 = u1; j2 = j1;
+                        u1 = h; j1 = j;
+                    } else if (h < u2) {
+                        u2 = h; j2 = j;
+                    }
+                }
+                if (j1 < 0) break;   // no allowed entry: reported by the search below
+                int i0 = cmatch[j1];
+                if (u1 < u2) {
+                    if (j2 >= 0) v[j1] -= u2 - u1;
+                } else if (i0 >= 0 && j2 >= 0) {
+                    j1 = j2;   // tie: take the second column instead of displacing
+                    i0 = cmatch[j1];
+                }
+                if (i0 >= 0) {
+                    rmatch[i0] = -1;
+                    if (u1 < u2 && k > 0) freel[--k] = i0;   // try the displaced row at once
+                    else freel.push_back(i0);
+                }
+                cmatch[j1] = i;
+                rmatch[i] = j1;
+            }
+        }
     }
     std::vector<double> dist(n, INF);
     std::vector<int32_t> pred(n, -1), stamp(n, -1), done(n, -1), scanned;

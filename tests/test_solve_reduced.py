@@ -16,7 +16,10 @@ def _csr(mask, w):
 
 
 @pytest.mark.parametrize("n,density,hi", [(1, 1.0, 5), (2, 1.0, 9), (7, 1.0, 1000), (40, 0.15, 1000),
-                                          (200, 0.05, 30000), (300, 1.0, 1000), (257, 0.02, 7)])
+                                          (200, 0.05, 30000), (300, 1.0, 1000), (257, 0.02, 7),
+                                          # many ties (the row reduction's tie rule) and a single
+                                          # allowed entry per row beside the permutation
+                                          (150, 0.3, 2), (120, 0.01, 3), (400, 0.5, 4)])
 def test_matches_oracle(n, density, hi):
     rng = np.random.default_rng(n * 7 + hi)
     w = rng.integers(1, hi + 1, size=(n, n)).astype(np.int64)
