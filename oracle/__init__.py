@@ -20,6 +20,9 @@ Every function follows a passage of Sharify, Gaubert and Grigori, arXiv:1104.383
                           exhaustive search for n <= 10
 * :func:`dual_violations` LP-duality optimality check for (alpha, beta)
 * :func:`preprocess`      Algorithm 1 with a fixed p schedule: scale, prune, solve B
+* :func:`algorithm1`      Algorithm 1 with the adaptive p of Sec. 5 (gamma <= opt_ratio)
+* :func:`newton`          the Newton scaling of Sec. 5.3 (Knight-Ruiz iteration on the
+                          symmetric embedding of A^(p)), dense FP64 solves
 
 Parity pins live in ``tests/test_oracle_*.py``.  Nothing is "parity unpinned" except
 the paper's Tables 1-3 and the printed digits of the 5x5 X(50), whose inputs are not
@@ -334,3 +337,68 @@ def algorithm1(w, opt_ratio=2.0, p0=100.0, dp=50.0, max_rounds=20, eps=None, t=N
         p += dp
     return out
 
+
+
+def newton(b, p, tol=1e-12, max_newton=200, delta=0.1):
+    """Diagonal scaling of A^(p) by Newton iteration (Sec. 5.3, after Knight and Ruiz).
+
+    The nonsymmetric A^(p) enters through its symmetric embedding S = [[0, A], [A^T, 0]];
+    the scaling x = (x_r, x_c) > 0 solves f(x) = D(x) S x - 1 = 0, and Newton's method
+    on f reads A_k x_{k+1} = S x_k + D(x_k)^{-1} 1 with A_k = S + D(x_k)^{-1} D(S x_k).
+    Each A_k is singular along the scaling gauge (x_r t, x_c / t) but the system is
+    consistent, so it is solved densely by least squares (numpy) after the change of
+    variables x_{k+1} = D(x_k) y that makes it symmetric.  The iteration starts from the
+    max-normalised point (rows, then columns, divided by their largest entry).  A step
+    whose new
+    x_{k+1} / x_k falls below delta anywhere is shortened so that its smallest ratio is
+    delta (keeps x positive; the paper defers such safeguards to Knight and Ruiz).
+
+    A^(p) is formed explicitly, scaled by exp(-p max b): this is the paper's remark that
+    a non-logarithmic scaling needs p (b_max - b_min) within the exponent range of the
+    arithmetic (Sec. 4.1.1); beyond 700 this raises ValueError.
+
+    Returns (u, v, iterations, residuals, status) with x_ij = exp(p b_ij - u_i - v_j);
+    residuals[k] = max |f(x_k)| (rows and columns); status 0 converged, 1 not.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    n = b.shape[0]
+    fin = np.isfinite(b)
+    bmax, bmin = float(b[fin].max()), float(b[fin].min())
+    if p * (bmax - bmin) > 700.0:
+        raise ValueError("p (b_max - b_min) > 700: A^(p) leaves the FP64 range")
+    shift = p * bmax
+    with np.errstate(invalid="ignore"):
+        a = np.where(fin, np.exp(p * b - shift), 0.0)
+    s = np.zeros((2 * n, 2 * n))
+    s[:n, n:] = a
+    s[n:, :n] = a.T
+    # starting point: rows, then columns, divided by their largest entry (a diagonal
+    # scaling, so X(p) is unchanged); from x = 1 the Newton systems of a wide-range
+    # A^(p) are numerically singular and the damped steps stall
+    x = np.ones(2 * n)
+    x[:n] = 1.0 / a.max(axis=1)
+    x[n:] = 1.0 / (x[:n, None] * a).max(axis=0)
+    res = []
+    status = 1
+    for k in range(max_newton + 1):
+        sx = s @ x
+        f = x * sx - 1.0
+        res.append(float(np.max(np.abs(f))))
+        if res[-1] <= tol:
+            status = 0
+            break
+        if k == max_newton:
+            break
+        # the same equation multiplied by D(x_k) on the left, in y = x_{k+1} / x_k:
+        # (D(x_k) S D(x_k) + D(v)) y = v + 1 with v = D(x_k) S x_k, which is symmetric
+        # and well scaled whatever the spread of x_k
+        vk = x * sx
+        mk = x[:, None] * s * x[None, :] + np.diag(vk)
+        y = np.linalg.lstsq(mk, vk + 1.0, rcond=None)[0]
+        if y.min() < delta:
+            tau = (1.0 - delta) / (1.0 - y.min())
+            y = 1.0 + tau * (y - 1.0)
+        x = x * y
+    u = shift - np.log(x[:n])
+    v = -np.log(x[n:])
+    return u, v, len(res) - 1, np.array(res), status
