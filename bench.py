@@ -60,7 +60,8 @@ _TRAFFIC = {
 
 KERNEL_NAMES = {1: "fused_kernel (single-read persistent sweep, SFU exp2/log2 per element)",
                 2: "row_lse_kernel + col_partial_kernel (plain sweep, host loop)",
-                3: "step_kernel (persistent sweep over the per-step FP32 matrix)"}
+                3: "step_kernel (persistent sweep over the per-step FP32 matrix)",
+                4: "nt_matvec_kernel + nt_fin_kernel + nt_upd_kernel (Newton-CG, one read of K per operator application)"}
 
 
 def measured_traffic(kernel_used, n, wbytes):
@@ -462,7 +463,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="planted8192")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "step", "fused", "plain"],
+    ap.add_argument("--kernel", default="auto", choices=["auto", "step", "fused", "plain", "newton"],
                     help="sweep implementation of sa_scale (auto: the library's choice)")
     ap.add_argument("--max-sweeps", type=int, default=20000)
     ap.add_argument("--batch-count", type=int, default=4096)

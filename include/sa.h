@@ -73,9 +73,17 @@ typedef enum { SA_PREC_MIXED = 0, SA_PREC_FP32 = 1, SA_PREC_FP64 = 2 } sa_prec;
  *   (4 bytes per element): no per-element SFU work in the sweeps and an error that does
  *   not grow with p.  Needs n <= 24576 (above 12288 the rows are read from global
  *   memory, prefetched into L2, instead of through the shared-memory ring).
+ * NEWTON: the Newton variant of Sec. 5.3 (Knight-Ruiz iteration on the symmetric
+ *   embedding S = [[0, A], [A^T, 0]], conjugate gradients for each Newton system).  At
+ *   every p step it evaluates the same K as STEP, then iterates on K; each CG iteration
+ *   and each residual check reads K once.  sweeps_total counts these operator
+ *   applications (the paper's "No.it." of Tables 2-3), and the stop test is
+ *   max(|row sum - 1|, |column sum - 1|) <= tol over rows and columns.  SA_PREC_MIXED
+ *   only; same layout needs as STEP; never chosen by AUTO.
  * AUTO: STEP for SA_PREC_MIXED when it applies, else FUSED when it applies, else PLAIN;
  *   PLAIN for SA_PREC_FP64. */
-typedef enum { SA_KERNEL_AUTO = 0, SA_KERNEL_FUSED = 1, SA_KERNEL_PLAIN = 2, SA_KERNEL_STEP = 3 } sa_kernel;
+typedef enum { SA_KERNEL_AUTO = 0, SA_KERNEL_FUSED = 1, SA_KERNEL_PLAIN = 2, SA_KERNEL_STEP = 3,
+               SA_KERNEL_NEWTON = 4 } sa_kernel;
 
 /* A device matrix: w points to n rows of ld weights of type wtype. */
 typedef struct {

@@ -21,7 +21,7 @@ SA_E_INVALID, SA_E_NOMEM, SA_E_CUDA, SA_E_NOT_CONVERGED = -1, -2, -3, -4
 SA_E_NO_PERFECT_MATCHING, SA_E_NONFINITE, SA_E_BUDGET, SA_E_TIMEOUT, SA_E_UNSUPPORTED = -5, -6, -7, -8, -9
 SA_I16, SA_I32 = 0, 1
 PREC = {"mixed": 0, "fp32": 1, "fp64": 2}
-KERNEL = {"auto": 0, "fused": 1, "plain": 2, "step": 3}
+KERNEL = {"auto": 0, "fused": 1, "plain": 2, "step": 3, "newton": 4}
 STATUS_NAMES = {0: "SA_OK", 1: "SA_PENDING", -1: "SA_E_INVALID", -2: "SA_E_NOMEM", -3: "SA_E_CUDA",
                 -4: "SA_E_NOT_CONVERGED", -5: "SA_E_NO_PERFECT_MATCHING", -6: "SA_E_NONFINITE",
                 -7: "SA_E_BUDGET", -8: "SA_E_TIMEOUT", -9: "SA_E_UNSUPPORTED"}

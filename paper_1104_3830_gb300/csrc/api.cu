@@ -105,7 +105,7 @@ static sa_status check_opts(const sa_scale_opts* o) {
     if (o->max_sweeps_per_p <= 0) { set_error("max_sweeps_per_p must be > 0"); return SA_E_INVALID; }
     if (o->resume_from < 0 || o->resume_from >= o->n_p) { set_error("resume_from out of range"); return SA_E_INVALID; }
     if (o->prec < SA_PREC_MIXED || o->prec > SA_PREC_FP64) { set_error("unknown precision"); return SA_E_INVALID; }
-    if (o->kernel < SA_KERNEL_AUTO || o->kernel > SA_KERNEL_STEP) { set_error("unknown kernel"); return SA_E_INVALID; }
+    if (o->kernel < SA_KERNEL_AUTO || o->kernel > SA_KERNEL_NEWTON) { set_error("unknown kernel"); return SA_E_INVALID; }
     return SA_OK;
 }
 
@@ -242,7 +242,12 @@ sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, doub
         set_error("step kernel needs SA_PREC_MIXED, a 16-byte aligned base, ld*sizeof(w) %% 16 == 0 and n <= 24576");
         return SA_E_UNSUPPORTED;
     }
-    if (kind == SA_KERNEL_STEP) rc = scale_step(ctx, a, o, d_u, d_v, info);
+    if (kind == SA_KERNEL_NEWTON && (o->prec != SA_PREC_MIXED || !newton_supported(ctx, a))) {
+        set_error("newton kernel needs SA_PREC_MIXED, a 16-byte aligned base and ld*sizeof(w) %% 16 == 0");
+        return SA_E_UNSUPPORTED;
+    }
+    if (kind == SA_KERNEL_NEWTON) rc = scale_newton(ctx, a, o, d_u, d_v, info);
+    else if (kind == SA_KERNEL_STEP) rc = scale_step(ctx, a, o, d_u, d_v, info);
     else if (kind == SA_KERNEL_FUSED) rc = scale_fused(ctx, a, o, d_u, d_v, info);
     else rc = scale_plain(ctx, a, o, d_u, d_v, info);
     if (rc == SA_OK || rc == SA_E_NOT_CONVERGED) {

@@ -105,6 +105,10 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
                      double* V, sa_scale_info* info);
 bool step_supported(const sa_ctx* ctx, const sa_matrix* a);
 size_t fused_workspace_bytes(const sa_ctx* ctx, const sa_matrix* a);
+// newton.cu: Newton scaling of Sec. 5.3 on the per-step matrix (SA_KERNEL_NEWTON)
+sa_status scale_newton(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double* U,
+                       double* V, sa_scale_info* info);
+bool newton_supported(const sa_ctx* ctx, const sa_matrix* a);
 
 // natural <-> log2 units, in place on the device (n doubles), y = x * f
 void launch_scale_vec(double* x, int n, double f, cudaStream_t s);

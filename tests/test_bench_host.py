@@ -24,7 +24,7 @@ def _bench():
 
 def test_bench_names_and_tables():
     b = _bench()
-    assert set(b.KERNEL_NAMES) == {1, 2, 3}
+    assert set(b.KERNEL_NAMES) == {1, 2, 3, 4}
     per_sweep, src = b.measured_traffic(3, 8192, 2)
     # either the capture matches the current kernel source or the figure is withheld
     assert (per_sweep is None and src is None) or (per_sweep > 268e6 and "ncu" in src)

@@ -29,7 +29,8 @@ def ctx():
 # opt_ratio sits between the gamma values of two consecutive rounds (several percent
 # apart), so both sides stop at the same round despite their different arithmetic
 @pytest.mark.parametrize("n,seed,kernel,ratio,rounds", [(64, 1, "step", 1.6, 6), (128, 2, "step", 2.0, 8),
-                                                         (200, 3, "fused", 2.04, 13), (96, 4, "plain", 1.95, 6)])
+                                                         (200, 3, "fused", 2.04, 13), (96, 4, "plain", 1.95, 6),
+                                                         (64, 1, "newton", 1.6, 6), (128, 2, "newton", 2.0, 8)])
 def test_matches_oracle_with_tight_eps(ctx, n, seed, kernel, ratio, rounds):
     w = W.uniform(n, 1, 1000, 1200 + seed, dtype=np.int32)
     d = api.to_device(w)
