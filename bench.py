@@ -549,7 +549,7 @@ def main():
     used = res["scale"].get("kernel_used")
     alg_bytes = sweeps_per_step * n * n * w.dtype.itemsize
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
-    read_per_sweep = (n * ((n + 3) // 4 * 4) * 4) if used == 3 else (n * n * w.dtype.itemsize * (2 if used == 2 else 1))
+    read_per_sweep = (n * ((n + 3) // 4 * 4) * 4) if used in (3, 4) else (n * n * w.dtype.itemsize * (2 if used == 2 else 1))
     traffic, tsrc = measured_traffic(used, n, w.dtype.itemsize)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic * sweeps_per_step if traffic else None,

@@ -2,9 +2,10 @@
 // Knight and Ruiz), the SA_KERNEL_NEWTON path of sa_scale.
 //
 // At every p of the schedule:
-//  1. K_ij = 2^(p log2 w_ij - C_i - V_j) with C_i = max_j (p log2 w_ij - V_j): the exponent
-//     in FP64 (exact log2 table for int16 weights), one FP32 rounding, written once as an
-//     n x ldk FP32 matrix.  X(p) is invariant under diagonal scaling (Sec. 2.1), so
+//  1. K_ij = 2^(p log2 w_ij - C_i - V_j) with C_i ~ max_j (p log2 w_ij - V_j) (any C_i keeps
+//     X; this one keeps K <= ~1): the exponent in float-pair arithmetic (exact two-product
+//     and two-sums, log2 w to about 2^-40), then one FP32 exp2, written once as an n x ldk
+//     FP32 matrix.  X(p) is invariant under diagonal scaling (Sec. 2.1), so
 //     scaling K or A^(p) gives the same X(p), and K has no range limit in p (A^(p) itself
 //     needs p (b_max - b_min) within the exponent range, Sec. 4.1.1).  V is the previous
 //     step's column potential (warm start).
@@ -20,12 +21,13 @@
 //     maximum 1) and kappa_j = 1 / max_i K_ij.  A CG step that leaves min y < 0.1 ends
 //     the inner solve and the Newton step is shortened to min y = 0.1.
 //
-// Control runs on the device.  A step is three launches: the matvec (one read of K),
-// the finalisation (column sums, v or w, one reduction) and the vector update (second
-// reduction).  The last block of the finalisation and of the update takes the scalar
-// decisions in a control block that the next launch reads; once the step converges every
-// launch returns at once.  The host queues batches of steps and polls the control block
-// between batches; no kernel waits on another block.
+// The whole Newton-CG iteration of a p step is one persistent cooperative kernel.  A step
+// of it is: the matvec (one read of K), grid barrier, the finalisation of each block's
+// slice of the 2n entries (column sums over the stripes, row sums over the tiles; v or w;
+// one set of block partials), grid barrier, then every block reduces all partials in the
+// same order and so takes the same decisions; a CG step then updates the block's slice
+// (second set of partials, third barrier).  Every barrier wait is bounded (2 s) and ends
+// the kernel with an error code.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -33,6 +35,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "log2pair.cuh"
 #include "sa_internal.h"
 
 namespace sa {
@@ -41,28 +44,37 @@ namespace {
 
 constexpr int kNtThreads = 256;
 constexpr int kNtWarps = kNtThreads / 32;
-constexpr int kNtBatch = 8;          // steps queued between polls of the control block
 constexpr double kNtDelta = 0.1;     // smallest y kept by a Newton step
 constexpr double kNtEtaMax = 0.1;    // forcing term of the inner solve: eta = sqrt(res),
 constexpr double kNtEtaMin = 1e-3;   //   clamped to [kNtEtaMin, kNtEtaMax]
 constexpr int kNtCgCap = 200;        // CG iterations per Newton step
+constexpr int kNtStages = 6;         // cp.async pipeline depth of the matvec (rows in flight)
+constexpr int kNtMaxSmem = 200 * 1024;
 
 enum : int { kNtRes = 0, kNtCg = 1, kNtDone = 2 };
 enum : int { kNtRunning = 0, kNtConverged = 1, kNtCapped = 2, kNtNonfinite = 3 };
 
-struct NtCtl {
-    int mode;        // kNtRes: next matvec is of 1 (residual); kNtCg: of r; kNtDone
-    int cstage;      // 1: the update kernel applies a CG step
+// Scalar state of the iteration; every block holds an identical copy in shared memory.
+struct NtState {
+    int mode;        // kNtRes: the next matvec is of 1 (residual); kNtCg: of r; kNtDone
+    int cstage;      // 1: this step applies a CG update
     int first;       // first CG iteration of the Newton step (beta = 0)
-    int apply;       // pending x <- x o (1 + tau (y - 1)), applied by the next matvec step
+    int apply;       // pending x <- x o (1 + tau (y - 1)), applied by the next residual step
     int breakdown;   // CG curvature not positive: end the inner solve
     int status;
     int matvecs;     // operator applications in this p step
-    int cap;
     int cg_it;
     int newton_it;
-    unsigned cnt_b, cnt_c;   // last-block counters of the finalise / update kernels
-    double tol, tau, res, gamma, gamma0, gamma_prev, alpha, alpha_prev, beta, thr;
+    double tau, res, gamma, gamma0, gamma_prev, alpha, alpha_prev, beta, thr;
+};
+
+// Result of one p step, written by block 0.
+struct NtOut {
+    int status;
+    int matvecs;
+    int newton_it;
+    int pad;
+    double res;
 };
 
 struct NtArgs {
@@ -70,55 +82,68 @@ struct NtArgs {
     int n;
     int ldk;        // row pitch of K and of the column partials (floats, multiple of 4)
     int T;          // column tiles
-    int W4;         // float4 chunks per column tile
+    int W4;         // float4 chunks per column tile (<= threads x CH)
     int R;          // row stripes
     int rows_per;
-    double* x;      // 2n: rho | kappa
-    double* v;      // 2n
-    double* y;
-    double* r;
-    double* pd;
-    double* s;
-    double* w;
-    double* prt;    // T x n row partials
+    // vectors of 2n FP32 entries (rows | columns); GB300 runs FP64 arithmetic at a small
+    // fraction of the FP32 rate, so FP64 is kept to the block partials and the scalars
+    float* x;       // rho | kappa
+    float* v;       // D(x) S x
+    float* y;
+    float* r;
+    float* pd;
+    float* s;
+    float* w;
+    float* prt;     // T x n row partials
     float* pc;      // R x ldk column partials
     double* bred;   // finalisation block partials (4 per block)
     double* cred;   // update block partials (4 per block)
-    NtCtl* ctl;
+    unsigned* bar;  // grid barrier (count, generation)
+    int* err;       // kErr* code of a failed wait or step
 };
 
-__device__ __forceinline__ double wlog2_f64(int w, const double* __restrict__ ltab) {
-    return w < 32768 ? __ldg(ltab + w) : log2((double)w);
+// Global float4 chunk (columns 4q .. 4q+3) of local chunk ql of column tile t; chunks past
+// the tile map beyond the matrix (4q >= n), which every use masks.
+__device__ __forceinline__ int nt_chunk(const NtArgs& A, int t, int ql) {
+    return ql < A.W4 ? t * A.W4 + ql : (A.n + 3) / 4;
 }
 
+// the 256-entry table of log2pair.cuh, built once per call
+__global__ void nt_tab_kernel(float4* t) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < 256) t[j] = log2_tab_entry(j);
+}
+
+// V_j as a float pair (hi, lo), and the same for p
+__global__ void nt_vsplit_kernel(const double* __restrict__ V, float2* __restrict__ vp, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) {
+        const float h = (float)V[j];
+        vp[j] = make_float2(h, (float)(V[j] - (double)h));
+    }
+}
+
+// C_i = max_j (p log2 w_ij - V_j) over w_ij > 0 to about 1e-4 (SFU log2; C_i only sets the
+// scale of row i of K); one warp per row
 template <typename WT>
-__device__ __forceinline__ int load_weight(const WT* p) {
-    return (int)*p;
-}
-
-// log2 of 1..32767 in FP64 (entry 0 unused)
-__global__ void nt_ltab_kernel(double* t) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < 32768) t[i] = i > 0 ? log2((double)i) : -INFINITY;
-}
-
-// C_i = max_j (p log2 w_ij - V_j) over w_ij > 0; one warp per row
-template <typename WT>
-__global__ void nt_rowmax_kernel(const WT* __restrict__ w, int n, int64_t ld, double p,
-                                 const double* __restrict__ V, const double* __restrict__ ltab,
+__global__ void nt_rowmax_kernel(const WT* __restrict__ w, int n, int64_t ld, float ph,
+                                 const float2* __restrict__ vp, float* __restrict__ Cf,
                                  double* __restrict__ C) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= n) return;
     const WT* wr = w + (int64_t)row * ld;
-    double m = -INFINITY;
+    float m = -INFINITY;
     for (int j = lane; j < n; j += 32) {
-        const int wv = load_weight(wr + j);
-        if (wv > 0) m = fmax(m, __fma_rn(p, wlog2_f64(wv, ltab), -__ldg(V + j)));
+        const int wv = (int)wr[j];
+        if (wv > 0) m = fmaxf(m, fmaf(ph, __log2f((float)wv), -vp[j].x));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) C[row] = m;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) {
+        Cf[row] = m;
+        C[row] = (double)m;
+    }
 }
 
 // four weights of a chunk (columns 4q .. 4q+3, all < ld)
@@ -137,34 +162,39 @@ __device__ __forceinline__ void load4(const int32_t* p, int v[4]) {
     v[3] = q.w;
 }
 
-// K_ij = 2^(d), d = (p log2 w_ij - V_j) - C_i <= 0 in FP64, as 2^hi (1 + lo ln 2) with
-// hi + lo = d; pad columns and zero weights give 0.  Also the column maxima of K over each
-// row stripe (pc), from which the starting kappa is taken.
+// K_ij = 2^d with d = p log2 w_ij - V_j - C_i evaluated in float pairs: the leading parts
+// cancel exactly (two-product, two-sums) and the small ones are added after, so d is exact
+// to about 2^-24 |d|; pad columns and zero weights give 0.  Also the column maxima of K
+// over each row stripe (pc), from which the starting kappa is taken.
 template <typename WT, int CH>
 __global__ void __launch_bounds__(kNtThreads) nt_kwrite_kernel(const WT* __restrict__ w, int64_t ld,
-                                                               double p, const double* __restrict__ V,
-                                                               const double* __restrict__ C,
-                                                               const double* __restrict__ ltab,
+                                                               float ph, float pl,
+                                                               const float2* __restrict__ vp,
+                                                               const float* __restrict__ Cf,
+                                                               const float4* __restrict__ gtab,
                                                                NtArgs A) {
+    __shared__ float4 s_tab[256];
     const int tid = threadIdx.x;
+    s_tab[tid] = gtab[tid];
+    __syncthreads();
     const int t = blockIdx.x % A.T, s = blockIdx.x / A.T;
     const int r0 = s * A.rows_per, r1 = min(A.n, r0 + A.rows_per);
     const int n = A.n;
-    double vj[4 * CH];
+    float2 vj[4 * CH];
     float cm[4 * CH];
     int q[CH];
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
-        q[k] = t * A.W4 + tid + kNtThreads * k;
+        q[k] = nt_chunk(A, t, tid + kNtThreads * k);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int j = 4 * q[k] + e;
-            vj[4 * k + e] = j < n ? V[j] : 0.0;
+            vj[4 * k + e] = j < n ? vp[j] : make_float2(0.0f, 0.0f);
             cm[4 * k + e] = 0.0f;
         }
     }
     for (int i = r0; i < r1; ++i) {
-        const double ci = C[i];
+        const float ci = Cf[i];
         const WT* wr = w + (int64_t)i * ld;
         float* kr = (float*)A.K + (int64_t)i * A.ldk;
 #pragma unroll
@@ -178,11 +208,15 @@ __global__ void __launch_bounds__(kNtThreads) nt_kwrite_kernel(const WT* __restr
                 const int j = 4 * q[k] + e;
                 kv[e] = 0.0f;
                 if (j < n && wv[e] > 0) {
-                    const double d = __fma_rn(p, wlog2_f64(wv[e], ltab), -vj[4 * k + e]) - ci;
-                    const float hi = __double2float_rn(d);
-                    const float lo = __double2float_rn(d - (double)hi);
-                    const float k0 = exp2f(hi);
-                    kv[e] = fmaf(k0, lo * 0.693147182f, k0);
+                    const float2 lw = wlog2(s_tab, wv[e]);
+                    const float2 v2 = vj[4 * k + e];
+                    const float tp = ph * lw.x;
+                    const float te = fmaf(ph, lw.x, -tp);
+                    float e1, e2;
+                    const float s1 = two_sum(tp, -v2.x, &e1);
+                    const float s2 = two_sum(s1, -ci, &e2);
+                    const float rest = ((te + e1) + e2) + (fmaf(ph, lw.y, pl * lw.x) - v2.y);
+                    kv[e] = exp2f(s2 + rest);
                 }
                 cm[4 * k + e] = fmaxf(cm[4 * k + e], kv[e]);
             }
@@ -196,408 +230,495 @@ __global__ void __launch_bounds__(kNtThreads) nt_kwrite_kernel(const WT* __restr
                 make_float4(cm[4 * k], cm[4 * k + 1], cm[4 * k + 2], cm[4 * k + 3]);
 }
 
-// starting point and control block of a p step
-__global__ void nt_init_kernel(NtArgs A, double tol, int cap) {
-    const int n = A.n;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * n; e += gridDim.x * blockDim.x) {
-        double xe = 1.0;
-        if (e >= n) {
-            const int j = e - n;
-            float m = 0.0f;
-            for (int s = 0; s < A.R; ++s) m = fmaxf(m, A.pc[(int64_t)s * A.ldk + j]);
-            xe = 1.0 / (double)m;   // +inf for an empty column: caught by the first residual
+// Sum (compensated, Kahan) or max over the R stripe partials of column j, the stripes split
+// over the 8 warps of the block; each lane issues its loads in batches of 24 independent
+// loads.
+template <bool MAX>
+__device__ __forceinline__ float nt_stripes(const float* __restrict__ pc, int R, int ldk, int j, int wid) {
+    constexpr int kB = 24;
+    float acc = 0.0f, comp = 0.0f;   // 0 is also the identity of the max: the partials are >= 0
+    for (int base = wid; base < R; base += kNtWarps * kB) {
+        float a[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int s = base + u * kNtWarps;
+            a[u] = s < R ? __ldcg(pc + (int64_t)s * ldk + j) : 0.0f;
         }
-        A.x[e] = xe;
-        A.y[e] = 1.0;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        NtCtl c{};
-        c.mode = kNtRes;
-        c.status = kNtRunning;
-        c.cap = cap;
-        c.tol = tol;
-        c.tau = 1.0;
-        *A.ctl = c;
-    }
-}
-
-// D(x) S D(x) z for z = 1 (residual) or z = r (CG): one read of K.  Block (s, t) takes the
-// rows of stripe s and the columns of tile t; each thread owns CH float4 chunks of columns.
-// Row results go to prt[t][i] (FP64, complete over the tile), column results to pc[s][j].
-template <int CH>
-__global__ void __launch_bounds__(kNtThreads, 2) nt_matvec_kernel(NtArgs A) {
-    __shared__ float red[2][kNtWarps][4];
-    extern __shared__ float zr_s[];
-    const NtCtl* ctl = A.ctl;
-    const int mode = ctl->mode;
-    if (mode == kNtDone) return;
-    const bool res_mode = mode == kNtRes;
-    const bool apply = ctl->apply != 0;
-    const double tau = ctl->tau;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int t = blockIdx.x % A.T, s = blockIdx.x / A.T;
-    const int r0 = s * A.rows_per, r1 = min(A.n, r0 + A.rows_per);
-    const int n = A.n;
-    float z[4 * CH], acc[4 * CH];
-    int q[CH];
 #pragma unroll
-    for (int k = 0; k < CH; ++k) {
-        q[k] = t * A.W4 + tid + kNtThreads * k;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int j = 4 * q[k] + e;
-            float zv = 0.0f;
-            if (j < n) {
-                double xe = A.x[n + j];
-                if (apply) xe *= 1.0 + tau * (A.y[n + j] - 1.0);
-                zv = (float)(res_mode ? xe : xe * A.r[n + j]);
+        for (int u = 0; u < kB; ++u) {
+            if (MAX) {
+                acc = fmaxf(acc, a[u]);
+            } else {
+                const float yk = a[u] - comp;
+                const float tk = acc + yk;
+                comp = (tk - acc) - yk;
+                acc = tk;
             }
-            z[4 * k + e] = zv;
-            acc[4 * k + e] = 0.0f;
         }
     }
-    for (int i = r0 + tid; i < r1; i += kNtThreads) {
-        double xe = A.x[i];
-        if (apply) xe *= 1.0 + tau * (A.y[i] - 1.0);
-        zr_s[i - r0] = (float)(res_mode ? xe : xe * A.r[i]);
-    }
-    __syncthreads();
-    int buf = 0;
-    for (int i = r0; i < r1; i += 4) {
-        float4 kv[4][CH];
-#pragma unroll
-        for (int g = 0; g < 4; ++g)
-#pragma unroll
-            for (int k = 0; k < CH; ++k)
-                kv[g][k] = (i + g < r1 && 4 * q[k] < n)
-                               ? *(const float4*)(A.K + (int64_t)(i + g) * A.ldk + 4 * q[k])
-                               : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        float dot[4];
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            const float zr = i + g < r1 ? zr_s[i + g - r0] : 0.0f;
-            float d = 0.0f;
-#pragma unroll
-            for (int k = 0; k < CH; ++k) {
-                d = fmaf(kv[g][k].x, z[4 * k], d);
-                d = fmaf(kv[g][k].y, z[4 * k + 1], d);
-                d = fmaf(kv[g][k].z, z[4 * k + 2], d);
-                d = fmaf(kv[g][k].w, z[4 * k + 3], d);
-                acc[4 * k] = fmaf(kv[g][k].x, zr, acc[4 * k]);
-                acc[4 * k + 1] = fmaf(kv[g][k].y, zr, acc[4 * k + 1]);
-                acc[4 * k + 2] = fmaf(kv[g][k].z, zr, acc[4 * k + 2]);
-                acc[4 * k + 3] = fmaf(kv[g][k].w, zr, acc[4 * k + 3]);
-            }
-            dot[g] = d;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int g = 0; g < 4; ++g) dot[g] += __shfl_xor_sync(0xffffffffu, dot[g], o);
-        if (lane == 0) {
-#pragma unroll
-            for (int g = 0; g < 4; ++g) red[buf][wid][g] = dot[g];
-        }
-        __syncthreads();
-        if (tid < 4 && i + tid < r1) {
-            double sm = 0.0;
-#pragma unroll
-            for (int x = 0; x < kNtWarps; ++x) sm += (double)red[buf][x][tid];
-            A.prt[(int64_t)t * n + i + tid] = sm;
-        }
-        buf ^= 1;
-    }
-#pragma unroll
-    for (int k = 0; k < CH; ++k)
-        if (4 * q[k] < n)
-            *(float4*)(A.pc + (int64_t)s * A.ldk + 4 * q[k]) =
-                make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+    return acc;
 }
 
-// block sum / min / max of doubles over 256 threads; result valid in thread 0
-__device__ __forceinline__ double nt_block_sum(double x, double* sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < kNtWarps; ++k) r += sh[k];
-    return r;
+// 16-byte asynchronous copy global -> shared (cp.async, cached in L2 only) and its groups
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ double nt_block_max(double x, double* sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
-    __syncthreads();
-    double r = -INFINITY;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < kNtWarps; ++k) r = fmax(r, sh[k]);
-    return r;
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
-__device__ __forceinline__ double nt_block_min(double x, double* sh) {
-    return -nt_block_max(-x, sh);
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// true in thread 0 of the last block to finish (its partials are then all visible)
-__device__ __forceinline__ bool nt_last_block(unsigned* cnt, int* s_last) {
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(cnt, 1u);
-        *s_last = prev == gridDim.x - 1;
-        if (*s_last) __threadfence();
-    }
-    __syncthreads();
-    return *s_last != 0;
-}
-
-// Column sums (over the stripes) and row sums (over the tiles) of the matvec, scaled by x:
-// m = D(x) S D(x) z.  Residual step: v = m, r = 1 - v, y = 1.  CG step: w = m + v o r.
-// Grid: ceil(n/32) column blocks, then ceil(n/256) row blocks.
-__global__ void __launch_bounds__(kNtThreads) nt_fin_kernel(NtArgs A) {
-    __shared__ double sred[kNtWarps][33];
-    __shared__ double sh[kNtWarps];
-    __shared__ int s_last;
-    NtCtl* ctl = A.ctl;
-    const int mode = ctl->mode;
-    if (mode == kNtDone) return;
-    const bool res_mode = mode == kNtRes;
-    const bool apply = ctl->apply != 0;
-    const double tau = ctl->tau;
+// starting point of a p step: rho = 1, kappa_j = 1 / max_i K_ij.
+// Grid: ceil(n/32) column blocks of 32 columns x 8 warps, then the row blocks.
+__global__ void __launch_bounds__(kNtThreads) nt_init_kernel(NtArgs A) {
+    __shared__ float sred[kNtWarps][33];
     const int n = A.n, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nbc = (n + 31) / 32;
-    int e = -1;
-    double tot = 0.0;
     if ((int)blockIdx.x < nbc) {
         const int j = blockIdx.x * 32 + lane;
-        double sm = 0.0;
-        if (j < n)
-            for (int s = wid; s < A.R; s += kNtWarps) sm += (double)A.pc[(int64_t)s * A.ldk + j];
-        sred[wid][lane] = sm;
+        sred[wid][lane] = j < n ? nt_stripes<true>(A.pc, A.R, A.ldk, j, wid) : 0.0f;
         __syncthreads();
         if (wid == 0 && j < n) {
-            for (int x = 0; x < kNtWarps; ++x) tot += sred[x][lane];
-            e = n + j;
+            float m = 0.0f;
+            for (int x = 0; x < kNtWarps; ++x) m = fmaxf(m, sred[x][lane]);
+            A.x[n + j] = 1.0f / m;   // +inf for an empty column: caught by the first residual
+            A.y[n + j] = 1.0f;
         }
     } else {
         const int i = (blockIdx.x - nbc) * kNtThreads + tid;
         if (i < n) {
-            for (int t = 0; t < A.T; ++t) tot += A.prt[(int64_t)t * n + i];
-            e = i;
+            A.x[i] = 1.0f;
+            A.y[i] = 1.0f;
         }
     }
-    double a0 = 0.0, a1 = 0.0, a2 = INFINITY;   // residual: max|v-1|, sum (1-v)^2, min v
-                                                // CG: sum w r
-    if (e >= 0) {
-        double xe = A.x[e];
-        if (apply) {
-            xe *= 1.0 + tau * (A.y[e] - 1.0);
-            A.x[e] = xe;
-        }
-        const double m = xe * tot;
-        if (res_mode) {
-            A.v[e] = m;
-            A.r[e] = 1.0 - m;
-            A.y[e] = 1.0;
-            a0 = fabs(m - 1.0);
-            a1 = (1.0 - m) * (1.0 - m);
-            a2 = (m > 0.0 && m < INFINITY) ? m : -1.0;   // -1 flags a zero or non-finite sum
-        } else {
-            const double re = A.r[e];
-            const double we = m + A.v[e] * re;
-            A.w[e] = we;
-            a0 = we * re;
-            a2 = (we > -INFINITY && we < INFINITY) ? 1.0 : -1.0;
-        }
-    }
-    const double b0 = res_mode ? nt_block_max(a0, sh) : nt_block_sum(a0, sh);
-    const double b1 = nt_block_sum(a1, sh);
-    const double b2 = nt_block_min(a2, sh);
-    if (tid == 0) {
-        A.bred[4 * blockIdx.x] = b0;
-        A.bred[4 * blockIdx.x + 1] = b1;
-        A.bred[4 * blockIdx.x + 2] = b2;
-    }
-    if (!nt_last_block(&ctl->cnt_b, &s_last)) return;
-    double c0 = res_mode ? -INFINITY : 0.0, c1 = 0.0, c2 = INFINITY;
-    for (int b = tid; b < (int)gridDim.x; b += kNtThreads) {
-        const double x0 = __ldcg(A.bred + 4 * b), x1 = __ldcg(A.bred + 4 * b + 1), x2 = __ldcg(A.bred + 4 * b + 2);
-        c0 = res_mode ? fmax(c0, x0) : c0 + x0;
-        c1 += x1;
-        c2 = fmin(c2, x2);
-    }
-    const double g0 = res_mode ? nt_block_max(c0, sh) : nt_block_sum(c0, sh);
-    const double g1 = nt_block_sum(c1, sh);
-    const double g2 = nt_block_min(c2, sh);
-    if (tid != 0) return;
-    NtCtl c = *ctl;
-    c.cnt_b = 0;
-    c.matvecs += 1;
-    c.cstage = 0;
-    if (!(g2 > 0.0)) {
-        c.status = kNtNonfinite;
-        c.mode = kNtDone;
-    } else if (res_mode) {
-        c.res = g0;
-        c.apply = 0;
-        if (g0 <= c.tol) {
-            c.status = kNtConverged;
-            c.mode = kNtDone;
-        } else if (c.matvecs >= c.cap) {
-            c.status = kNtCapped;
-            c.mode = kNtDone;
-        } else {
-            const double eta = fmin(kNtEtaMax, fmax(kNtEtaMin, sqrt(g0)));
-            c.gamma = c.gamma0 = g1;
-            c.thr = eta * eta * g1;
-            c.first = 1;
-            c.cg_it = 0;
-            c.breakdown = 0;
-            c.mode = kNtCg;
-        }
-    } else {
-        const double delta = g0;
-        if (c.first) {
-            c.beta = 0.0;
-            c.alpha = c.gamma / delta;
-        } else {
-            c.beta = c.gamma / c.gamma_prev;
-            c.alpha = c.gamma / (delta - c.beta * c.gamma / c.alpha_prev);
-        }
-        if (!(c.alpha > 0.0 && c.alpha < INFINITY)) {
-            c.alpha = 0.0;
-            c.breakdown = 1;
-        }
-        c.cstage = 1;
-    }
-    *ctl = c;
 }
 
-// p = r + beta p, s = w + beta s, y += alpha p, r -= alpha s; the last block ends the
-// inner solve (||r||^2 <= eta^2 ||r_0||^2, CG cap, min y < delta, breakdown, matvec cap)
-__global__ void __launch_bounds__(kNtThreads) nt_upd_kernel(NtArgs A) {
-    __shared__ double sh[kNtWarps];
-    __shared__ int s_last;
-    NtCtl* ctl = A.ctl;
-    if (ctl->mode == kNtDone || ctl->cstage != 1) return;
-    const bool first = ctl->first != 0;
-    const double alpha = ctl->alpha, beta = ctl->beta;
-    const int n2 = 2 * A.n, tid = threadIdx.x;
-    double rr = 0.0, ymin = INFINITY;
-    for (int e = blockIdx.x * kNtThreads + tid; e < n2; e += gridDim.x * kNtThreads) {
-        const double re = A.r[e], we = A.w[e];
-        const double pe = first ? re : re + beta * A.pd[e];
-        const double se = first ? we : we + beta * A.s[e];
-        const double ye = A.y[e] + alpha * pe;
-        const double rn = re - alpha * se;
-        A.pd[e] = pe;
-        A.s[e] = se;
-        A.y[e] = ye;
-        A.r[e] = rn;
-        rr += rn * rn;
-        ymin = fmin(ymin, ye);
+// Block reduction of three FP32 values at once: v0 by max (MAX0) or sum, v1 by sum, v2 by
+// min; the warp results are combined in FP64 by thread 0, where the results are valid.
+template <bool MAX0>
+__device__ __forceinline__ void nt_block_reduce3(float v0, float v1, float v2, float (*sh)[kNtWarps],
+                                                 double* o0, double* o1, double* o2) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float u0 = __shfl_xor_sync(0xffffffffu, v0, o);
+        v0 = MAX0 ? fmaxf(v0, u0) : v0 + u0;
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 = fminf(v2, __shfl_xor_sync(0xffffffffu, v2, o));
     }
-    const double b0 = nt_block_sum(rr, sh);
-    const double b1 = nt_block_min(ymin, sh);
-    if (tid == 0) {
-        A.cred[4 * blockIdx.x] = b0;
-        A.cred[4 * blockIdx.x + 1] = b1;
+    __syncthreads();   // sh may still be read by thread 0 of the previous reduction
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = v0;
+        sh[1][threadIdx.x >> 5] = v1;
+        sh[2][threadIdx.x >> 5] = v2;
     }
-    if (!nt_last_block(&ctl->cnt_c, &s_last)) return;
-    double c0 = 0.0, c1 = INFINITY;
-    for (int b = tid; b < (int)gridDim.x; b += kNtThreads) {
-        c0 += __ldcg(A.cred + 4 * b);
-        c1 = fmin(c1, __ldcg(A.cred + 4 * b + 1));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r0 = sh[0][0], r1 = sh[1][0], r2 = sh[2][0];
+        for (int k = 1; k < kNtWarps; ++k) {
+            r0 = MAX0 ? fmax(r0, (double)sh[0][k]) : r0 + sh[0][k];
+            r1 += sh[1][k];
+            r2 = fmin(r2, (double)sh[2][k]);
+        }
+        *o0 = r0;
+        *o1 = r1;
+        *o2 = r2;
     }
-    const double g0 = nt_block_sum(c0, sh);
-    const double g1 = nt_block_min(c1, sh);
-    if (tid != 0) return;
-    NtCtl c = *ctl;
-    c.cnt_c = 0;
-    c.cstage = 0;
-    c.gamma_prev = c.gamma;
-    c.gamma = g0;
-    c.alpha_prev = c.alpha;
-    c.first = 0;
-    c.cg_it += 1;
+}
+
+// Reduction of the G block partials (4 doubles each, the first three used) by warp 0 in a
+// fixed order, so that every block obtains identical values; valid in lane 0 of warp 0.
+template <bool MAX0>
+__device__ __forceinline__ void nt_grid_reduce3(const double* part, int G, double* g0, double* g1, double* g2) {
+    double a0 = 0.0, a1 = 0.0, a2 = INFINITY;   // 0 is also the identity of the max of |v - 1|
+    for (int x = threadIdx.x; x < G; x += 32) {
+        const double x0 = __ldcg(part + 4 * x);
+        a0 = MAX0 ? fmax(a0, x0) : a0 + x0;
+        a1 += __ldcg(part + 4 * x + 1);
+        a2 = fmin(a2, __ldcg(part + 4 * x + 2));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double u0 = __shfl_xor_sync(0xffffffffu, a0, o);
+        a0 = MAX0 ? fmax(a0, u0) : a0 + u0;
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 = fmin(a2, __shfl_xor_sync(0xffffffffu, a2, o));
+    }
+    *g0 = a0;
+    *g1 = a1;
+    *g2 = a2;
+}
+
+// Decisions after the finalisation (g0: max |v - 1| or sum w r; g1: sum (1 - v)^2;
+// g2: min v, or a negative flag for a zero or non-finite value)
+__device__ __forceinline__ void nt_after_fin(NtState& S, bool res_mode, double g0, double g1, double g2,
+                                             double tol, int cap) {
+    S.matvecs += 1;
+    S.cstage = 0;
+    if (!(g2 > 0.0)) {
+        S.status = kNtNonfinite;
+        S.mode = kNtDone;
+    } else if (res_mode) {
+        S.res = g0;
+        S.apply = 0;
+        if (g0 <= tol) {
+            S.status = kNtConverged;
+            S.mode = kNtDone;
+        } else if (S.matvecs >= cap) {
+            S.status = kNtCapped;
+            S.mode = kNtDone;
+        } else {
+            const double eta = fmin(kNtEtaMax, fmax(kNtEtaMin, sqrt(g0)));
+            S.gamma = S.gamma0 = g1;
+            S.thr = eta * eta * g1;
+            S.first = 1;
+            S.cg_it = 0;
+            S.breakdown = 0;
+            S.mode = kNtCg;
+        }
+    } else {
+        // Chronopoulos-Gear: alpha = gamma / (delta - beta gamma / alpha_prev), delta = r.Mr
+        if (S.first) {
+            S.beta = 0.0;
+            S.alpha = S.gamma / g0;
+        } else {
+            S.beta = S.gamma / S.gamma_prev;
+            S.alpha = S.gamma / (g0 - S.beta * S.gamma / S.alpha_prev);
+        }
+        if (!(S.alpha > 0.0 && S.alpha < INFINITY)) {
+            S.alpha = 0.0;
+            S.breakdown = 1;
+        }
+        S.cstage = 1;
+    }
+}
+
+// Decisions after a CG update (g0 = ||r||^2, g1 = min y): end of the inner solve when the
+// residual reached eta ||r_0||, at the CG cap, on breakdown, at the matvec cap, or when y
+// left [delta, inf) (the Newton step is then shortened to min y = delta)
+__device__ __forceinline__ void nt_after_upd(NtState& S, double g0, double g1, int cap) {
+    S.gamma_prev = S.gamma;
+    S.gamma = g0;
+    S.alpha_prev = S.alpha;
+    S.first = 0;
+    S.cg_it += 1;
     if (!(g0 < INFINITY) || !(g1 > -INFINITY && g1 < INFINITY)) {
-        c.status = kNtNonfinite;
-        c.mode = kNtDone;
-    } else if (g0 <= c.thr || c.cg_it >= kNtCgCap || g1 < kNtDelta || c.breakdown || c.matvecs >= c.cap) {
-        c.apply = 1;
-        c.tau = g1 < kNtDelta ? (1.0 - kNtDelta) / (1.0 - g1) : 1.0;
-        c.mode = kNtRes;
-        c.newton_it += 1;
+        S.status = kNtNonfinite;
+        S.mode = kNtDone;
+    } else if (g0 <= S.thr || S.cg_it >= kNtCgCap || g1 < kNtDelta || S.breakdown || S.matvecs >= cap) {
+        S.apply = 1;
+        S.tau = g1 < kNtDelta ? (1.0 - kNtDelta) / (1.0 - g1) : 1.0;
+        S.mode = kNtRes;
+        S.newton_it += 1;
     }
-    *ctl = c;
+}
+
+// Dynamic shared memory of the solve kernel: the cp.async stages, the per-warp row dots of
+// the stripe, the stripe's row factors and the totals of the owned entries.
+__host__ __device__ inline size_t nt_smem_bytes(int ch, int rows_per, int own) {
+    return (size_t)kNtStages * ch * kNtThreads * 16 + (size_t)rows_per * kNtWarps * 4 + (size_t)rows_per * 4 +
+           (size_t)2 * own * 4;
+}
+
+// One p step of the Newton-CG iteration on K.  Block (s, t) = (blockIdx / T, blockIdx % T)
+// streams rows [s rows_per, ...) x the columns of tile t in the matvec; for the
+// finalisation and the CG update it owns columns [b cs, (b+1) cs) and the rows with the
+// same indices.
+template <int CH>
+__global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, double tol, int cap,
+                                                                 NtOut* out) {
+    __shared__ float sred[kNtWarps][33];
+    __shared__ float sh[3][kNtWarps];
+    __shared__ NtState S;
+    extern __shared__ __align__(16) unsigned char nt_dyn[];
+    if (*(volatile int*)A.err != 0) return;   // an earlier step of this call failed
+    const int n = A.n, G = gridDim.x, b = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int t = b % A.T, s = b / A.T;
+    const int r0 = s * A.rows_per, r1 = min(n, r0 + A.rows_per), nrows = r1 - r0;
+    const int cs = (n + G - 1) / G;
+    const int c0 = min(n, b * cs), c1 = min(n, c0 + cs);   // owned columns and rows
+    const int own = c1 - c0;
+    float4* stage = (float4*)nt_dyn;                                   // [stages][CH][threads]
+    float* rowdot = (float*)(stage + kNtStages * CH * kNtThreads);     // [rows_per][warps]
+    float* zr_s = rowdot + A.rows_per * kNtWarps;                      // [rows_per]
+    float* tot_s = zr_s + A.rows_per;                                  // [2 cs]
+    if (tid == 0) {
+        NtState z{};
+        z.mode = kNtRes;
+        z.status = kNtRunning;
+        z.tau = 1.0;
+        S = z;
+    }
+    __syncthreads();
+    int q[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k) q[k] = nt_chunk(A, t, tid + kNtThreads * k);
+    const float* krow0 = A.K + (int64_t)r0 * A.ldk;
+    // this thread's chunks of row `row` of the stripe into stage row % kNtStages
+    auto issue = [&](int row) {
+        float4* dst = stage + (row % kNtStages) * CH * kNtThreads + tid;
+#pragma unroll
+        for (int k = 0; k < CH; ++k)
+            if (4 * q[k] < n) cp_async16(dst + k * kNtThreads, krow0 + (int64_t)row * A.ldk + 4 * q[k]);
+    };
+    for (;;) {
+        const bool res_mode = S.mode == kNtRes;
+        const bool apply = S.apply != 0;
+        const float tau = (float)S.tau;
+        // ---- A: D(x) S D(x) z for z = 1 or r, one read of the block's tile of K ----
+        {
+            float z[4 * CH], acc[4 * CH];
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int j = 4 * q[k] + e;
+                    float zv = 0.0f;
+                    if (j < n) {
+                        float xe = A.x[n + j];
+                        if (apply) xe *= fmaf(tau, A.y[n + j] - 1.0f, 1.0f);
+                        zv = res_mode ? xe : xe * A.r[n + j];
+                    }
+                    z[4 * k + e] = zv;
+                    acc[4 * k + e] = 0.0f;
+                }
+            }
+            for (int i = tid; i < nrows; i += kNtThreads) {
+                float xe = A.x[r0 + i];
+                if (apply) xe *= fmaf(tau, A.y[r0 + i] - 1.0f, 1.0f);
+                zr_s[i] = res_mode ? xe : xe * A.r[r0 + i];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int st = 0; st < kNtStages - 1; ++st) {
+                if (st < nrows) issue(st);
+                cp_async_commit();
+            }
+            for (int row = 0; row < nrows; ++row) {
+                if (row + kNtStages - 1 < nrows) issue(row + kNtStages - 1);
+                cp_async_commit();
+                cp_async_wait<kNtStages - 1>();   // this thread's copies of `row` have landed
+                const float4* src = stage + (row % kNtStages) * CH * kNtThreads + tid;
+                const float zr = zr_s[row];
+                float d = 0.0f;
+#pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    if (4 * q[k] < n) {
+                        const float4 kv = src[k * kNtThreads];
+                        d = fmaf(kv.x, z[4 * k], d);
+                        d = fmaf(kv.y, z[4 * k + 1], d);
+                        d = fmaf(kv.z, z[4 * k + 2], d);
+                        d = fmaf(kv.w, z[4 * k + 3], d);
+                        acc[4 * k] = fmaf(kv.x, zr, acc[4 * k]);
+                        acc[4 * k + 1] = fmaf(kv.y, zr, acc[4 * k + 1]);
+                        acc[4 * k + 2] = fmaf(kv.z, zr, acc[4 * k + 2]);
+                        acc[4 * k + 3] = fmaf(kv.w, zr, acc[4 * k + 3]);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                if (lane == 0) rowdot[row * kNtWarps + wid] = d;
+            }
+            cp_async_wait<0>();
+            __syncthreads();
+            for (int i = tid; i < nrows; i += kNtThreads) {
+                float sm = 0.0f;
+#pragma unroll
+                for (int x = 0; x < kNtWarps; ++x) sm += rowdot[i * kNtWarps + x];
+                A.prt[(int64_t)t * n + r0 + i] = sm;
+            }
+#pragma unroll
+            for (int k = 0; k < CH; ++k)
+                if (4 * q[k] < n)
+                    *(float4*)(A.pc + (int64_t)s * A.ldk + 4 * q[k]) =
+                        make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+        }
+        if (!group_barrier(A.bar, G, A.err, kWaitTimeoutNs)) break;
+        // ---- B: finalise the owned entries: m = D(x) S D(x) z; v, r, y or w ----
+        {
+            for (int cb = c0; cb < c1; cb += 32) {
+                const int j = cb + lane;
+                sred[wid][lane] = j < c1 ? nt_stripes<false>(A.pc, A.R, A.ldk, j, wid) : 0.0f;
+                __syncthreads();
+                if (wid == 0 && j < c1) {
+                    float tot = 0.0f;
+                    for (int x = 0; x < kNtWarps; ++x) tot += sred[x][lane];
+                    tot_s[j - c0] = tot;
+                }
+                __syncthreads();
+            }
+            for (int i = c0 + tid; i < c1; i += kNtThreads) {
+                float tot = 0.0f;
+                for (int tt = 0; tt < A.T; ++tt) tot += A.prt[(int64_t)tt * n + i];
+                tot_s[own + (i - c0)] = tot;
+            }
+            __syncthreads();
+            // residual step: a0 = max |v - 1|, a1 = sum (1 - v)^2, a2 = min v (or -1 for a
+            // zero or non-finite sum); CG step: a0 = sum w r, a2 = -1 for a non-finite w
+            float a0 = 0.0f, a1 = 0.0f, a2 = INFINITY;
+            for (int x = tid; x < 2 * own; x += kNtThreads) {
+                const int e = x < own ? n + c0 + x : c0 + (x - own);
+                float xe = A.x[e];
+                if (apply) {
+                    xe *= fmaf(tau, A.y[e] - 1.0f, 1.0f);
+                    A.x[e] = xe;
+                }
+                const float m = xe * tot_s[x];
+                if (res_mode) {
+                    A.v[e] = m;
+                    A.r[e] = 1.0f - m;
+                    A.y[e] = 1.0f;
+                    a0 = fmaxf(a0, fabsf(m - 1.0f));
+                    a1 = fmaf(1.0f - m, 1.0f - m, a1);
+                    a2 = fminf(a2, (m > 0.0f && m < INFINITY) ? m : -1.0f);
+                } else {
+                    const float re = A.r[e];
+                    const float we = fmaf(A.v[e], re, m);
+                    A.w[e] = we;
+                    a0 = fmaf(we, re, a0);
+                    a2 = fminf(a2, (we > -INFINITY && we < INFINITY) ? 1.0f : -1.0f);
+                }
+            }
+            double b0, b1, b2;
+            if (res_mode) nt_block_reduce3<true>(a0, a1, a2, sh, &b0, &b1, &b2);
+            else nt_block_reduce3<false>(a0, a1, a2, sh, &b0, &b1, &b2);
+            if (tid == 0) {
+                A.bred[4 * b] = b0;
+                A.bred[4 * b + 1] = b1;
+                A.bred[4 * b + 2] = b2;
+            }
+        }
+        if (!group_barrier(A.bar, G, A.err, kWaitTimeoutNs)) break;
+        // ---- C: every block reduces all partials in the same order: same decisions ----
+        if (wid == 0) {
+            double g0, g1, g2;
+            if (res_mode) nt_grid_reduce3<true>(A.bred, G, &g0, &g1, &g2);
+            else nt_grid_reduce3<false>(A.bred, G, &g0, &g1, &g2);
+            if (lane == 0) nt_after_fin(S, res_mode, g0, g1, g2, tol, cap);
+        }
+        __syncthreads();
+        if (S.mode == kNtDone) break;
+        if (!S.cstage) continue;
+        // ---- CG update of the owned entries: p, s (= M p), y, r ----
+        {
+            const bool first = S.first != 0;
+            const float alpha = (float)S.alpha, beta = (float)S.beta;
+            float rr = 0.0f, ymin = INFINITY;
+            for (int x = tid; x < 2 * own; x += kNtThreads) {
+                const int e = x < own ? n + c0 + x : c0 + (x - own);
+                const float re = A.r[e], we = A.w[e];
+                const float pe = first ? re : fmaf(beta, A.pd[e], re);
+                const float se = first ? we : fmaf(beta, A.s[e], we);
+                const float ye = fmaf(alpha, pe, A.y[e]);
+                const float rn = fmaf(-alpha, se, re);
+                A.pd[e] = pe;
+                A.s[e] = se;
+                A.y[e] = ye;
+                A.r[e] = rn;
+                rr = fmaf(rn, rn, rr);
+                ymin = fminf(ymin, ye);
+            }
+            double b0, b1, b2;
+            nt_block_reduce3<false>(rr, 0.0f, ymin, sh, &b0, &b1, &b2);
+            if (tid == 0) {
+                A.cred[4 * b] = b0;
+                A.cred[4 * b + 1] = 0.0;
+                A.cred[4 * b + 2] = b2;
+            }
+        }
+        if (!group_barrier(A.bar, G, A.err, kWaitTimeoutNs)) break;
+        if (wid == 0) {
+            double g0, g1, g2;
+            nt_grid_reduce3<false>(A.cred, G, &g0, &g1, &g2);
+            if (lane == 0) nt_after_upd(S, g0, g2, cap);
+        }
+        __syncthreads();
+        if (S.mode == kNtDone) break;
+    }
+    if (b == 0 && tid == 0) {
+        NtOut o{};
+        o.status = S.status;
+        o.matvecs = S.matvecs;
+        o.newton_it = S.newton_it;
+        o.res = S.res;
+        *out = o;
+    }
 }
 
 // potentials of X = D(rho) K D(kappa) in log2 units: U = C - log2 rho, V -= log2 kappa
-__global__ void nt_potentials_kernel(const double* __restrict__ x, const double* __restrict__ C,
+__global__ void nt_potentials_kernel(const float* __restrict__ x, const double* __restrict__ C,
                                      double* __restrict__ U, double* __restrict__ V, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        U[i] = C[i] - log2(x[i]);
-        V[i] = V[i] - log2(x[n + i]);
+        U[i] = C[i] - log2((double)x[i]);
+        V[i] = V[i] - log2((double)x[n + i]);
     }
 }
 
 struct NtPlan {
-    int ch, T, W4, R, rows_per, grid_a, nb_fin, nb_upd;
+    int ch, T, W4, R, rows_per, grid;
+    size_t smem;
 };
 
 template <int CH>
 int nt_occupancy(size_t smem) {
+    static const cudaError_t attr = cudaFuncSetAttribute(nt_solve_kernel<CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         kNtMaxSmem);
+    if (attr != cudaSuccess) return 0;
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nt_matvec_kernel<CH>, kNtThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nt_solve_kernel<CH>, kNtThreads, smem);
     return occ;
 }
 
+// Column tiles of at most 1024 CH columns (CH float4 chunks per thread), equal in width;
+// as many row stripes as fill the co-resident grid.
 NtPlan nt_plan(const sa_ctx* ctx, int n) {
     NtPlan P{};
     P.ch = n <= 1024 ? 1 : n <= 2048 ? 2 : 4;
-    P.W4 = kNtThreads * P.ch;
-    P.T = (n + 4 * P.W4 - 1) / (4 * P.W4);
-    int occ = P.ch == 1 ? nt_occupancy<1>(0) : P.ch == 2 ? nt_occupancy<2>(0) : nt_occupancy<4>(0);
-    occ = std::max(1, std::min(occ, 2));
-    int G = ctx->num_sms * occ;
-    if (ctx->max_grid > 0) G = std::min(G, ctx->max_grid);
-    int R = std::max(1, std::min(n, G / P.T));
-    P.rows_per = (n + R - 1) / R;
-    P.R = (n + P.rows_per - 1) / P.rows_per;
-    P.grid_a = P.R * P.T;
-    P.nb_fin = (n + 31) / 32 + (n + kNtThreads - 1) / kNtThreads;
-    P.nb_upd = std::max(1, std::min((2 * n + kNtThreads - 1) / kNtThreads, 2 * ctx->num_sms));
+    const int nq = (n + 3) / 4;                                  // float4 chunks of a row
+    P.T = (nq + kNtThreads * P.ch - 1) / (kNtThreads * P.ch);
+    P.W4 = (nq + P.T - 1) / P.T;                                 // balanced tiles
+    auto occupancy = [&](size_t smem) {
+        const int occ = P.ch == 1 ? nt_occupancy<1>(smem) : P.ch == 2 ? nt_occupancy<2>(smem) : nt_occupancy<4>(smem);
+        return std::max(0, std::min(occ, 2));
+    };
+    // two blocks per SM when their shared memory fits, else one; the grid must be
+    // co-resident for the cooperative launch
+    for (int per_sm = 2; per_sm >= 1; --per_sm) {
+        int G = ctx->num_sms * per_sm;
+        if (ctx->max_grid > 0) G = std::min(G, ctx->max_grid);
+        const int R = std::max(1, std::min(n, G / P.T));
+        P.rows_per = (n + R - 1) / R;
+        P.R = (n + P.rows_per - 1) / P.rows_per;
+        P.grid = P.R * P.T;
+        const int cs = (n + P.grid - 1) / P.grid;
+        P.smem = nt_smem_bytes(P.ch, P.rows_per, cs);
+        if (P.smem <= (size_t)kNtMaxSmem && P.grid <= ctx->num_sms * occupancy(P.smem)) return P;
+    }
+    P.grid = 0;
     return P;
 }
 
-sa_status launch_matvec(const NtPlan& P, const NtArgs& A, cudaStream_t st) {
-    const size_t smem = (size_t)P.rows_per * sizeof(float);
-    if (P.ch == 1) nt_matvec_kernel<1><<<P.grid_a, kNtThreads, smem, st>>>(A);
-    else if (P.ch == 2) nt_matvec_kernel<2><<<P.grid_a, kNtThreads, smem, st>>>(A);
-    else nt_matvec_kernel<4><<<P.grid_a, kNtThreads, smem, st>>>(A);
+sa_status launch_solve(const NtPlan& P, NtArgs A, double tol, int cap, NtOut* out, cudaStream_t st) {
+    void* params[] = {(void*)&A, (void*)&tol, (void*)&cap, (void*)&out};
+    const void* kern = P.ch == 1 ? (const void*)nt_solve_kernel<1>
+                     : P.ch == 2 ? (const void*)nt_solve_kernel<2> : (const void*)nt_solve_kernel<4>;
+    SA_CUDA(cudaLaunchCooperativeKernel(kern, dim3(P.grid), dim3(kNtThreads), params, P.smem, st));
+    count_launch();
     return SA_OK;
-}
-
-template <typename WT>
-void launch_eval(const NtPlan& P, const sa_matrix* a, double p, const double* V, const double* C,
-                 const double* ltab, const NtArgs& A, cudaStream_t st) {
-    const WT* w = (const WT*)a->w;
-    if (P.ch == 1) nt_kwrite_kernel<WT, 1><<<P.grid_a, kNtThreads, 0, st>>>(w, a->ld, p, V, C, ltab, A);
-    else if (P.ch == 2) nt_kwrite_kernel<WT, 2><<<P.grid_a, kNtThreads, 0, st>>>(w, a->ld, p, V, C, ltab, A);
-    else nt_kwrite_kernel<WT, 4><<<P.grid_a, kNtThreads, 0, st>>>(w, a->ld, p, V, C, ltab, A);
 }
 
 }  // namespace
 
 bool newton_supported(const sa_ctx* ctx, const sa_matrix* a) {
-    (void)ctx;
     const int sz = wbytes(a->wtype);
     if (((uintptr_t)a->w & 15) != 0) return false;
     if (((size_t)a->ld * sz) % 16 != 0) return false;
-    return a->n >= 1 && a->n <= (1 << 16);
+    if (a->n < 1 || a->n > (1 << 16)) return false;
+    return nt_plan(ctx, a->n).grid > 0;
 }
 
 sa_status scale_newton(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, double* U, double* V,
@@ -605,39 +726,45 @@ sa_status scale_newton(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, 
     const int n = a->n;
     cudaStream_t st = ctx->stream;
     const NtPlan P = nt_plan(ctx, n);
-    const int ldk = (int)align_up((size_t)n, 4);
-    size_t bytes = 0;
-    {
-        bytes += align_up((size_t)n * ldk * 4, 256);
-        bytes += align_up((size_t)n * 8, 256);            // C
-        bytes += 7 * align_up((size_t)2 * n * 8, 256);    // x v y r p s w
-        bytes += align_up((size_t)P.T * n * 8, 256);      // prt
-        bytes += align_up((size_t)P.R * ldk * 4, 256);    // pc
-        bytes += align_up((size_t)P.nb_fin * 32, 256);
-        bytes += align_up((size_t)P.nb_upd * 32, 256);
-        bytes += align_up(sizeof(NtCtl), 256);
-        bytes += align_up((size_t)32768 * 8, 256);
-        bytes += 4096;
+    if (P.grid <= 0) {
+        set_error("newton scaling: no co-resident grid for n = %d", n);
+        return SA_E_UNSUPPORTED;
     }
+    const int ldk = (int)align_up((size_t)n, 4);
+    const size_t bytes = align_up((size_t)n * ldk * 4, 256)       // K
+                       + align_up((size_t)n * 8, 256)              // C
+                       + 7 * align_up((size_t)2 * n * 4, 256)      // x v y r p s w
+                       + align_up((size_t)P.T * n * 4, 256)        // row partials
+                       + align_up((size_t)P.R * ldk * 4, 256)      // column partials
+                       + 2 * align_up((size_t)P.grid * 32, 256)    // block partials
+                       + align_up((size_t)o->n_p * sizeof(NtOut), 256)
+                       + align_up((size_t)256 * 16, 256)           // log2 table
+                       + align_up((size_t)n * 8, 256)              // V pairs
+                       + align_up((size_t)n * 4, 256)              // C (FP32)
+                       + 3 * 256;                                  // barrier, error flag
     sa_status rc = ctx->ws.reserve(bytes);
     if (rc) return rc;
     Carve cv(ctx->ws.ptr);
     NtArgs A{};
     A.K = cv.take<float>((size_t)n * ldk);
     double* C = cv.take<double>(n);
-    A.x = cv.take<double>(2 * (size_t)n);
-    A.v = cv.take<double>(2 * (size_t)n);
-    A.y = cv.take<double>(2 * (size_t)n);
-    A.r = cv.take<double>(2 * (size_t)n);
-    A.pd = cv.take<double>(2 * (size_t)n);
-    A.s = cv.take<double>(2 * (size_t)n);
-    A.w = cv.take<double>(2 * (size_t)n);
-    A.prt = cv.take<double>((size_t)P.T * n);
+    A.x = cv.take<float>(2 * (size_t)n);
+    A.v = cv.take<float>(2 * (size_t)n);
+    A.y = cv.take<float>(2 * (size_t)n);
+    A.r = cv.take<float>(2 * (size_t)n);
+    A.pd = cv.take<float>(2 * (size_t)n);
+    A.s = cv.take<float>(2 * (size_t)n);
+    A.w = cv.take<float>(2 * (size_t)n);
+    A.prt = cv.take<float>((size_t)P.T * n);
     A.pc = cv.take<float>((size_t)P.R * ldk);
-    A.bred = cv.take<double>((size_t)P.nb_fin * 4);
-    A.cred = cv.take<double>((size_t)P.nb_upd * 4);
-    A.ctl = cv.take<NtCtl>(1);
-    double* ltab = cv.take<double>(32768);
+    A.bred = cv.take<double>((size_t)P.grid * 4);
+    A.cred = cv.take<double>((size_t)P.grid * 4);
+    NtOut* d_out = cv.take<NtOut>(o->n_p);
+    float4* tab = cv.take<float4>(256);
+    float2* vp = cv.take<float2>(n);
+    float* Cf = cv.take<float>(n);
+    A.bar = cv.take<unsigned>(2);
+    A.err = cv.take<int>(1);
     A.n = n;
     A.ldk = ldk;
     A.T = P.T;
@@ -645,97 +772,66 @@ sa_status scale_newton(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, 
     A.R = P.R;
     A.rows_per = P.rows_per;
 
-    rc = ctx->pinned.reserve(2 * align_up(sizeof(NtCtl), 64));
-    if (rc) return rc;
-    NtCtl* h_ctl[2] = {(NtCtl*)ctx->pinned.ptr, (NtCtl*)((char*)ctx->pinned.ptr + align_up(sizeof(NtCtl), 64))};
-
     const int k0 = o->resume_from > 0 ? o->resume_from : 0;
     if (k0 == 0) {
         SA_CUDA(cudaMemsetAsync(U, 0, n * sizeof(double), st));
         SA_CUDA(cudaMemsetAsync(V, 0, n * sizeof(double), st));
     }
-    nt_ltab_kernel<<<32768 / 256, 256, 0, st>>>(ltab);
+    SA_CUDA(cudaMemsetAsync(A.err, 0, sizeof(int), st));
+    SA_CUDA(cudaMemsetAsync(d_out, 0, o->n_p * sizeof(NtOut), st));
+    nt_tab_kernel<<<1, 256, 0, st>>>(tab);
     count_launch();
-    cudaEvent_t ev0, ev1, evb[2];
+    cudaEvent_t ev0, ev1;
     SA_CUDA(cudaEventCreate(&ev0));
     SA_CUDA(cudaEventCreate(&ev1));
-    SA_CUDA(cudaEventCreateWithFlags(&evb[0], cudaEventDisableTiming));
-    SA_CUDA(cudaEventCreateWithFlags(&evb[1], cudaEventDisableTiming));
-    auto destroy = [&]() {
-        cudaEventDestroy(ev0);
-        cudaEventDestroy(ev1);
-        cudaEventDestroy(evb[0]);
-        cudaEventDestroy(evb[1]);
-    };
     SA_CUDA(cudaEventRecord(ev0, st));
-    int64_t total = 0;
-    int conv = 1, nonfinite = 0;
-    double last_res = 0.0;
     for (int k = k0; k < o->n_p; ++k) {
         const double p = o->p[k];
         if (k > 0 && !o->warm_keep_v) launch_scale_vec(V, n, p / o->p[k - 1], st);
-        if (a->wtype == SA_I16)
-            nt_rowmax_kernel<int16_t><<<(n + 7) / 8, 256, 0, st>>>((const int16_t*)a->w, n, a->ld, p, V, ltab, C);
-        else
-            nt_rowmax_kernel<int32_t><<<(n + 7) / 8, 256, 0, st>>>((const int32_t*)a->w, n, a->ld, p, V, ltab, C);
-        if (a->wtype == SA_I16) launch_eval<int16_t>(P, a, p, V, C, ltab, A, st);
-        else launch_eval<int32_t>(P, a, p, V, C, ltab, A, st);
-        nt_init_kernel<<<std::max(1, std::min((2 * n + 255) / 256, 4 * ctx->num_sms)), 256, 0, st>>>(
-            A, o->tol, o->max_sweeps_per_p);
-        count_launch(3);
-        cudaError_t le = cudaGetLastError();
-        if (le != cudaSuccess) { destroy(); return cuda_fail(le, "newton evaluation"); }
-        // batches of steps; at most two in flight, polled through pinned copies
-        const int max_batches = (o->max_sweeps_per_p + 2) / kNtBatch + 3;
-        int issued = 0, polled = 0;
-        bool done = false;
-        auto issue = [&]() -> sa_status {
-            for (int b = 0; b < kNtBatch; ++b) {
-                launch_matvec(P, A, st);
-                nt_fin_kernel<<<P.nb_fin, kNtThreads, 0, st>>>(A);
-                nt_upd_kernel<<<P.nb_upd, kNtThreads, 0, st>>>(A);
-            }
-            count_launch(3 * kNtBatch);
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) return cuda_fail(e, "newton step");
-            SA_CUDA(cudaMemcpyAsync(h_ctl[issued & 1], A.ctl, sizeof(NtCtl), cudaMemcpyDeviceToHost, st));
-            SA_CUDA(cudaEventRecord(evb[issued & 1], st));
-            ++issued;
-            return SA_OK;
-        };
-        while (!done) {
-            while (issued - polled < 2 && issued < max_batches) {
-                if ((rc = issue())) { destroy(); return rc; }
-            }
-            if (polled == issued) break;
-            cudaError_t e = cudaEventSynchronize(evb[polled & 1]);
-            if (e != cudaSuccess) { destroy(); return cuda_fail(e, "newton poll"); }
-            done = h_ctl[polled & 1]->mode == kNtDone;
-            ++polled;
+        const float ph = (float)p, pl = (float)(p - (double)ph);
+        nt_vsplit_kernel<<<(n + 255) / 256, 256, 0, st>>>(V, vp, n);
+        if (a->wtype == SA_I16) {
+            const int16_t* w = (const int16_t*)a->w;
+            nt_rowmax_kernel<int16_t><<<(n + 7) / 8, 256, 0, st>>>(w, n, a->ld, ph, vp, Cf, C);
+            if (P.ch == 1) nt_kwrite_kernel<int16_t, 1><<<P.grid, kNtThreads, 0, st>>>(w, a->ld, ph, pl, vp, Cf, tab, A);
+            else if (P.ch == 2) nt_kwrite_kernel<int16_t, 2><<<P.grid, kNtThreads, 0, st>>>(w, a->ld, ph, pl, vp, Cf, tab, A);
+            else nt_kwrite_kernel<int16_t, 4><<<P.grid, kNtThreads, 0, st>>>(w, a->ld, ph, pl, vp, Cf, tab, A);
+        } else {
+            const int32_t* w = (const int32_t*)a->w;
+            nt_rowmax_kernel<int32_t><<<(n + 7) / 8, 256, 0, st>>>(w, n, a->ld, ph, vp, Cf, C);
+            if (P.ch == 1) nt_kwrite_kernel<int32_t, 1><<<P.grid, kNtThreads, 0, st>>>(w, a->ld, ph, pl, vp, Cf, tab, A);
+            else if (P.ch == 2) nt_kwrite_kernel<int32_t, 2><<<P.grid, kNtThreads, 0, st>>>(w, a->ld, ph, pl, vp, Cf, tab, A);
+            else nt_kwrite_kernel<int32_t, 4><<<P.grid, kNtThreads, 0, st>>>(w, a->ld, ph, pl, vp, Cf, tab, A);
         }
-        SA_CUDA(cudaStreamSynchronize(st));
-        const NtCtl& c = *h_ctl[(polled - 1) & 1];
-        if (c.mode != kNtDone) {
-            destroy();
-            set_error("newton scaling: the step at p = %g did not end within its matvec cap", p);
-            return SA_E_NOT_CONVERGED;
-        }
-        total += c.matvecs;
-        last_res = c.res;
-        if (c.status == kNtNonfinite) {
-            nonfinite = 1;
-            conv = 0;
-            break;
-        }
-        if (c.status != kNtConverged) conv = 0;
+        nt_init_kernel<<<(n + 31) / 32 + (n + kNtThreads - 1) / kNtThreads, kNtThreads, 0, st>>>(A);
+        count_launch(4);
+        SA_CUDA(cudaMemsetAsync(A.bar, 0, 2 * sizeof(unsigned), st));
+        rc = launch_solve(P, A, o->tol, o->max_sweeps_per_p, d_out + k, st);
+        if (rc) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); return rc; }
         nt_potentials_kernel<<<(n + 255) / 256, 256, 0, st>>>(A.x, C, U, V, n);
         count_launch();
     }
     SA_CUDA(cudaEventRecord(ev1, st));
+    rc = ctx->pinned.reserve(64 + (size_t)o->n_p * sizeof(NtOut));
+    if (rc) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); return rc; }
+    int* h_err = (int*)ctx->pinned.ptr;
+    NtOut* h_out = (NtOut*)((char*)ctx->pinned.ptr + 64);
+    SA_CUDA(cudaMemcpyAsync(h_err, A.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaMemcpyAsync(h_out, d_out, o->n_p * sizeof(NtOut), cudaMemcpyDeviceToHost, st));
     SA_CUDA(cudaStreamSynchronize(st));
     float kms = 0.0f;
     SA_CUDA(cudaEventElapsedTime(&kms, ev0, ev1));
-    destroy();
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    int64_t total = 0;
+    int conv = 1, nonfinite = 0;
+    double last_res = 0.0;
+    for (int k = k0; k < o->n_p; ++k) {
+        total += h_out[k].matvecs;
+        last_res = h_out[k].res;
+        if (h_out[k].status != kNtConverged) conv = 0;
+        if (h_out[k].status == kNtNonfinite) nonfinite = 1;
+    }
     if (info) {
         info->sweeps_total = total;
         info->residual = last_res;
@@ -747,6 +843,10 @@ sa_status scale_newton(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, 
         info->kernel_ms = kms;
         info->sparse_epochs = 0;
         info->reanchors = 0;
+    }
+    if (*h_err == kErrTimeout) {
+        set_error("newton scaling: a bounded grid-barrier wait timed out (grid of %d blocks)", P.grid);
+        return SA_E_TIMEOUT;
     }
     if (nonfinite) {
         set_error("newton scaling: a row or column sum was zero or not finite (matrix without support?)");
