@@ -47,12 +47,13 @@ constexpr int kNtWarps = kNtThreads / 32;
 constexpr double kNtDelta = 0.1;     // smallest y kept by a Newton step
 constexpr double kNtEtaMax = 0.1;    // forcing term of the inner solve: eta = sqrt(res),
 constexpr double kNtEtaMin = 1e-3;   //   clamped to [kNtEtaMin, kNtEtaMax]
-constexpr int kNtCgCap = 200;        // CG iterations per Newton step
+constexpr int kNtCgCap = 50;         // CG iterations per Newton step (stagnation guard)
+constexpr int kNtStallWindow = 20;   // Newton steps without halving the residual end the p step
 constexpr int kNtStages = 6;         // cp.async pipeline depth of the matvec (rows in flight)
 constexpr int kNtMaxSmem = 200 * 1024;
 
 enum : int { kNtRes = 0, kNtCg = 1, kNtDone = 2 };
-enum : int { kNtRunning = 0, kNtConverged = 1, kNtCapped = 2, kNtNonfinite = 3 };
+enum : int { kNtRunning = 0, kNtConverged = 1, kNtCapped = 2, kNtNonfinite = 3, kNtStalled = 4 };
 
 // Scalar state of the iteration; every block holds an identical copy in shared memory.
 struct NtState {
@@ -65,7 +66,9 @@ struct NtState {
     int matvecs;     // operator applications in this p step
     int cg_it;
     int newton_it;
+    int stall;       // Newton steps since the residual last fell below half of res_ref
     double tau, res, gamma, gamma0, gamma_prev, alpha, alpha_prev, beta, thr;
+    double res_ref;
 };
 
 // Result of one p step, written by block 0.
@@ -85,16 +88,20 @@ struct NtArgs {
     int W4;         // float4 chunks per column tile (<= threads x CH)
     int R;          // row stripes
     int rows_per;
-    // vectors of 2n FP32 entries (rows | columns); GB300 runs FP64 arithmetic at a small
-    // fraction of the FP32 rate, so FP64 is kept to the block partials and the scalars
-    float* x;       // rho | kappa
-    float* v;       // D(x) S x
-    float* y;
-    float* r;
-    float* pd;
-    float* s;
-    float* w;
-    float* prt;     // T x n row partials
+    // vectors of 2n entries (rows | columns) in FP64, each updated only by the block that
+    // owns the entry (a few dozen per block); the matvec reads FP32 copies of x, y and r,
+    // as GB300 runs FP64 arithmetic at a small fraction of the FP32 rate
+    double* x;      // rho | kappa
+    double* v;      // D(x) S x
+    double* y;
+    double* r;
+    double* pd;
+    double* s;
+    double* w;
+    float* xf;      // FP32 copies of x, y, r
+    float* yf;
+    float* rf;
+    double* prt;    // T x n row partials
     float* pc;      // R x ldk column partials
     double* bred;   // finalisation block partials (4 per block)
     double* cred;   // update block partials (4 per block)
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(kNtThreads) nt_kwrite_kernel(const WT* __restr
 // over the 8 warps of the block; each lane issues its loads in batches of 24 independent
 // loads.
 template <bool MAX>
-__device__ __forceinline__ float nt_stripes(const float* __restrict__ pc, int R, int ldk, int j, int wid) {
+__device__ __forceinline__ double nt_stripes(const float* __restrict__ pc, int R, int ldk, int j, int wid) {
     constexpr int kB = 24;
     float acc = 0.0f, comp = 0.0f;   // 0 is also the identity of the max: the partials are >= 0
     for (int base = wid; base < R; base += kNtWarps * kB) {
@@ -256,7 +263,7 @@ __device__ __forceinline__ float nt_stripes(const float* __restrict__ pc, int R,
             }
         }
     }
-    return acc;
+    return MAX ? (double)acc : (double)acc - (double)comp;   // the compensated sum in FP64
 }
 
 // 16-byte asynchronous copy global -> shared (cp.async, cached in L2 only) and its groups
@@ -279,19 +286,24 @@ __global__ void __launch_bounds__(kNtThreads) nt_init_kernel(NtArgs A) {
     const int nbc = (n + 31) / 32;
     if ((int)blockIdx.x < nbc) {
         const int j = blockIdx.x * 32 + lane;
-        sred[wid][lane] = j < n ? nt_stripes<true>(A.pc, A.R, A.ldk, j, wid) : 0.0f;
+        sred[wid][lane] = j < n ? (float)nt_stripes<true>(A.pc, A.R, A.ldk, j, wid) : 0.0f;
         __syncthreads();
         if (wid == 0 && j < n) {
             float m = 0.0f;
             for (int x = 0; x < kNtWarps; ++x) m = fmaxf(m, sred[x][lane]);
-            A.x[n + j] = 1.0f / m;   // +inf for an empty column: caught by the first residual
-            A.y[n + j] = 1.0f;
+            const double k = 1.0 / (double)m;   // +inf for an empty column: caught by the first residual
+            A.x[n + j] = k;
+            A.xf[n + j] = (float)k;
+            A.y[n + j] = 1.0;
+            A.yf[n + j] = 1.0f;
         }
     } else {
         const int i = (blockIdx.x - nbc) * kNtThreads + tid;
         if (i < n) {
-            A.x[i] = 1.0f;
-            A.y[i] = 1.0f;
+            A.x[i] = 1.0;
+            A.xf[i] = 1.0f;
+            A.y[i] = 1.0;
+            A.yf[i] = 1.0f;
         }
     }
 }
@@ -363,11 +375,22 @@ __device__ __forceinline__ void nt_after_fin(NtState& S, bool res_mode, double g
     } else if (res_mode) {
         S.res = g0;
         S.apply = 0;
+        // stall guard: the FP32 operator limits how far Newton gets on nearly decomposable
+        // X(p) (Sec. 3.1); without progress the step ends instead of cycling to the cap
+        if (S.matvecs == 1 || g0 <= 0.5 * S.res_ref) {
+            S.res_ref = g0;
+            S.stall = 0;
+        } else {
+            S.stall += 1;
+        }
         if (g0 <= tol) {
             S.status = kNtConverged;
             S.mode = kNtDone;
         } else if (S.matvecs >= cap) {
             S.status = kNtCapped;
+            S.mode = kNtDone;
+        } else if (S.stall >= kNtStallWindow) {
+            S.status = kNtStalled;
             S.mode = kNtDone;
         } else {
             const double eta = fmin(kNtEtaMax, fmax(kNtEtaMin, sqrt(g0)));
@@ -419,7 +442,7 @@ __device__ __forceinline__ void nt_after_upd(NtState& S, double g0, double g1, i
 // the stripe, the stripe's row factors and the totals of the owned entries.
 __host__ __device__ inline size_t nt_smem_bytes(int ch, int rows_per, int own) {
     return (size_t)kNtStages * ch * kNtThreads * 16 + (size_t)rows_per * kNtWarps * 4 + (size_t)rows_per * 4 +
-           (size_t)2 * own * 4;
+           8 + (size_t)2 * own * 8;
 }
 
 // One p step of the Newton-CG iteration on K.  Block (s, t) = (blockIdx / T, blockIdx % T)
@@ -429,7 +452,7 @@ __host__ __device__ inline size_t nt_smem_bytes(int ch, int rows_per, int own) {
 template <int CH>
 __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, double tol, int cap,
                                                                  NtOut* out) {
-    __shared__ float sred[kNtWarps][33];
+    __shared__ double sred[kNtWarps][33];
     __shared__ float sh[3][kNtWarps];
     __shared__ NtState S;
     extern __shared__ __align__(16) unsigned char nt_dyn[];
@@ -444,7 +467,7 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
     float4* stage = (float4*)nt_dyn;                                   // [stages][CH][threads]
     float* rowdot = (float*)(stage + kNtStages * CH * kNtThreads);     // [rows_per][warps]
     float* zr_s = rowdot + A.rows_per * kNtWarps;                      // [rows_per]
-    float* tot_s = zr_s + A.rows_per;                                  // [2 cs]
+    double* tot_s = (double*)(((uintptr_t)(zr_s + A.rows_per) + 7) & ~(uintptr_t)7);   // [2 cs]
     if (tid == 0) {
         NtState z{};
         z.mode = kNtRes;
@@ -478,18 +501,18 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
                     const int j = 4 * q[k] + e;
                     float zv = 0.0f;
                     if (j < n) {
-                        float xe = A.x[n + j];
-                        if (apply) xe *= fmaf(tau, A.y[n + j] - 1.0f, 1.0f);
-                        zv = res_mode ? xe : xe * A.r[n + j];
+                        float xe = A.xf[n + j];
+                        if (apply) xe *= fmaf(tau, A.yf[n + j] - 1.0f, 1.0f);
+                        zv = res_mode ? xe : xe * A.rf[n + j];
                     }
                     z[4 * k + e] = zv;
                     acc[4 * k + e] = 0.0f;
                 }
             }
             for (int i = tid; i < nrows; i += kNtThreads) {
-                float xe = A.x[r0 + i];
-                if (apply) xe *= fmaf(tau, A.y[r0 + i] - 1.0f, 1.0f);
-                zr_s[i] = res_mode ? xe : xe * A.r[r0 + i];
+                float xe = A.xf[r0 + i];
+                if (apply) xe *= fmaf(tau, A.yf[r0 + i] - 1.0f, 1.0f);
+                zr_s[i] = res_mode ? xe : xe * A.rf[r0 + i];
             }
             __syncthreads();
 #pragma unroll
@@ -525,9 +548,9 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
             cp_async_wait<0>();
             __syncthreads();
             for (int i = tid; i < nrows; i += kNtThreads) {
-                float sm = 0.0f;
+                double sm = 0.0;
 #pragma unroll
-                for (int x = 0; x < kNtWarps; ++x) sm += rowdot[i * kNtWarps + x];
+                for (int x = 0; x < kNtWarps; ++x) sm += (double)rowdot[i * kNtWarps + x];
                 A.prt[(int64_t)t * n + r0 + i] = sm;
             }
 #pragma unroll
@@ -541,44 +564,50 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
         {
             for (int cb = c0; cb < c1; cb += 32) {
                 const int j = cb + lane;
-                sred[wid][lane] = j < c1 ? nt_stripes<false>(A.pc, A.R, A.ldk, j, wid) : 0.0f;
+                sred[wid][lane] = j < c1 ? nt_stripes<false>(A.pc, A.R, A.ldk, j, wid) : 0.0;
                 __syncthreads();
                 if (wid == 0 && j < c1) {
-                    float tot = 0.0f;
+                    double tot = 0.0;
                     for (int x = 0; x < kNtWarps; ++x) tot += sred[x][lane];
                     tot_s[j - c0] = tot;
                 }
                 __syncthreads();
             }
             for (int i = c0 + tid; i < c1; i += kNtThreads) {
-                float tot = 0.0f;
+                double tot = 0.0;
                 for (int tt = 0; tt < A.T; ++tt) tot += A.prt[(int64_t)tt * n + i];
                 tot_s[own + (i - c0)] = tot;
             }
             __syncthreads();
             // residual step: a0 = max |v - 1|, a1 = sum (1 - v)^2, a2 = min v (or -1 for a
             // zero or non-finite sum); CG step: a0 = sum w r, a2 = -1 for a non-finite w
+            // the owned entries in FP64 (a few dozen per block)
             float a0 = 0.0f, a1 = 0.0f, a2 = INFINITY;
+            const double taud = S.tau;
             for (int x = tid; x < 2 * own; x += kNtThreads) {
                 const int e = x < own ? n + c0 + x : c0 + (x - own);
-                float xe = A.x[e];
+                double xe = A.x[e];
                 if (apply) {
-                    xe *= fmaf(tau, A.y[e] - 1.0f, 1.0f);
+                    xe *= 1.0 + taud * (A.y[e] - 1.0);
                     A.x[e] = xe;
+                    A.xf[e] = (float)xe;
                 }
-                const float m = xe * tot_s[x];
+                const double m = xe * tot_s[x];
                 if (res_mode) {
+                    const double re = 1.0 - m;
                     A.v[e] = m;
-                    A.r[e] = 1.0f - m;
-                    A.y[e] = 1.0f;
-                    a0 = fmaxf(a0, fabsf(m - 1.0f));
-                    a1 = fmaf(1.0f - m, 1.0f - m, a1);
-                    a2 = fminf(a2, (m > 0.0f && m < INFINITY) ? m : -1.0f);
+                    A.r[e] = re;
+                    A.rf[e] = (float)re;
+                    A.y[e] = 1.0;
+                    A.yf[e] = 1.0f;
+                    a0 = fmaxf(a0, (float)fabs(re));
+                    a1 += (float)(re * re);
+                    a2 = fminf(a2, (m > 0.0 && m < INFINITY) ? (float)m : -1.0f);
                 } else {
-                    const float re = A.r[e];
-                    const float we = fmaf(A.v[e], re, m);
+                    const double re = A.r[e];
+                    const double we = m + A.v[e] * re;
                     A.w[e] = we;
-                    a0 = fmaf(we, re, a0);
+                    a0 += (float)(we * re);
                     a2 = fminf(a2, (we > -INFINITY && we < INFINITY) ? 1.0f : -1.0f);
                 }
             }
@@ -605,21 +634,23 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
         // ---- CG update of the owned entries: p, s (= M p), y, r ----
         {
             const bool first = S.first != 0;
-            const float alpha = (float)S.alpha, beta = (float)S.beta;
+            const double alpha = S.alpha, beta = S.beta;
             float rr = 0.0f, ymin = INFINITY;
             for (int x = tid; x < 2 * own; x += kNtThreads) {
                 const int e = x < own ? n + c0 + x : c0 + (x - own);
-                const float re = A.r[e], we = A.w[e];
-                const float pe = first ? re : fmaf(beta, A.pd[e], re);
-                const float se = first ? we : fmaf(beta, A.s[e], we);
-                const float ye = fmaf(alpha, pe, A.y[e]);
-                const float rn = fmaf(-alpha, se, re);
+                const double re = A.r[e], we = A.w[e];
+                const double pe = first ? re : re + beta * A.pd[e];
+                const double se = first ? we : we + beta * A.s[e];
+                const double ye = A.y[e] + alpha * pe;
+                const double rn = re - alpha * se;
                 A.pd[e] = pe;
                 A.s[e] = se;
                 A.y[e] = ye;
+                A.yf[e] = (float)ye;
                 A.r[e] = rn;
-                rr = fmaf(rn, rn, rr);
-                ymin = fminf(ymin, ye);
+                A.rf[e] = (float)rn;
+                rr += (float)(rn * rn);
+                ymin = fminf(ymin, (float)ye);
             }
             double b0, b1, b2;
             nt_block_reduce3<false>(rr, 0.0f, ymin, sh, &b0, &b1, &b2);
@@ -649,12 +680,12 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
 }
 
 // potentials of X = D(rho) K D(kappa) in log2 units: U = C - log2 rho, V -= log2 kappa
-__global__ void nt_potentials_kernel(const float* __restrict__ x, const double* __restrict__ C,
+__global__ void nt_potentials_kernel(const double* __restrict__ x, const double* __restrict__ C,
                                      double* __restrict__ U, double* __restrict__ V, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        U[i] = C[i] - log2((double)x[i]);
-        V[i] = V[i] - log2((double)x[n + i]);
+        U[i] = C[i] - log2(x[i]);
+        V[i] = V[i] - log2(x[n + i]);
     }
 }
 
@@ -733,8 +764,9 @@ sa_status scale_newton(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, 
     const int ldk = (int)align_up((size_t)n, 4);
     const size_t bytes = align_up((size_t)n * ldk * 4, 256)       // K
                        + align_up((size_t)n * 8, 256)              // C
-                       + 7 * align_up((size_t)2 * n * 4, 256)      // x v y r p s w
-                       + align_up((size_t)P.T * n * 4, 256)        // row partials
+                       + 7 * align_up((size_t)2 * n * 8, 256)      // x v y r p s w
+                       + 3 * align_up((size_t)2 * n * 4, 256)      // FP32 copies of x y r
+                       + align_up((size_t)P.T * n * 8, 256)        // row partials
                        + align_up((size_t)P.R * ldk * 4, 256)      // column partials
                        + 2 * align_up((size_t)P.grid * 32, 256)    // block partials
                        + align_up((size_t)o->n_p * sizeof(NtOut), 256)
@@ -748,14 +780,17 @@ sa_status scale_newton(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, 
     NtArgs A{};
     A.K = cv.take<float>((size_t)n * ldk);
     double* C = cv.take<double>(n);
-    A.x = cv.take<float>(2 * (size_t)n);
-    A.v = cv.take<float>(2 * (size_t)n);
-    A.y = cv.take<float>(2 * (size_t)n);
-    A.r = cv.take<float>(2 * (size_t)n);
-    A.pd = cv.take<float>(2 * (size_t)n);
-    A.s = cv.take<float>(2 * (size_t)n);
-    A.w = cv.take<float>(2 * (size_t)n);
-    A.prt = cv.take<float>((size_t)P.T * n);
+    A.x = cv.take<double>(2 * (size_t)n);
+    A.v = cv.take<double>(2 * (size_t)n);
+    A.y = cv.take<double>(2 * (size_t)n);
+    A.r = cv.take<double>(2 * (size_t)n);
+    A.pd = cv.take<double>(2 * (size_t)n);
+    A.s = cv.take<double>(2 * (size_t)n);
+    A.w = cv.take<double>(2 * (size_t)n);
+    A.xf = cv.take<float>(2 * (size_t)n);
+    A.yf = cv.take<float>(2 * (size_t)n);
+    A.rf = cv.take<float>(2 * (size_t)n);
+    A.prt = cv.take<double>((size_t)P.T * n);
     A.pc = cv.take<float>((size_t)P.R * ldk);
     A.bred = cv.take<double>((size_t)P.grid * 4);
     A.cred = cv.take<double>((size_t)P.grid * 4);
