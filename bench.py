@@ -50,18 +50,20 @@ def load_peaks():
 # capture was taken on: after any change to these files the figure is unknown (null).
 _TRAFFIC = {
     # step kernel: planted n=8192 int16, p=256 from a cold start, 200 sweeps + 1 evaluation of K
-    (3, 8192, 2): (55.163e9 / 200, "ncu capture, planted n=8192 int16, p=256, 200 sweeps (one launch)",
+    (3, 8192, 2): ((53.879e9 + 1.283e9) / 200, "ncu capture, planted n=8192 int16, p=256, 200 sweeps (one launch)",
                    {"paper_1104_3830_gb300/csrc/sweep_step.cu":
-                    "1c881b89f5f8b2e693d096369ebd91441a13d7e1cc5b79d7fbfecff60f3e44a9",
+                    "bb5810e89521b7cb691ab11040c5de960f4deb8dabb2465ed419d6c1c09c92b6",
                     "paper_1104_3830_gb300/csrc/common.cuh":
-                    "a6671f98cbd36384cd1797923d09a590dde55eb3479341ec323ebc1b9836442c"}),
+                    "a6671f98cbd36384cd1797923d09a590dde55eb3479341ec323ebc1b9836442c",
+                    "paper_1104_3830_gb300/csrc/log2pair.cuh":
+                    "d0d997e23dba7b51d1c07b556aa6d5e60d23cf230a79b17de392b2f3074ae3d0"}),
 }
 
 
 KERNEL_NAMES = {1: "fused_kernel (single-read persistent sweep, SFU exp2/log2 per element)",
                 2: "row_lse_kernel + col_partial_kernel (plain sweep, host loop)",
                 3: "step_kernel (persistent sweep over the per-step FP32 matrix)",
-                4: "nt_matvec_kernel + nt_fin_kernel + nt_upd_kernel (Newton-CG, one read of K per operator application)"}
+                4: "nt_solve_kernel (persistent Newton-CG over the per-step FP32 matrix, one read per operator application)"}
 
 
 def measured_traffic(kernel_used, n, wbytes):
@@ -473,6 +475,8 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=96)
     ap.add_argument("--serve-dist", default="uniform", choices=["uniform", "zipf"])
     ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--no-newton", action="store_true",
+                    help="skip the Newton-path time-to-solution measurement beside the main line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -578,6 +582,27 @@ def main():
     d2h = n * 8 + (r2["nnz_final"] + r2["nnz_first"]) * 8 + 8 * (n + 1)
     e2e = {"value": e2e_val, "unit": "sweeps/s", "h2d_bytes_per_step": int(w.nbytes), "d2h_bytes_per_step": int(d2h)}
 
+    # the Newton variant (Sec. 5.3) on the same instance: time to the same certified result
+    newton = None
+    if not args.no_newton and args.kernel in ("auto", "step"):
+        for _ in range(2):
+            api.sa_assign(ctx, d, ps, 1e-6, args.max_sweeps, kernel="newton")
+        nt_t, nt_reads, rn = [], 0, None
+        for _ in range(3):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rn = api.sa_assign(ctx, d, ps, 1e-6, args.max_sweeps, kernel="newton")
+            e1.record(stream)
+            e1.synchronize()
+            nt_t.append(e0.elapsed_time(e1))
+            nt_reads += rn["scale"]["sweeps_total"]
+        newton = {"kernel": KERNEL_NAMES[4], "ms_per_assign": statistics.mean(nt_t),
+                  "reads_of_K_per_assign": nt_reads / 3, "converged": rn["scale"]["converged"],
+                  "gamma": rn["gamma"], "ms_scale": rn["ms_scale"],
+                  "sinkhorn_ms_per_assign": total_ms / args.steps}
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -589,6 +614,8 @@ def main():
                                ms_scale=res["ms_scale"], ms_prune=res["ms_prune"], ms_solve=res["ms_solve"],
                                ms_certify=res["ms_certify"], converged=res["scale"]["converged"]),
                 "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
+        if newton is not None:
+            line["newton_variant"] = newton
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, ps)
         print(json.dumps(line), flush=True)

@@ -131,19 +131,23 @@ __global__ void nt_vsplit_kernel(const double* __restrict__ V, float2* __restric
 }
 
 // C_i = max_j (p log2 w_ij - V_j) over w_ij > 0 to about 1e-4 (SFU log2; C_i only sets the
-// scale of row i of K); one warp per row
+// scale of row i of K); one warp per row, 16-byte loads (8 int16 or 4 int32 weights)
 template <typename WT>
 __global__ void nt_rowmax_kernel(const WT* __restrict__ w, int n, int64_t ld, float ph,
                                  const float2* __restrict__ vp, float* __restrict__ Cf,
                                  double* __restrict__ C) {
+    constexpr int kV = 16 / sizeof(WT);
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= n) return;
     const WT* wr = w + (int64_t)row * ld;
     float m = -INFINITY;
-    for (int j = lane; j < n; j += 32) {
-        const int wv = (int)wr[j];
-        if (wv > 0) m = fmaxf(m, fmaf(ph, __log2f((float)wv), -vp[j].x));
+    for (int j0 = kV * lane; j0 < n; j0 += 32 * kV) {
+        WT wv[kV];
+        *(int4*)wv = *(const int4*)(wr + j0);   // j0 + kV <= ld: ld * sizeof(WT) is a multiple of 16
+#pragma unroll
+        for (int e = 0; e < kV; ++e)
+            if (j0 + e < n && wv[e] > 0) m = fmaxf(m, fmaf(ph, __log2f((float)wv[e]), -vp[j0 + e].x));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -171,8 +175,9 @@ __device__ __forceinline__ void load4(const int32_t* p, int v[4]) {
 
 // K_ij = 2^d with d = p log2 w_ij - V_j - C_i evaluated in float pairs: the leading parts
 // cancel exactly (two-product, two-sums) and the small ones are added after, so d is exact
-// to about 2^-24 |d|; pad columns and zero weights give 0.  Also the column maxima of K
-// over each row stripe (pc), from which the starting kappa is taken.
+// to about 2^-24 |d|, and one SFU exp2 (2^-22) follows; pad columns and zero weights give
+// 0.  Also the column maxima of K over each row stripe (pc), from which the starting kappa
+// is taken.
 template <typename WT, int CH>
 __global__ void __launch_bounds__(kNtThreads) nt_kwrite_kernel(const WT* __restrict__ w, int64_t ld,
                                                                float ph, float pl,
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(kNtThreads) nt_kwrite_kernel(const WT* __restr
                     const float s1 = two_sum(tp, -v2.x, &e1);
                     const float s2 = two_sum(s1, -ci, &e2);
                     const float rest = ((te + e1) + e2) + (fmaf(ph, lw.y, pl * lw.x) - v2.y);
-                    kv[e] = exp2f(s2 + rest);
+                    kv[e] = ex2_approx(s2 + rest);   // SFU exp2, relative error about 2^-22
                 }
                 cm[4 * k + e] = fmaxf(cm[4 * k + e], kv[e]);
             }
