@@ -131,23 +131,19 @@ __global__ void nt_vsplit_kernel(const double* __restrict__ V, float2* __restric
 }
 
 // C_i = max_j (p log2 w_ij - V_j) over w_ij > 0 to about 1e-4 (SFU log2; C_i only sets the
-// scale of row i of K); one warp per row, 16-byte loads (8 int16 or 4 int32 weights)
+// scale of row i of K); one warp per row
 template <typename WT>
 __global__ void nt_rowmax_kernel(const WT* __restrict__ w, int n, int64_t ld, float ph,
                                  const float2* __restrict__ vp, float* __restrict__ Cf,
                                  double* __restrict__ C) {
-    constexpr int kV = 16 / sizeof(WT);
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= n) return;
     const WT* wr = w + (int64_t)row * ld;
     float m = -INFINITY;
-    for (int j0 = kV * lane; j0 < n; j0 += 32 * kV) {
-        WT wv[kV];
-        *(int4*)wv = *(const int4*)(wr + j0);   // j0 + kV <= ld: ld * sizeof(WT) is a multiple of 16
-#pragma unroll
-        for (int e = 0; e < kV; ++e)
-            if (j0 + e < n && wv[e] > 0) m = fmaxf(m, fmaf(ph, __log2f((float)wv[e]), -vp[j0 + e].x));
+    for (int j = lane; j < n; j += 32) {
+        const int wv = (int)wr[j];
+        if (wv > 0) m = fmaxf(m, fmaf(ph, __log2f((float)wv), -vp[j].x));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
