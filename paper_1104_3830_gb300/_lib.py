@@ -55,6 +55,12 @@ class sa_csr(ctypes.Structure):
                 ("col", ctypes.POINTER(ctypes.c_int32)), ("w", ctypes.POINTER(ctypes.c_int32))]
 
 
+class sa_auction_info(ctypes.Structure):
+    _fields_ = [("phases", ctypes.c_int32), ("rounds", ctypes.c_int64), ("complete", ctypes.c_int32),
+                ("auction_sum_log_w", ctypes.c_double), ("eps_final", ctypes.c_double),
+                ("auction_ms", ctypes.c_double), ("host_ms", ctypes.c_double)]
+
+
 class sa_assign_result(ctypes.Structure):
     _fields_ = [("perm", ctypes.POINTER(ctypes.c_int32)), ("sum_log_w", ctypes.c_double),
                 ("log_ub", ctypes.c_double), ("gamma", ctypes.c_double), ("nnz_first", ctypes.c_int64),
@@ -100,6 +106,8 @@ SIGNATURES = {
     "sa_prune": (ctypes.c_int, [_VP, ctypes.POINTER(sa_matrix), ctypes.c_double, _VP, _VP, ctypes.c_double,
                                 ctypes.c_int32, ctypes.POINTER(sa_csr), _DP]),
     "sa_solve_reduced": (ctypes.c_int, [ctypes.POINTER(sa_csr), _I32P, _DP, _DP, _DP]),
+    "sa_solve_reduced_gpu": (ctypes.c_int, [_VP, ctypes.POINTER(sa_csr), _DP, _I32P, _DP, _DP, _DP,
+                                            ctypes.POINTER(sa_auction_info)]),
     "sa_certify": (ctypes.c_int, [_VP, ctypes.POINTER(sa_matrix), _DP, _DP, ctypes.c_double, _I64P,
                                   ctypes.c_int64, ctypes.POINTER(sa_csr)]),
     "sa_csr_free": (None, [ctypes.POINTER(sa_csr)]),

@@ -158,6 +158,28 @@ def sa_solve_reduced(row_ptr, col, w, n=None):
     return perm, s.value, al, be
 
 
+def sa_solve_reduced_gpu(ctx: Context, row_ptr, col, w, price0=None, n=None):
+    """Exact solve of a CSR instance with GPU-auction prices first: (perm, sum_log_w, alpha,
+    beta, info)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.int32)
+    n = len(row_ptr) - 1 if n is None else n
+    c = L.sa_csr(n, len(col), row_ptr.ctypes.data_as(L._I64P), col.ctypes.data_as(L._I32P),
+                 w.ctypes.data_as(L._I32P))
+    perm = np.zeros(n, dtype=np.int32)
+    s = ctypes.c_double()
+    al = np.zeros(n)
+    be = np.zeros(n)
+    info = L.sa_auction_info()
+    p0 = None if price0 is None else np.ascontiguousarray(price0, dtype=np.float64)
+    check(lib().sa_solve_reduced_gpu(ctx.handle, ctypes.byref(c), None if p0 is None else p0.ctypes.data_as(L._DP),
+                                     perm.ctypes.data_as(L._I32P), ctypes.byref(s), al.ctypes.data_as(L._DP),
+                                     be.ctypes.data_as(L._DP), ctypes.byref(info)))
+    d = {k: getattr(info, k) for k, _ in info._fields_}
+    return perm, s.value, al, be, d
+
+
 def sa_certify(ctx: Context, w, alpha, beta, tau=1e-9, max_add=1 << 16):
     """(number of dual violations on A, CSR of up to max_add of them)."""
     m = matrix(w)

@@ -63,6 +63,7 @@ struct sa_ctx {
     int fused_nt = 512;      // threads per block of the fused kernel when 512 < chunks <= 1024
                              // (256 or 512; SA_FUSED_NT in the environment overrides)
     int step_sparse = 0;     // step kernel: allow sparse epochs (SA_STEP_SPARSE=1 enables)
+    int solve_gpu = 0;       // sa_assign: reduced solve through the GPU auction (SA_SOLVE_GPU=1)
     sa::Workspace ws;        // scratch for sweeps, prune, certify
     sa::Workspace input;     // device copy of host inputs (sa_assign_host)
     sa::PinnedBuf pinned;    // staging for small device->host results
@@ -137,6 +138,11 @@ sa_status narrow_device(sa_ctx* ctx, const int32_t* src, int64_t lds, int16_t* d
 // Returns SA_OK / SA_E_NO_PERFECT_MATCHING.
 sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const double* logw,
                         int32_t* perm, double* alpha, double* beta, const double* price0 = nullptr);
+
+// auction.cu: eps-scaling forward auction on a device CSR (prices >= 0 in and out)
+sa_status auction_device(sa_ctx* ctx, int n, const int64_t* d_rp, const int32_t* d_col, const double* d_val,
+                         double eps0, double eps_final, int64_t max_rounds, double* d_price, int* d_assigned,
+                         int* phases, int64_t* rounds, int* complete);
 
 // csr helpers (api.cu)
 sa_status csr_alloc(sa_csr* c, int n, int64_t nnz);
