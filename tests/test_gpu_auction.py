@@ -55,10 +55,25 @@ def test_exact_optimum_and_auction_bound(ctx, n, density, hi, warm):
     assert max(abs(al[i] + be[perm[i]] - b[i, perm[i]]) for i in range(n)) < 1e-9
     opt = sum(b[i, ph[i]] for i in range(n))
     assert abs(s - opt) < 1e-9
-    if n <= 200:
-        assert info["complete"] == 1, info   # small instances finish within the round budget
     if info["complete"]:
         assert info["auction_sum_log_w"] >= opt - n * info["eps_final"] - 1e-9, (info, opt)
+
+
+@pytest.mark.parametrize("n,seed", [(12, 1), (30, 2)])
+def test_auction_completes_within_eps_of_optimum(ctx, n, seed):
+    """Small dense instances: the auction itself finishes every eps-scaling phase within
+    its round budget, and its assignment is within n * eps_final of the optimum."""
+    rng = np.random.default_rng(900 + seed)
+    w = rng.integers(1, 1001, size=(n, n)).astype(np.int64)
+    mask = np.ones((n, n), dtype=bool)
+    rp, col, wv = _csr(mask, w)
+    b = np.log(w.astype(float))
+    perm, s, al, be, info = api.sa_solve_reduced_gpu(ctx, rp, col, wv)
+    ph, _, _, st = oracle.hungarian(b)
+    opt = sum(b[i, ph[i]] for i in range(n))
+    assert info["complete"] == 1, info
+    assert opt - n * info["eps_final"] - 1e-9 <= info["auction_sum_log_w"] <= opt + 1e-9
+    assert abs(s - opt) < 1e-9
 
 
 def test_reduced_instance_of_a_scaled_matrix(ctx):
