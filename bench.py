@@ -500,6 +500,43 @@ def run_reduced(args):
                       "higher_is_better": False, "data": "synthetic", "results": out}), flush=True)
 
 
+def run_euclidean(args):
+    """The paper's Euclidean random matrix (Sec. 5; n = 1000, 2n points uniform in the unit
+    cube, a_ij = exp(-d), quantised to round(2^20 a_ij)) through Algorithm 1 with the
+    paper's settings (p = 100, 150, ... on the prescaled scale, eps = t = 1/n, stop at gamma
+    <= 2), with the Sinkhorn (step kernel) and the Newton scaling: gamma, final p, O(n^2)
+    operations (sweeps / reads of K), remaining entries and time, beside the paper's row
+    (Tables 1 and 3: gamma 1.728, p 200, 1416 Sinkhorn iterations / 742 Newton operations,
+    0.92 % remaining; a different random instance of the same distribution)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1104_3830_gb300 import api
+    from paper_1104_3830_gb300 import workloads as W
+    ctx = api.sa_create(0, torch.cuda.current_stream().cuda_stream)
+    n = 1000
+    w, _, _ = W.euclidean(n, 20261202 + 50)
+    d = api.to_device(w)
+    out = {}
+    for kernel in ("step", "newton"):
+        api.sa_algorithm1(ctx, d, opt_ratio=2.0, p0=100.0, dp=50.0, max_rounds=30, kernel=kernel,
+                          allow_not_converged=True)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = api.sa_algorithm1(ctx, d, opt_ratio=2.0, p0=100.0, dp=50.0, max_rounds=30, kernel=kernel,
+                              allow_not_converged=True)
+        t1 = time.perf_counter()
+        out[kernel] = {"gamma": g["gamma"], "p_final": g["p_final"], "rounds": g["rounds"],
+                       "operations": g["sweeps_total"], "remaining_pct": 100.0 * g["nnz"] / (n * n),
+                       "ms": (t1 - t0) * 1e3, "status": g["status"]}
+    ctx.close()
+    print(json.dumps({"metric": "Algorithm 1 on the Euclidean random matrix (Tables 1 and 3)", "unit": "ms",
+                      "higher_is_better": False, "data": "synthetic", "config": {"n": n, "opt_ratio": 2.0,
+                      "p0": 100.0, "dp": 50.0, "eps": "1/n", "t": "1/n"}, "results": out,
+                      "paper": {"gamma": 1.728, "p": 200, "sinkhorn_iterations": 1416, "newton_operations": 742,
+                                "remaining_pct": 0.92}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -531,6 +568,8 @@ def main():
         return run_precision(args)
     if args.workload == "reduced":
         return run_reduced(args)
+    if args.workload == "euclidean1000":
+        return run_euclidean(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -19,6 +19,10 @@ Workloads (n x n integer weights w_ij >= 1, a_ij = w_ij):
                                     pairs get all four cross entries at 10000, making
                                     2^pairs optimal permutations
 * ``zipf(n, s, hi, seed)``          Zipf(s) weights on {1..hi} by inverse CDF
+* ``euclidean(n, seed)``            the Euclidean random matrix of the paper's experiments:
+                                    2n points uniform in the unit cube, a_ij =
+                                    exp(-|x_i - y_j|), quantised to integers
+                                    w_ij = round(2^20 a_ij) (in [185000, 2^20])
 * ``loguniform_sizes(k, lo, hi, seed)`` instance sizes floor(exp(U(ln lo, ln(hi+1))))
 * ``poisson_arrivals(rate, duration, seed)`` arrival times with exponential gaps
 """
@@ -117,6 +121,20 @@ def zipf(n: int, s: float, hi: int, seed: int, dtype=np.int16, tag: int = 0) -> 
     u = uniform01(key, 0, n * n)
     idx = np.searchsorted(cdf, u, side="right")
     return (np.minimum(idx, hi - 1) + 1).astype(dtype).reshape(n, n)
+
+
+def euclidean(n: int, seed: int, scale: int = 1 << 20):
+    """n x n int32 weights round(scale * exp(-|x_i - y_j|)) for points x_i, y_j uniform in
+    the unit cube of R^3 (the Euclidean random matrix of the paper's experiments), and the
+    points (x, y).  The weights are the input's definition, quantised so that the integer
+    kernels take them: an optimum of w is within n * 1.1e-5 of the optimal total distance
+    (each log w is within 0.5 / (scale * e^-sqrt(3)) of -d)."""
+    key = stream_key(seed, 6, n)
+    pts = uniform01(key, 0, 6 * n).reshape(2, n, 3)
+    x, y = pts[0], pts[1]
+    d = np.sqrt(((x[:, None, :] - y[None, :, :]) ** 2).sum(axis=2))
+    w = np.maximum(1, np.rint(scale * np.exp(-d))).astype(np.int32)
+    return w, x, y
 
 
 def loguniform_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:

@@ -71,3 +71,20 @@ def test_not_converged_reports_last_round(ctx):
     assert g["status"] == api.SaError(-4, "").status and g["rounds"] == 2 and g["gamma"] > 1.0000001
     with pytest.raises(api.SaError):
         api.sa_algorithm1(ctx, d, opt_ratio=0.5)
+
+
+def test_euclidean_random_matrix_newton_matches_oracle(ctx):
+    """The paper's Euclidean random matrix (n = 200, weights round(2^20 exp(-d))) through
+    Algorithm 1 with the Newton kernel, against the oracle's Sinkhorn run to convergence
+    (same X(p) up to the tolerance, so the same rounds, p, B optimum and gamma)."""
+    w, _, _ = W.euclidean(200, 21)
+    d = api.to_device(w)
+    g = api.sa_algorithm1(ctx, d, opt_ratio=1.3, p0=100.0, dp=50.0, max_rounds=30, eps=1e-6, kernel="newton")
+    o = oracle.algorithm1(w, opt_ratio=1.3, p0=100.0, dp=50.0, max_rounds=30, eps=1e-6, max_sweeps=400000)
+    assert o["status"] == 0 and g["status"] == 0 and o["rounds"] == 2
+    assert g["rounds"] == o["rounds"] and g["p_final"] == o["p_final"]
+    b = oracle.log_weights(w.astype(np.int64))
+    gw = float(sum(b[i, g["perm"][i]] for i in range(200)))
+    assert abs(gw - o["log_w_B"]) < 1e-9
+    assert abs(np.log(g["gamma"]) - np.log(o["gamma"])) < 1e-4
+    assert g["sweeps_total"] < o["sweeps"] / 20   # Newton: far fewer reads than Sinkhorn sweeps

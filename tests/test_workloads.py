@@ -1,5 +1,6 @@
 """The seeded generators: reproducible, chunk-independent, and with the stated structure."""
 import numpy as np
+import pytest
 
 import oracle
 from paper_1104_3830_gb300 import workloads as W
@@ -39,3 +40,23 @@ def test_zipf_sizes_arrivals():
     assert n.min() >= 16 and n.max() <= 512 and abs(np.median(n) - np.sqrt(16 * 513)) < 15
     t = W.poisson_arrivals(2000.0, 2.0, 3)
     assert abs(len(t) - 4000) < 300 and np.all(np.diff(t) > 0)
+
+
+def test_euclidean_generator_and_quantisation_bound():
+    """The Euclidean random matrix (Sec. 5): weights in the stated range, deterministic, and
+    the optimum of the quantised weights is within 2 n delta of the minimum total distance
+    (delta = 0.5 / (2^20 e^-sqrt(3)), the largest error of one log weight)."""
+    import math
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    n = 60
+    w, x, y = W.euclidean(n, 11)
+    w2, _, _ = W.euclidean(n, 11)
+    assert np.array_equal(w, w2) and w.dtype == np.int32
+    assert w.min() >= int(round((1 << 20) * math.exp(-math.sqrt(3)))) and w.max() <= (1 << 20)
+    d = np.sqrt(((x[:, None, :] - y[None, :, :]) ** 2).sum(axis=2))
+    assert np.max(np.abs(np.log(w / float(1 << 20)) + d)) <= 0.5 / ((1 << 20) * math.exp(-math.sqrt(3)))
+    r, c = scipy_opt.linear_sum_assignment(d)
+    perm, _, _, st = oracle.hungarian(oracle.log_weights(w.astype(np.int64)))
+    assert st == 0
+    delta = 0.5 / ((1 << 20) * math.exp(-math.sqrt(3)))
+    assert d[np.arange(n), perm].sum() <= d[r, c].sum() + 2 * n * delta + 1e-12
