@@ -49,7 +49,7 @@ constexpr double kNtEtaMax = 0.1;    // forcing term of the inner solve: eta = s
 constexpr double kNtEtaMin = 1e-3;   //   clamped to [kNtEtaMin, kNtEtaMax]
 constexpr int kNtCgCap = 50;         // CG iterations per Newton step (stagnation guard)
 constexpr int kNtStallWindow = 20;   // Newton steps without halving the residual end the p step
-constexpr int kNtStages = 6;         // cp.async pipeline depth of the matvec (rows in flight)
+constexpr int kNtStages = 6;         // slots of the matvec's bulk-copy ring (row tiles in flight)
 constexpr int kNtMaxSmem = 200 * 1024;
 
 enum : int { kNtRes = 0, kNtCg = 1, kNtDone = 2 };
@@ -267,18 +267,6 @@ __device__ __forceinline__ double nt_stripes(const float* __restrict__ pc, int R
     return MAX ? (double)acc : (double)acc - (double)comp;   // the compensated sum in FP64
 }
 
-// 16-byte asynchronous copy global -> shared (cp.async, cached in L2 only) and its groups
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 // starting point of a p step: rho = 1, kappa_j = 1 / max_i K_ij.
 // Grid: ceil(n/32) column blocks of 32 columns x 8 warps, then the row blocks.
 __global__ void __launch_bounds__(kNtThreads) nt_init_kernel(NtArgs A) {
@@ -456,6 +444,10 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
     __shared__ double sred[kNtWarps][33];
     __shared__ float sh[3][kNtWarps];
     __shared__ NtState S;
+    __shared__ __align__(8) uint64_t full[kNtStages];   // a slot's row tile has landed
+    __shared__ unsigned rel_cnt[kNtStages];               // warp releases of a slot
+    __shared__ unsigned iss_cnt[kNtStages];               // copies issued into a slot
+    __shared__ int s_fail;
     extern __shared__ __align__(16) unsigned char nt_dyn[];
     if (*(volatile int*)A.err != 0) return;   // an earlier step of this call failed
     const int n = A.n, G = gridDim.x, b = blockIdx.x;
@@ -465,7 +457,7 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
     const int cs = (n + G - 1) / G;
     const int c0 = min(n, b * cs), c1 = min(n, c0 + cs);   // owned columns and rows
     const int own = c1 - c0;
-    float4* stage = (float4*)nt_dyn;                                   // [stages][CH][threads]
+    float4* stage = (float4*)nt_dyn;                                   // [slots][CH x threads]
     float* rowdot = (float*)(stage + kNtStages * CH * kNtThreads);     // [rows_per][warps]
     float* zr_s = rowdot + A.rows_per * kNtWarps;                      // [rows_per]
     double* tot_s = (double*)(((uintptr_t)(zr_s + A.rows_per) + 7) & ~(uintptr_t)7);   // [2 cs]
@@ -475,19 +467,50 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
         z.status = kNtRunning;
         z.tau = 1.0;
         S = z;
+        s_fail = 0;
+        for (int k = 0; k < kNtStages; ++k) {
+            mbar_init(&full[k], 1);
+            rel_cnt[k] = iss_cnt[k] = 0u;
+        }
+        mbar_fence_init();
     }
     __syncthreads();
     int q[CH];
 #pragma unroll
     for (int k = 0; k < CH; ++k) q[k] = nt_chunk(A, t, tid + kNtThreads * k);
-    const float* krow0 = A.K + (int64_t)r0 * A.ldk;
-    // this thread's chunks of row `row` of the stripe into stage row % kNtStages
-    auto issue = [&](int row) {
-        float4* dst = stage + (row % kNtStages) * CH * kNtThreads + tid;
-#pragma unroll
-        for (int k = 0; k < CH; ++k)
-            if (4 * q[k] < n) cp_async16(dst + k * kNtThreads, krow0 + (int64_t)row * A.ldk + 4 * q[k]);
+    // The block's row tiles stream through a ring of kNtStages slots filled by 1-D bulk
+    // copies: ring index v is row v % nrows of the stripe, in slot v % kNtStages.  K does
+    // not change within the launch, so the ring runs on across matvec phases: the warp
+    // whose release completes a slot's count refills it with index v + kNtStages, and the
+    // next phase's first rows are in flight during this phase's barriers.
+    const int nq = (n + 3) / 4;
+    const unsigned tile_bytes = (unsigned)(min(nq, (t + 1) * A.W4) - t * A.W4) * 16u;
+    const float* ktile = A.K + (int64_t)r0 * A.ldk + 4 * (int64_t)t * A.W4;
+    auto issue = [&](uint32_t v) {   // one thread
+        const uint32_t slot = v % (uint32_t)kNtStages;
+        iss_cnt[slot] += 1u;
+        mbar_arrive_expect_tx(&full[slot], tile_bytes);
+        bulk_g2s(stage + (size_t)slot * CH * kNtThreads, ktile + (int64_t)(v % (uint32_t)nrows) * A.ldk, tile_bytes,
+                 &full[slot]);
     };
+    auto release = [&](uint32_t v) {   // lane 0 after __syncwarp
+        const uint32_t slot = v % (uint32_t)kNtStages;
+        unsigned old;
+        asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_u32(&rel_cnt[slot])), "r"(1u) : "memory");
+        if ((old + 1u) % (unsigned)kNtWarps == 0u) {
+            fence_proxy_async_smem();
+            issue(v + (uint32_t)kNtStages);
+        }
+    };
+    auto wait_copies = [&]() {   // tid 0: the last copy issued into every slot has landed
+        for (int k = 0; k < kNtStages; ++k) {
+            const unsigned c = iss_cnt[k];
+            if (c > 0u && !mbar_wait(&full[k], (c - 1u) & 1u, A.err, kWaitTimeoutNs)) break;
+        }
+    };
+    if (tid == 0)
+        for (uint32_t v = 0; v < (uint32_t)kNtStages; ++v) issue(v);
+    uint32_t vbase = 0;   // ring index of the phase's first row
     for (;;) {
         const bool res_mode = S.mode == kNtRes;
         const bool apply = S.apply != 0;
@@ -516,16 +539,13 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
                 zr_s[i] = res_mode ? xe : xe * A.rf[r0 + i];
             }
             __syncthreads();
-#pragma unroll
-            for (int st = 0; st < kNtStages - 1; ++st) {
-                if (st < nrows) issue(st);
-                cp_async_commit();
-            }
             for (int row = 0; row < nrows; ++row) {
-                if (row + kNtStages - 1 < nrows) issue(row + kNtStages - 1);
-                cp_async_commit();
-                cp_async_wait<kNtStages - 1>();   // this thread's copies of `row` have landed
-                const float4* src = stage + (row % kNtStages) * CH * kNtThreads + tid;
+                // after a failed wait the warp stops (warp-uniform: lanes meet at __syncwarp)
+                if (__any_sync(0xffffffffu, *(volatile int*)&s_fail != 0)) break;
+                const uint32_t v = vbase + (uint32_t)row;
+                const uint32_t slot = v % (uint32_t)kNtStages;
+                if (!mbar_wait(&full[slot], (v / (uint32_t)kNtStages) & 1u, A.err, kWaitTimeoutNs)) s_fail = 1;
+                const float4* src = stage + (size_t)slot * CH * kNtThreads + tid;
                 const float zr = zr_s[row];
                 float d = 0.0f;
 #pragma unroll
@@ -544,9 +564,13 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                if (lane == 0) rowdot[row * kNtWarps + wid] = d;
+                __syncwarp();
+                if (lane == 0) {
+                    rowdot[row * kNtWarps + wid] = d;
+                    if (*(volatile int*)&s_fail == 0) release(v);   // no refill over a copy that never landed
+                }
             }
-            cp_async_wait<0>();
+            vbase += (uint32_t)nrows;
             __syncthreads();
             for (int i = tid; i < nrows; i += kNtThreads) {
                 double sm = 0.0;
@@ -560,6 +584,7 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
                     *(float4*)(A.pc + (int64_t)s * A.ldk + 4 * q[k]) =
                         make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
         }
+        if (s_fail) atomicCAS(A.err, 0, kErrTimeout);   // a ring wait gave up: every block stops
         if (!group_barrier(A.bar, G, A.err, kWaitTimeoutNs)) break;
         // ---- B: finalise the owned entries: m = D(x) S D(x) z; v, r, y or w ----
         {
@@ -670,6 +695,10 @@ __global__ void __launch_bounds__(kNtThreads, 2) nt_solve_kernel(NtArgs A, doubl
         __syncthreads();
         if (S.mode == kNtDone) break;
     }
+    // the ring's refills in flight (issued for a phase that does not come) land before exit
+    __syncthreads();
+    if (tid == 0) wait_copies();
+    __syncthreads();
     if (b == 0 && tid == 0) {
         NtOut o{};
         o.status = S.status;
