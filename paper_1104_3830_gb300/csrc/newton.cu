@@ -331,27 +331,14 @@ __device__ __forceinline__ void nt_block_reduce3(float v0, float v1, float v2, f
 
 // Reduction of the G block partials (4 doubles each, the first three used) by warp 0 in a
 // fixed order, so that every block obtains identical values; valid in lane 0 of warp 0.
-// Each lane loads its partials in batches of kB independent loads.
 template <bool MAX0>
 __device__ __forceinline__ void nt_grid_reduce3(const double* part, int G, double* g0, double* g1, double* g2) {
-    constexpr int kB = 8;
     double a0 = 0.0, a1 = 0.0, a2 = INFINITY;   // 0 is also the identity of the max of |v - 1|
-    for (int base = threadIdx.x; base < G; base += 32 * kB) {
-        double x0[kB], x1[kB], x2[kB];
-#pragma unroll
-        for (int u = 0; u < kB; ++u) {
-            const int x = base + 32 * u;
-            const bool ok = x < G;
-            x0[u] = ok ? __ldcg(part + 4 * x) : 0.0;
-            x1[u] = ok ? __ldcg(part + 4 * x + 1) : 0.0;
-            x2[u] = ok ? __ldcg(part + 4 * x + 2) : INFINITY;
-        }
-#pragma unroll
-        for (int u = 0; u < kB; ++u) {
-            a0 = MAX0 ? fmax(a0, x0[u]) : a0 + x0[u];
-            a1 += x1[u];
-            a2 = fmin(a2, x2[u]);
-        }
+    for (int x = threadIdx.x; x < G; x += 32) {
+        const double x0 = __ldcg(part + 4 * x);
+        a0 = MAX0 ? fmax(a0, x0) : a0 + x0;
+        a1 += __ldcg(part + 4 * x + 1);
+        a2 = fmin(a2, __ldcg(part + 4 * x + 2));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
