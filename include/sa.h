@@ -68,8 +68,8 @@ typedef enum { SA_PREC_MIXED = 0, SA_PREC_FP32 = 1, SA_PREC_FP64 = 2 } sa_prec;
  * PLAIN: separate row and column kernels per sweep launched from the host (two reads of
  *   the matrix per sweep), the comparison path; the only path for SA_PREC_FP64.
  * STEP: one persistent cooperative kernel; at the start of every p step it evaluates
- *   K = 2^(p log2 w - C_i - V_j) once (FP64 exponent from an exact log2 table, one FP32
- *   rounding) into a workspace of n * ceil(n/4)*4 floats, and each sweep reads K once
+ *   K = 2^(p log2 w - C_i - V_j) once (exponent in float-pair arithmetic, log2 w to about
+ *   2^-40, one SFU exp2) into a workspace of n * ceil(n/4)*4 floats, and each sweep reads K once
  *   (4 bytes per element): no per-element SFU work in the sweeps and an error that does
  *   not grow with p.  Needs n <= 24576 (above 12288 the rows are read from global
  *   memory, prefetched into L2, instead of through the shared-memory ring).

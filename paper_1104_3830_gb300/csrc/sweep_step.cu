@@ -3,8 +3,9 @@
 //
 // At the start of every p step each block evaluates, for its own row stripe,
 //     K_ij = 2^(p log2 w_ij - C_i - V_j)        (C_i ~ max_j (p log2 w_ij - V_j))
-// once, with the exponent formed in FP64 from an exact FP64 table of log2 w, and stores K as
-// FP32 in a global workspace.  K is the iterate X(p) at the step start, so every entry is
+// once, with the exponent formed in float-pair arithmetic (log2 w to about 2^-40 from a
+// 256-entry shared table and a series; exact two-product and two-sums), one SFU exp2, and
+// stores K as FP32 in a global workspace.  K is the iterate X(p) at the step start, so every entry is
 // in [0, ~1] and its relative error (about 2e-7) does not grow with p.  Within the step
 // the potentials move only through a column factor c_j = 2^(Vs_j - V_j) (Vs = V at the
 // step start) and the fresh row sums, so a sweep is
