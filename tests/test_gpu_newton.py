@@ -157,3 +157,20 @@ def test_newton_needs_mixed_precision(ctx):
     w = W.uniform(64, 1, 1000, 1684, dtype=np.int16)
     with pytest.raises(api.SaError):
         api.sa_scale(ctx, api.to_device(w), [1.0], 1e-6, kernel="newton", prec="fp32")
+
+
+@pytest.mark.parametrize("n", [12290, 20000, 24576])
+def test_wide_matrices_fp64_sums(ctx, n):
+    """Four to six column tiles (n = 12290 ragged): FP64 row and column sums of the result
+    by the library's own verification, the property that holds at any size."""
+    w = W.uniform(n, 1, 1000, 1690 + n % 97, dtype=np.int16)
+    d = api.to_device(w)
+    u, v, info = api.sa_scale(ctx, d, [1.0, 2.0], 1e-6, 500, kernel="newton")
+    assert info["status"] == 0 and info["kernel_used"] == 4, info
+    er, ec = api.sa_verify(ctx, d, 2.0, u, v)
+    assert max(er, ec) < NEWTON_SUM_BOUND, (er, ec)
+    # sampled rows against the definition x_ij = exp(p b_ij - u_i - v_j) in FP64
+    uu, vv = u.cpu().numpy(), v.cpu().numpy()
+    for i in (0, n // 3, n - 1):
+        row = np.exp(2.0 * np.log(w[i].astype(np.float64)) - uu[i] - vv)
+        assert abs(row.sum() - 1.0) < NEWTON_SUM_BOUND
