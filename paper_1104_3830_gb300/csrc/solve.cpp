@@ -41,20 +41,21 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
         for (int j = 0; j < n; ++j)
             if (std::isfinite(price0[j])) v[j] = price0[j];
     std::vector<int32_t> rmatch(n, -1), cmatch(n, -1);
+    std::vector<double> mcost(n, INF);   // cost -log w of each row's assigned entry
     // greedy assignment on least-reduced-cost columns
     for (int i = 0; i < n; ++i) {
-        double best = INF;
+        double best = INF, bc = INF;
         int bj = -1;
         for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
             if (!(logw[e] > -INF)) continue;
             const double h = -logw[e] - v[col[e]];
-            if (h < best) { best = h; bj = col[e]; }
+            if (h < best) { best = h; bj = col[e]; bc = -logw[e]; }
         }
         if (bj < 0) {
             set_error("reduced instance: row %d has no allowed entry", i);
             return SA_E_NO_PERFECT_MATCHING;
         }
-        if (cmatch[bj] < 0) { cmatch[bj] = i; rmatch[i] = bj; }
+        if (cmatch[bj] < 0) { cmatch[bj] = i; rmatch[i] = bj; mcost[i] = bc; }
     }
     // Augmenting row reduction (Jonker and Volgenant, 1987): a free row takes its least
     // reduced-cost column j1; when that is strictly below the second least, the price of j1
@@ -71,17 +72,17 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
             int64_t budget = 8 * (int64_t)n + 64;
             while (k < freel.size() && budget-- > 0) {
                 const int i = freel[k++];
-                double u1 = INF, u2 = INF;
+                double u1 = INF, u2 = INF, c1 = INF, c2 = INF;
                 int j1 = -1, j2 = -1;
                 for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
                     if (!(logw[e] > -INF)) continue;
                     const int j = col[e];
                     const double h = -logw[e] - v[j];
                     if (h < u1) {
-                        u2 = u1; j2 = j1;
-                        u1 = h; j1 = j;
+                        u2 = u1; j2 = j1; c2 = c1;
+                        u1 = h; j1 = j; c1 = -logw[e];
                     } else if (h < u2) {
-                        u2 = h; j2 = j;
+                        u2 = h; j2 = j; c2 = -logw[e];
                     }
                 }
                 if (j1 < 0) break;   // no allowed entry: reported by the search below
@@ -90,6 +91,7 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
                     if (j2 >= 0) v[j1] -= u2 - u1;
                 } else if (i0 >= 0 && j2 >= 0) {
                     j1 = j2;   // tie: take the second column instead of displacing
+                    c1 = c2;
                     i0 = cmatch[j1];
                 }
                 if (i0 >= 0) {
@@ -99,10 +101,11 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
                 }
                 cmatch[j1] = i;
                 rmatch[i] = j1;
+                mcost[i] = c1;
             }
         }
     }
-    std::vector<double> dist(n, INF);
+    std::vector<double> dist(n, INF), pcost(n, INF);   // pcost: cost of the entry (pred, j)
     std::vector<int32_t> pred(n, -1), stamp(n, -1), done(n, -1), scanned;
     scanned.reserve(n);
     typedef std::pair<double, int32_t> Item;
@@ -120,6 +123,7 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
                 stamp[j] = epoch;
                 dist[j] = d;
                 pred[j] = r;
+                pcost[j] = -logw[e];
                 heap.push(Item(d, j));
             }
         }
@@ -135,10 +139,7 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
             scanned.push_back(j);
             const int i = cmatch[j];
             // reduced cost of the assigned entry (i, j); zero-length step through row i
-            double ci = INF;
-            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-                if (col[e] == j) { ci = -logw[e]; break; }
-            const double ui = ci - v[j];
+            const double ui = mcost[i] - v[j];
             for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
                 if (!(logw[e] > -INF)) continue;
                 const int k = col[e];
@@ -148,6 +149,7 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
                     stamp[k] = epoch;
                     dist[k] = nd;
                     pred[k] = i;
+                    pcost[k] = -logw[e];
                     heap.push(Item(nd, k));
                 }
             }
@@ -164,6 +166,7 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
             cmatch[j] = i;
             const int prev = rmatch[i];
             rmatch[i] = j;
+            mcost[i] = pcost[j];
             if (i == r) break;
             j = prev;
         }
@@ -171,11 +174,7 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
     for (int i = 0; i < n; ++i) perm[i] = rmatch[i];
     if (alpha || beta) {
         std::vector<double> u(n, 0.0);
-        for (int i = 0; i < n; ++i) {
-            const int j = rmatch[i];
-            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-                if (col[e] == j) { u[i] = -logw[e] - v[j]; break; }
-        }
+        for (int i = 0; i < n; ++i) u[i] = mcost[i] - v[rmatch[i]];
         if (alpha) for (int i = 0; i < n; ++i) alpha[i] = -u[i];
         if (beta) for (int j = 0; j < n; ++j) beta[j] = -v[j];
     }
