@@ -236,12 +236,14 @@ typedef struct {
 } sa_auction_info;
 
 /*
- * sa_solve_reduced_gpu: the same exact optimum and LP duals as sa_solve_reduced, with the
- * column prices first moved toward an optimal dual by a forward auction with eps-scaling
- * on the GPU (all free rows bid in parallel each round; at most 1000 rounds, down to eps =
- * 1e-3 of the range of log w); the exact sparse solver then starts from those prices.  It
- * pays on large B (measured: 1.9x on 362k entries, even at 91k, slower below).  Not in the
- * paper, which solves B sequentially (Sec. 4.2).
+ * sa_solve_reduced_gpu: the same exact optimum and LP duals as sa_solve_reduced, on the
+ * GPU where it pays: the column prices first moved toward an optimal dual by a forward
+ * auction with eps-scaling (all free rows bid in parallel each round; at most 1000 rounds,
+ * down to eps = 1e-3 of the range of log w), then the exact solver's greedy pass and row
+ * reduction on the host, and each of its shortest-augmenting-path searches on the GPU
+ * (label-correcting search, then the dual update and the path flip on the device).
+ * Measured: 3.9x on a B of 362k entries, slower than the host below about 100k.  Not in
+ * the paper, which solves B sequentially (Sec. 4.2).
  *   b       host CSR (as from sa_prune); copied to the device for the call
  *   price0  host FP64[n] or NULL: starting column prices in the maximisation form (beta;
  *           e.g. v/p of the scaling); NULL starts from zero

@@ -145,11 +145,12 @@ static sa_status csr_union(const sa_csr& a, const sa_csr& b, sa_csr* out) {
 }
 
 static sa_status solve_csr(const sa_csr& b, int32_t* perm, double* sum_log_w, double* alpha,
-                           double* beta, const double* price0 = nullptr) {
+                           double* beta, const double* price0 = nullptr, SspFn ssp = nullptr,
+                           void* ssp_user = nullptr) {
     std::vector<double> lw((size_t)std::max<int64_t>(b.nnz, 1));
     for (int64_t e = 0; e < b.nnz; ++e)
         lw[e] = b.w[e] > 0 ? std::log((double)b.w[e]) : -std::numeric_limits<double>::infinity();
-    sa_status rc = sparse_assign(b.n, b.row_ptr, b.col, lw.data(), perm, alpha, beta, price0);
+    sa_status rc = sparse_assign(b.n, b.row_ptr, b.col, lw.data(), perm, alpha, beta, price0, ssp, ssp_user);
     if (rc) return rc;
     if (sum_log_w) {
         double s = 0.0;
@@ -240,9 +241,10 @@ static sa_status solve_csr_gpu(sa_ctx* ctx, const sa_csr& b, const double* price
                 if (b.col[e] == asg[i]) { s += lw[e]; break; }
         info->auction_sum_log_w = s;
     }
-    // the exact solver from the auction's prices (its minimisation-form prices are -beta)
+    // the exact solver from the auction's prices (its minimisation-form prices are -beta),
+    // its shortest-augmenting-path searches on the GPU
     for (int j = 0; j < n; ++j) price[j] = -price[j];
-    rc = solve_csr(b, perm, sum_log_w, alpha, beta, price.data());
+    rc = solve_csr(b, perm, sum_log_w, alpha, beta, price.data(), ssp_device, ctx);
     info->host_ms = now_ms() - t1;
     return rc;
 }

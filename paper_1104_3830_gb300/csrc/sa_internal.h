@@ -136,8 +136,26 @@ sa_status narrow_device(sa_ctx* ctx, const int32_t* src, int64_t lds, int16_t* d
 // Max sum of logw over perfect matchings of a CSR bipartite graph (rows -> cols).
 // price0 (may be null): starting column prices of the minimisation form (-beta_j).
 // Returns SA_OK / SA_E_NO_PERFECT_MATCHING.
+// State handed to a replacement of the shortest-augmenting-path phase (ssp.cu): column
+// prices v (minimisation form), the matching and the cost -log w of each row's assigned
+// entry; every assigned row sits on a least-reduced-cost column.  The replacement assigns
+// the free rows and keeps that invariant.
+struct SspState {
+    int n;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const double* logw;
+    double* v;
+    int32_t* rmatch;
+    int32_t* cmatch;
+    double* mcost;
+};
+typedef sa_status (*SspFn)(void* user, SspState& st);
 sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const double* logw,
-                        int32_t* perm, double* alpha, double* beta, const double* price0 = nullptr);
+                        int32_t* perm, double* alpha, double* beta, const double* price0 = nullptr,
+                        SspFn ssp = nullptr, void* ssp_user = nullptr);
+// ssp.cu: the shortest-augmenting-path phase on the GPU (user = sa_ctx*)
+sa_status ssp_device(void* ctx, SspState& st);
 
 // auction.cu: eps-scaling forward auction on a device CSR (prices >= 0 in and out)
 sa_status auction_device(sa_ctx* ctx, int n, const int64_t* d_rp, const int32_t* d_col, const double* d_val,

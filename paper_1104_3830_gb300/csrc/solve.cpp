@@ -23,7 +23,8 @@
 namespace sa {
 
 sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const double* logw,
-                        int32_t* perm, double* alpha, double* beta, const double* price0) {
+                        int32_t* perm, double* alpha, double* beta, const double* price0, SspFn ssp,
+                        void* ssp_user) {
     const double INF = std::numeric_limits<double>::infinity();
     std::vector<double> v(n, INF);
     for (int i = 0; i < n; ++i)
@@ -104,6 +105,11 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
                 mcost[i] = c1;
             }
         }
+    }
+    if (ssp) {
+        SspState st{n, row_ptr, col, logw, v.data(), rmatch.data(), cmatch.data(), mcost.data()};
+        const sa_status rc = ssp(ssp_user, st);
+        if (rc) return rc;
     }
     std::vector<double> dist(n, INF), pcost(n, INF);   // pcost: cost of the entry (pred, j)
     std::vector<int32_t> pred(n, -1), stamp(n, -1), done(n, -1), scanned;
