@@ -120,3 +120,25 @@ def test_assign_through_gpu_auction_matches(ctx, monkeypatch):
     assert r1["nnz_first"] >= 150000
     assert oracle.perm_weight_exact(w.astype(np.int64), r1["perm"]) == \
         oracle.perm_weight_exact(w.astype(np.int64), r2["perm"])
+
+
+@pytest.mark.parametrize("n,hi,density", [(256, 1, 1.0), (400, 2, 0.2), (333, 1000, 0.05)])
+def test_exact_dual_start_and_full_ties(ctx, n, hi, density):
+    """The searches on the GPU at their degenerate extreme: prices started at an optimal dual
+    (the oracle's beta), so every shortest augmenting path has length 0 and whole regions of
+    columns sit at the same distance; with hi = 1 every entry ties.  The predecessor tree must
+    stay acyclic and reach a free column behind columns at exactly that distance."""
+    rng = np.random.default_rng(5000 + n + hi)
+    w = rng.integers(1, hi + 1, size=(n, n)).astype(np.int64)
+    mask = rng.random((n, n)) < density
+    mask[np.arange(n), rng.permutation(n)] = True
+    rp, col, wv = _csr(mask, w)
+    b = np.where(mask, np.log(w.astype(float)), -np.inf)
+    ph, _, beta, st = oracle.hungarian(b)
+    assert st == 0
+    for price0 in (beta, None):
+        perm, s, al, be, _ = api.sa_solve_reduced_gpu(ctx, rp, col, wv, price0=price0)
+        assert sorted(perm) == list(range(n)) and all(mask[i, perm[i]] for i in range(n))
+        assert oracle.perm_weight_exact(w, perm) == oracle.perm_weight_exact(w, ph)
+        assert oracle.dual_violations(b, al, be, 1e-9)[0] == 0
+        assert max(abs(al[i] + be[perm[i]] - b[i, perm[i]]) for i in range(n)) < 1e-9
