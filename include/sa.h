@@ -232,7 +232,9 @@ typedef struct {
     double auction_sum_log_w; /* sum_i log w of the auction's own assignment (if complete):
                                  within n * eps_final of the optimum */
     double eps_final;
-    double auction_ms, host_ms;
+    double auction_ms;        /* wall time of the auction */
+    double host_ms;           /* wall time of the exact phase after it: greedy pass and row
+                                 reduction on the host, shortest-path searches on the GPU */
 } sa_auction_info;
 
 /*
