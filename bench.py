@@ -480,7 +480,7 @@ def run_reduced(args):
     ctx = api.sa_create(0, torch.cuda.current_stream().cuda_stream)
     ps = [2.0 ** k for k in range(9)]
     out = []
-    for n in (1024, 2048, 4096):
+    for n in [int(x) for x in args.reduced_sizes.split(",")]:
         w = W.uniform(n, 1, 1000, 20261202 + 40 + n, dtype=np.int16)
         d = api.to_device(w)
         u, v, info = api.sa_scale(ctx, d, ps, 1e-6, 20000)
@@ -495,6 +495,7 @@ def run_reduced(args):
         out.append({"n": n, "nnz": int(len(col)), "host_ms": (t1 - t0) * 1e3, "gpu_auction_ms": ai["auction_ms"],
                     "gpu_exact_phase_ms": ai["host_ms"], "gpu_total_ms": (t2 - t1) * 1e3,
                     "rounds": ai["rounds"], "phases": ai["phases"], "complete": ai["complete"],
+                    "gpu_searches": ai["searches"], "gpu_search_rounds": ai["search_rounds"],
                     "same_optimum": abs(s_h - s_g) < 1e-9})
     ctx.close()
     print(json.dumps({"metric": "reduced exact solve: host vs GPU path", "unit": "ms",
@@ -546,6 +547,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="planted8192")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reduced-sizes", default="1024,2048,4096",
+                    help="orders n of the reduced-solve workload, comma-separated")
     ap.add_argument("--kernel", default="auto", choices=["auto", "step", "fused", "plain", "newton"],
                     help="sweep implementation of sa_scale (auto: the library's choice)")
     ap.add_argument("--max-sweeps", type=int, default=20000)

@@ -235,6 +235,8 @@ typedef struct {
     double auction_ms;        /* wall time of the auction */
     double host_ms;           /* wall time of the exact phase after it: greedy pass and row
                                  reduction on the host, shortest-path searches on the GPU */
+    int64_t searches;         /* shortest augmenting path searches run on the GPU */
+    int64_t search_rounds;    /* their label-correcting rounds and tree levels, in all */
 } sa_auction_info;
 
 /*

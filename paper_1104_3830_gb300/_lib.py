@@ -58,7 +58,8 @@ class sa_csr(ctypes.Structure):
 class sa_auction_info(ctypes.Structure):
     _fields_ = [("phases", ctypes.c_int32), ("rounds", ctypes.c_int64), ("complete", ctypes.c_int32),
                 ("auction_sum_log_w", ctypes.c_double), ("eps_final", ctypes.c_double),
-                ("auction_ms", ctypes.c_double), ("host_ms", ctypes.c_double)]
+                ("auction_ms", ctypes.c_double), ("host_ms", ctypes.c_double),
+                ("searches", ctypes.c_int64), ("search_rounds", ctypes.c_int64)]
 
 
 class sa_assign_result(ctypes.Structure):

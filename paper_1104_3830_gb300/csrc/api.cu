@@ -245,8 +245,11 @@ static sa_status solve_csr_gpu(sa_ctx* ctx, const sa_csr& b, const double* price
     // the exact solver from the auction's prices (its minimisation-form prices are -beta),
     // its shortest-augmenting-path searches on the GPU
     for (int j = 0; j < n; ++j) price[j] = -price[j];
-    rc = solve_csr(b, perm, sum_log_w, alpha, beta, price.data(), ssp_device, ctx);
+    SspRun run{ctx};
+    rc = solve_csr(b, perm, sum_log_w, alpha, beta, price.data(), ssp_device, &run);
     info->host_ms = now_ms() - t1;
+    info->searches = run.searches;
+    info->search_rounds = run.rounds;
     return rc;
 }
 

@@ -154,8 +154,13 @@ typedef sa_status (*SspFn)(void* user, SspState& st);
 sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const double* logw,
                         int32_t* perm, double* alpha, double* beta, const double* price0 = nullptr,
                         SspFn ssp = nullptr, void* ssp_user = nullptr);
-// ssp.cu: the shortest-augmenting-path phase on the GPU (user = sa_ctx*)
-sa_status ssp_device(void* ctx, SspState& st);
+// ssp.cu: the shortest-augmenting-path phase on the GPU (user = SspRun*)
+struct SspRun {
+    sa_ctx* ctx;
+    int64_t searches = 0;        // shortest-path searches run on the GPU
+    int64_t rounds = 0;          // label-correcting rounds and tree levels launched, in all
+};
+sa_status ssp_device(void* user, SspState& st);
 
 // auction.cu: eps-scaling forward auction on a device CSR (prices >= 0 in and out)
 sa_status auction_device(sa_ctx* ctx, int n, const int64_t* d_rp, const int32_t* d_col, const double* d_val,

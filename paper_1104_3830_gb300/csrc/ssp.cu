@@ -214,7 +214,8 @@ __global__ void sp_flip_kernel(SpArgs A, int r) {
 }  // namespace
 
 sa_status ssp_device(void* user, SspState& st) {
-    sa_ctx* ctx = (sa_ctx*)user;
+    SspRun* run = (SspRun*)user;
+    sa_ctx* ctx = run->ctx;
     const int n = st.n;
     std::vector<int> freel;
     for (int i = 0; i < n; ++i)
@@ -272,6 +273,7 @@ sa_status ssp_device(void* user, SspState& st) {
     const int ge = (n + kSpT - 1) / kSpT;
     const int wpb = kSpT / 32;
     for (int r : freel) {
+        ++run->searches;
         sp_reset_kernel<<<ge, kSpT, 0, s>>>(A);
         sp_seed_kernel<<<1, kSpT, 0, s>>>(A, r);
         count_launch(2);
@@ -280,6 +282,7 @@ sa_status ssp_device(void* user, SspState& st) {
         for (int round = 0; round <= n; round += kBatch) {
             for (int b = 0; b < kBatch; ++b) sp_relax_kernel<<<gfull, kSpT, 0, s>>>(A, round + b);
             count_launch(kBatch);
+            run->rounds += kBatch;
             SA_CUDA(cudaMemcpyAsync(h, A.nfront + (round + kBatch) % 3, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             SA_CUDA(cudaStreamSynchronize(s));
             if (*h == 0) break;   // an empty frontier stays empty
@@ -290,6 +293,7 @@ sa_status ssp_device(void* user, SspState& st) {
         for (int L = 0; L <= n; L += kBatch) {
             for (int b = 0; b < kBatch; ++b) sp_tree_kernel<<<gfull, kSpT, 0, s>>>(A, L + b);
             count_launch(kBatch);
+            run->rounds += kBatch;
             SA_CUDA(cudaMemcpyAsync(h, A.nfront + (L + kBatch) % 3, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             SA_CUDA(cudaStreamSynchronize(s));
             if (*h == 0) break;

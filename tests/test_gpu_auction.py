@@ -90,6 +90,9 @@ def test_reduced_instance_of_a_scaled_matrix(ctx):
     assert abs(s_g - s_h) < 1e-9
     assert oracle.perm_weight_exact(w.astype(np.int64), perm_g) == oracle.perm_weight_exact(w.astype(np.int64), perm_h)
     assert ai["rounds"] >= 1
+    # every search on the GPU runs at least one batch of 8 label-correcting rounds and one of
+    # 8 tree levels
+    assert ai["searches"] >= 0 and ai["search_rounds"] >= 16 * ai["searches"]
 
 
 def test_no_perfect_matching(ctx):
