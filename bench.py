@@ -75,6 +75,19 @@ KERNEL_NAMES = {1: "fused_kernel (single-read persistent sweep, SFU exp2/log2 pe
                 4: "nt_solve_kernel (persistent Newton-CG over the per-step FP32 matrix, one read per operator application)"}
 
 
+def over_ranks(ms, units, dist=None, device="cpu"):
+    """Whole-job timing of replicas: (the slowest rank's time, the units of all ranks).
+    dist is torch.distributed with an initialised process group, or None for one rank."""
+    if dist is None:
+        return float(ms), float(units)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def measured_traffic(kernel_used, n, wbytes):
     """(bytes per sweep, source) if a capture of this kernel source and size exists."""
     import hashlib
@@ -620,15 +633,7 @@ def main():
             kms.append(res["scale"]["kernel_ms"])
     launches = (_lib.lib().sa_kernel_launches() - launches0) // args.steps
     barrier()
-    total_ms = sum(times)
-    if dist is not None:
-        t = torch.tensor([total_ms, float(sweeps)], dtype=torch.float64, device=f"cuda:{local}")
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, all_sweeps = float(tmax[0]), float(t[1])
-    else:
-        all_sweeps = float(sweeps)
+    total_ms, all_sweeps = over_ranks(sum(times), sweeps, dist, f"cuda:{local}")
     value = all_sweeps / (total_ms / 1e3)
 
     # roofline of the dominant kernel (the scaling kernel: over 99% of the step).
@@ -666,7 +671,8 @@ def main():
         e1.synchronize()
         e2e_t.append(e0.elapsed_time(e1))
         e2e_sw += r2["scale"]["sweeps_total"]
-    e2e_val = e2e_sw / (sum(e2e_t) / 1e3) * world
+    e2e_ms, e2e_all = over_ranks(sum(e2e_t), e2e_sw, dist, f"cuda:{local}")
+    e2e_val = e2e_all / (e2e_ms / 1e3)
     d2h = n * 8 + (r2["nnz_final"] + r2["nnz_first"]) * 8 + 8 * (n + 1)
     e2e = {"value": e2e_val, "unit": "sweeps/s", "h2d_bytes_per_step": int(w.nbytes), "d2h_bytes_per_step": int(d2h)}
 
