@@ -143,12 +143,9 @@ sa_status auction_device(sa_ctx* ctx, int n, const int64_t* d_rp, const int32_t*
     if (rc) return rc;
     int* h_free = (int*)ctx->pinned.ptr;
     const int gb = (n + 7) / 8, ge = (n + kAuThreads - 1) / kAuThreads;
-    // a bid on a row's only column raises the price by this much (more than any value gap)
-    double big = 1.0;
-    {
-        // the value range is bounded by the caller's eps0 (a quarter of it); keep big well above
-        big = std::max(1.0, 8.0 * eps0);
-    }
+    // a row with a single column has no second-best value: its bid raises that column's
+    // price by this increment (any increment >= eps keeps eps-complementary slackness)
+    const double big = std::max(1.0, 8.0 * eps0);
     *phases = 0;
     *rounds = 0;
     *complete = 0;
