@@ -71,6 +71,7 @@ def _load():
         i, d = ctypes.c_int, ctypes.c_double
         sig = {
             "orc_num_threads": (i, []),
+            "orc_set_num_threads": (None, [i]),
             "orc_sinkhorn": (i, [i, dp, dp, i, d, i, i, dp, dp, ip, dp]),
             "orc_sinkhorn_from": (i, [i, dp, d, d, i, dp, dp, ip, dp]),
             "orc_xmatrix": (i, [i, dp, d, dp, dp, dp]),
@@ -108,6 +109,12 @@ def _square(b):
 def num_threads() -> int:
     """OpenMP threads the oracle's parallel loops use."""
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """Threads of the oracle's later parallel loops (timing only: each loop splits
+    independent rows or columns, so the results do not depend on it)."""
+    _load().orc_set_num_threads(int(k))
 
 
 def log_weights(a) -> np.ndarray:

@@ -38,6 +38,15 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* threads of the later parallel loops (k >= 1); the arithmetic does not depend on it */
+void orc_set_num_threads(int k) {
+#ifdef _OPENMP
+    omp_set_num_threads(k >= 1 ? k : 1);
+#else
+    (void)k;
+#endif
+}
+
 /* ------------------------------------------------------------------------------------
  * Log-domain Sinkhorn iteration at a fixed p (Sec. 4.1.2, "logarithmic p-Sinkhorn"),
  * which is the iteration of Eqs. dad1-dad3 written in log coordinates with the row and

@@ -329,3 +329,21 @@ def test_algorithm1_prescaling_scale():
     w2 = (np.ones((16, 16)) * 2 + np.eye(16)).astype(np.int32)   # max/min = 1.5 < e
     r2 = oracle.algorithm1(w2, opt_ratio=1e9, p0=100.0)
     assert r2["p_raw"] == 100.0
+
+
+def test_thread_count_does_not_change_the_result():
+    """The oracle's parallel loops split independent rows or columns, so one thread and all
+    threads give bit-identical potentials (the one-core CPU baseline times the same
+    arithmetic)."""
+    w = W.uniform(97, 1, 1000, 4242, dtype=np.int32).astype(np.int64)
+    b = oracle.log_weights(w)
+    k = oracle.num_threads()
+    u0, v0 = np.zeros(97), np.zeros(97)
+    ua, va, *_ = oracle.sinkhorn_from(b, 4.0, u0, v0, 1e-300, 40)
+    oracle.set_num_threads(1)
+    try:
+        ub, vb, *_ = oracle.sinkhorn_from(b, 4.0, u0, v0, 1e-300, 40)
+    finally:
+        oracle.set_num_threads(k)
+    assert oracle.num_threads() == k
+    assert np.array_equal(ua, ub) and np.array_equal(va, vb)
