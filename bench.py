@@ -183,7 +183,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(w, ps, budget_s=12.0):
+def cpu_baseline(w, ps, budget_s=12.0, one_core=True):
     """The FP64 oracle (as it stands) on this host: sweeps/s of its log-domain Sinkhorn on
     the same matrix, timed on a bounded number of sweeps at the top of the schedule."""
     import oracle
@@ -201,6 +201,10 @@ def cpu_baseline(w, ps, budget_s=12.0):
     t0 = time.perf_counter()
     oracle.sinkhorn_from(b, p, u, v, 1e-300, k)
     dt = time.perf_counter() - t0
+    line = {"value": k / dt, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{k} FP64 log-domain Sinkhorn sweeps of the oracle at p={p:g} on the same n={n} matrix"}
+    if not one_core:
+        return line
     # the same sweeps on one core, on a smaller sample (a probe sweep, then what fits)
     oracle.set_num_threads(1)
     try:
@@ -213,10 +217,41 @@ def cpu_baseline(w, ps, budget_s=12.0):
         dt1 = time.perf_counter() - t0
     finally:
         oracle.set_num_threads(cores)
-    return {"value": k / dt, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{k} FP64 log-domain Sinkhorn sweeps of the oracle at p={p:g} on the same n={n} matrix",
-            "one_core": {"value": k1 / dt1, "unit": "sweeps/s", "cores": 1,
-                         "sample": f"{k1} sweeps of the same iteration on one thread"}}
+    line["one_core"] = {"value": k1 / dt1, "unit": "sweeps/s", "cores": 1,
+                        "sample": f"{k1} sweeps of the same iteration on one thread"}
+    return line
+
+
+def oracle_instances_baseline(mats, ps, budget_s=10.0, tol=1e-6, max_sweeps=20000):
+    """The oracle's FP64 Sinkhorn over the whole schedule, instance after instance in the
+    workload's own (random) order until the budget is spent: instances/s on this host."""
+    import oracle
+    cores = oracle.num_threads()
+    done, sweeps = 0, 0
+    t0 = time.perf_counter()
+    for m in mats:
+        _, _, sw, _, _ = oracle.sinkhorn(oracle.log_weights(np.asarray(m, dtype=np.int64)), ps, tol, max_sweeps)
+        done += 1
+        sweeps += int(sw.sum())
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "instances/s", "cores": cores, "kind": "oracle",
+            "sample": f"the first {done} instances of the workload, whole schedule to tol {tol:g} "
+                      f"({sweeps} FP64 sweeps)"}
+
+
+def oracle_algorithm1_baseline(w, **kw):
+    """The oracle's Algorithm 1 (FP64 Sinkhorn, prune, exact solve of B) on the same matrix
+    and settings: its wall time and result."""
+    import oracle
+    cores = oracle.num_threads()
+    t0 = time.perf_counter()
+    r = oracle.algorithm1(w, **kw)
+    dt = time.perf_counter() - t0
+    return {"value": dt * 1e3, "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": "the whole Algorithm 1 run on the same matrix", "gamma": r["gamma"],
+            "p_final": r["p_final"], "rounds": r["rounds"], "sweeps": r["sweeps"], "status": r["status"]}
 
 
 def run_reference(args):
@@ -336,6 +371,8 @@ def run_batch(args):
                          "frac": achieved / ex2_peak, "traffic": None,
                          "peak_source": "own micro-benchmark: 30 ex2/clk/SM x 152 SMs x 2.07 GHz"},
             "gpu_launches": int(launches), "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_instances_baseline(mats, ps)
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -409,6 +446,8 @@ def run_precision(args):
                          "traffic": None, "kernel": m["kernel"], "peak_source": f"{peak_kind} hbm_gbs",
                          "note": "whole scaling call incl. the per-step evaluation of K, 3 sweeps per step"},
             "e2e": None, "gpu_launches": int(launches), "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, ps, budget_s=8.0, one_core=False)
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -577,11 +616,14 @@ def run_euclidean(args):
                        "operations": g["sweeps_total"], "remaining_pct": 100.0 * g["nnz"] / (n * n),
                        "ms": (t1 - t0) * 1e3, "status": g["status"]}
     ctx.close()
-    print(json.dumps({"metric": "Algorithm 1 on the Euclidean random matrix (Tables 1 and 3)", "unit": "ms",
-                      "higher_is_better": False, "data": "synthetic", "config": {"n": n, "opt_ratio": 2.0,
-                      "p0": 100.0, "dp": 50.0, "eps": "1/n", "t": "1/n"}, "results": out,
-                      "paper": {"gamma": 1.728, "p": 200, "sinkhorn_iterations": 1416, "newton_operations": 742,
-                                "remaining_pct": 0.92}}), flush=True)
+    line = {"metric": "Algorithm 1 on the Euclidean random matrix (Tables 1 and 3)", "unit": "ms",
+            "higher_is_better": False, "data": "synthetic", "config": {"n": n, "opt_ratio": 2.0,
+            "p0": 100.0, "dp": 50.0, "eps": "1/n", "t": "1/n"}, "results": out,
+            "paper": {"gamma": 1.728, "p": 200, "sinkhorn_iterations": 1416, "newton_operations": 742,
+                      "remaining_pct": 0.92}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_algorithm1_baseline(w, opt_ratio=2.0, p0=100.0, dp=50.0, max_rounds=30)
+    print(json.dumps(line), flush=True)
 
 
 def main():

@@ -38,3 +38,20 @@ def test_bench_workload_shapes():
     assert w.shape == (256, 256) and w.dtype == np.int32 and ps[-1] == 256.0 and "workload" in cfg
     w, ps, cfg = b.workload("small")
     assert w.shape == (2048, 2048) and w.dtype == np.int16
+
+
+def test_oracle_baselines_small():
+    """The CPU-baseline legs on tiny inputs: finite rates, the stated units, and the oracle's
+    Algorithm 1 result fields."""
+    b = _bench()
+    from paper_1104_3830_gb300 import workloads as W
+    w = W.uniform(64, 1, 1000, 11, dtype=np.int16)
+    cb = b.cpu_baseline(w, [1.0, 2.0], budget_s=0.2)
+    assert cb["value"] > 0 and cb["unit"] == "sweeps/s" and cb["one_core"]["cores"] == 1
+    assert "one_core" not in b.cpu_baseline(w, [1.0], budget_s=0.1, one_core=False)
+    mats = [W.uniform(n, 1, 1000, 12 + n, dtype=np.int32) for n in (16, 23, 40)]
+    ib = b.oracle_instances_baseline(mats, [1.0, 2.0, 4.0], budget_s=0.5)
+    assert ib["unit"] == "instances/s" and ib["value"] > 0
+    a1 = b.oracle_algorithm1_baseline(W.uniform(40, 1, 1000, 13, dtype=np.int32).astype(np.int64),
+                                      opt_ratio=2.0, p0=100.0, dp=50.0, max_rounds=30)
+    assert a1["unit"] == "ms" and a1["status"] == 0 and a1["gamma"] <= 2.0
