@@ -12,6 +12,9 @@
 // If the instance's log2 table (n^2 FP32) fits in shared memory it is computed once per
 // instance and the sweeps read it (one SFU exp2 per element); otherwise the sweeps read
 // the weights from global memory (L2-resident after the first sweep) and take log2 too.
+// Two blocks run on each SM (128 registers a thread, 110 KB of shared memory a block, so
+// the table fits up to n = 142): a sweep of a small instance is mostly the latency of its
+// block-wide reductions, which the other block's instance hides.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -46,7 +49,7 @@ struct BatchArgs {
 };
 
 template <typename WT, int NT, int KC>
-__global__ void __launch_bounds__(NT, 1) batch_kernel(BatchArgs A) {
+__global__ void __launch_bounds__(NT, 2) batch_kernel(BatchArgs A) {
     constexpr int NW = NT / 32;
     constexpr int VEC = 16 / sizeof(WT);
     constexpr int M = KC * VEC;   // columns per lane
@@ -314,7 +317,7 @@ extern "C" sa_status sa_batch_scale(sa_ctx* ctx, int32_t k, const void* const* d
     constexpr int NT = 256;
     constexpr int NW = NT / 32;
     const size_t fixed = kBatchMaxN * 8 + 4 * kBatchMaxN * 4 + (size_t)NW * kBatchMaxN * 4 + NW * 8 + 64;
-    size_t smem = std::min<size_t>(ctx->smem_optin, 200 * 1024);
+    size_t smem = std::min<size_t>(ctx->smem_optin, 110 * 1024);   // two blocks per SM
     args.smem_table = smem > fixed ? smem - fixed : 0;
     int grid = 0;
     auto launch = [&](auto kern) -> sa_status {
