@@ -224,6 +224,22 @@ sa_status sa_prune(sa_ctx* ctx, const sa_matrix* a, double p, const double* d_u,
 sa_status sa_solve_reduced(const sa_csr* b, int32_t* perm, double* sum_log_w, double* alpha,
                            double* beta);
 
+/*
+ * sa_solve_reduced_warm: sa_solve_reduced started from given column duals instead of the
+ * column minima: the same exact optimum (ties may pick another optimal permutation) and LP
+ * duals.  Exact duals of a nearby instance (sa_assign's re-solve after its certificate
+ * added entries) make it fast.  The scaling's approximate duals v/p (sa_assign's first
+ * solve) return duals that also hold on the rest of A, so its certificate rarely adds
+ * entries, but they make nearly every entry of B almost tight and can make the solve much
+ * slower than the cold start (measured 22.5 s against 26 ms on a Zipf-weighted B of
+ * n = 2048).
+ *   beta0  host FP64[n] in: maximisation-form column duals (natural log units); a
+ *          non-finite entry falls back to that column's minimum cost.
+ *   perm, sum_log_w, alpha, beta  as sa_solve_reduced.  Host only.
+ */
+sa_status sa_solve_reduced_warm(const sa_csr* b, const double* beta0, int32_t* perm, double* sum_log_w,
+                                double* alpha, double* beta);
+
 /* Statistics of sa_solve_reduced_gpu. */
 typedef struct {
     int32_t phases;           /* eps-scaling phases of the auction */

@@ -141,8 +141,9 @@ def sa_prune(ctx: Context, w, p, u, v, t=0.0, guard=True):
     return rp, col, wv, ub.value
 
 
-def sa_solve_reduced(row_ptr, col, w, n=None):
-    """Exact solve of a CSR instance: (perm, sum_log_w, alpha, beta)."""
+def sa_solve_reduced(row_ptr, col, w, n=None, beta0=None):
+    """Exact solve of a CSR instance: (perm, sum_log_w, alpha, beta).  beta0: starting
+    column duals in maximisation form (e.g. the scaling's v/p), else the column minima."""
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
     w = np.ascontiguousarray(w, dtype=np.int32)
@@ -153,8 +154,15 @@ def sa_solve_reduced(row_ptr, col, w, n=None):
     s = ctypes.c_double()
     al = np.zeros(n)
     be = np.zeros(n)
-    check(lib().sa_solve_reduced(ctypes.byref(c), perm.ctypes.data_as(L._I32P), ctypes.byref(s),
-                                 al.ctypes.data_as(L._DP), be.ctypes.data_as(L._DP)))
+    if beta0 is None:
+        check(lib().sa_solve_reduced(ctypes.byref(c), perm.ctypes.data_as(L._I32P), ctypes.byref(s),
+                                     al.ctypes.data_as(L._DP), be.ctypes.data_as(L._DP)))
+    else:
+        b0 = np.ascontiguousarray(beta0, dtype=np.float64)
+        if b0.shape != (n,):
+            raise ValueError("beta0 must have n entries")
+        check(lib().sa_solve_reduced_warm(ctypes.byref(c), b0.ctypes.data_as(L._DP), perm.ctypes.data_as(L._I32P),
+                                          ctypes.byref(s), al.ctypes.data_as(L._DP), be.ctypes.data_as(L._DP)))
     return perm, s.value, al, be
 
 

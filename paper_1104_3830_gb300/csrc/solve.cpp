@@ -4,12 +4,17 @@
 // Minimisation form: cost c_e = -log w_e on each kept entry.  Column prices v_j are kept
 // such that every assigned row i sits on a column of least reduced cost c_ij - v_j
 // (Jonker-Volgenant invariant).  Start: v_j = min_i c_ij, or caller-supplied prices (any
-// prices keep the invariant once every row takes its least-reduced-cost column; near
-// optimal ones -- the scaling's -v/p, dual feasible because x_ij(p) <= 1 -- leave few
-// conflicts and short augmenting paths), and a greedy assignment on each row's
-// least-reduced-cost column.  Each free row then runs Dijkstra over columns with a binary
-// heap until it reaches a free column; the prices of the columns finalised before the
-// target are lowered by (d_target - d_j) and the path is flipped.  At the end
+// prices keep the invariant once every row takes its least-reduced-cost column).  The
+// exact duals of a nearby instance (a re-solve after entries were added) leave few
+// conflicts.  The scaling's approximate duals -v/p give duals that also hold on the rest
+// of A (what the certificate of sa_assign checks), but under them nearly every entry of B
+// is almost tight, the greedy pass collides and the searches can sweep wide near-tied
+// regions; solves that need no certificate start from the column minima.  Then a greedy
+// assignment on each
+// row's least-reduced-cost column and augmenting row reduction; each free row then runs
+// Dijkstra over columns with a binary heap until no column in the heap is nearer than the
+// nearest free column reached; the prices of the columns finalised before it are lowered
+// by (d_target - d_j) and the path is flipped.  At the end
 // u_i = c_{i,sigma(i)} - v_{sigma(i)} and (alpha, beta) = (-u, -v) are optimal LP duals
 // of the maximisation: alpha_i + beta_j >= log w_ij on B, with equality on sigma.
 #include <cmath>
@@ -121,6 +126,11 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
         ++epoch;
         scanned.clear();
         std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+        // the nearest free column reached so far: it goes to no heap, and the search ends
+        // as soon as no column in the heap is strictly nearer (Dijkstra's stopping rule at
+        // the first target; on ties it saves scanning every matched column at that distance)
+        int sink = -1;
+        double dmin = INF;
         for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
             if (!(logw[e] > -INF)) continue;
             const int j = col[e];
@@ -130,17 +140,19 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
                 dist[j] = d;
                 pred[j] = r;
                 pcost[j] = -logw[e];
-                heap.push(Item(d, j));
+                if (cmatch[j] < 0) {
+                    if (d < dmin) { dmin = d; sink = j; }
+                } else {
+                    heap.push(Item(d, j));
+                }
             }
         }
-        int sink = -1;
-        double dmin = INF;
         while (!heap.empty()) {
             Item top = heap.top();
+            if (top.first >= dmin) break;
             heap.pop();
             const int j = top.second;
             if (done[j] == epoch || top.first > dist[j]) continue;
-            if (cmatch[j] < 0) { sink = j; dmin = dist[j]; break; }
             done[j] = epoch;
             scanned.push_back(j);
             const int i = cmatch[j];
@@ -156,7 +168,11 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
                     dist[k] = nd;
                     pred[k] = i;
                     pcost[k] = -logw[e];
-                    heap.push(Item(nd, k));
+                    if (cmatch[k] < 0) {
+                        if (nd < dmin) { dmin = nd; sink = k; }
+                    } else if (nd < dmin) {
+                        heap.push(Item(nd, k));
+                    }
                 }
             }
         }

@@ -46,3 +46,64 @@ def test_no_perfect_matching_is_reported():
     with pytest.raises(api.SaError) as e:
         api.sa_solve_reduced(rp, col, wv)
     assert e.value.status == -5
+
+
+def _check(mask, w, perm, s, al, be):
+    n = len(perm)
+    assert sorted(perm) == list(range(n)) and all(mask[i, perm[i]] for i in range(n))
+    b = np.where(mask, np.log(w.astype(float)), -np.inf)
+    ph, _, _, st = oracle.hungarian(b)
+    assert st == 0
+    assert oracle.perm_weight_exact(w, perm) == oracle.perm_weight_exact(w, ph)
+    assert oracle.dual_violations(b, al, be, 1e-9)[0] == 0
+    assert max(abs(al[i] + be[perm[i]] - b[i, perm[i]]) for i in range(n)) < 1e-9
+    assert abs(s - sum(b[i, perm[i]] for i in range(n))) < 1e-9
+
+
+@pytest.mark.parametrize("n,density,hi,start", [(60, 0.2, 1000, "exact"), (150, 0.3, 2, "exact"),
+                                                (200, 0.05, 30000, "noisy"), (300, 1.0, 1, "noisy"),
+                                                (257, 0.02, 7, "exact"), (400, 0.5, 4, "noisy"),
+                                                (90, 0.1, 1000, "nonfinite")])
+def test_warm_start_matches_oracle(n, density, hi, start):
+    """sa_solve_reduced_warm from given column duals: the exact duals of the instance itself
+    (every search then has length 0, the most tied case), the same plus noise (approximate
+    duals, as the scaling gives), or duals with non-finite entries (the column minimum is
+    used there).  The optimum and the LP duals are exact whatever the start."""
+    rng = np.random.default_rng(n * 13 + hi)
+    w = rng.integers(1, hi + 1, size=(n, n)).astype(np.int64)
+    mask = rng.random((n, n)) < density
+    mask[np.arange(n), rng.permutation(n)] = True
+    rp, col, wv = _csr(mask, w)
+    b = np.where(mask, np.log(w.astype(float)), -np.inf)
+    _, _, beta_opt, st = oracle.hungarian(b)
+    assert st == 0
+    beta0 = beta_opt.copy()
+    if start == "noisy":
+        beta0 += rng.normal(0.0, 0.05, size=n)
+    elif start == "nonfinite":
+        beta0[::3] = np.nan
+        beta0[1::7] = np.inf
+    perm, s, al, be = api.sa_solve_reduced(rp, col, wv, beta0=beta0)
+    _check(mask, w, perm, s, al, be)
+
+
+def test_warm_start_argument_checks():
+    rp, col, wv = _csr(np.eye(3, dtype=bool), np.full((3, 3), 2, dtype=np.int64))
+    with pytest.raises(ValueError):
+        api.sa_solve_reduced(rp, col, wv, beta0=np.zeros(2))
+    perm, s, _, _ = api.sa_solve_reduced(rp, col, wv, beta0=np.zeros(3))
+    assert list(perm) == [0, 1, 2] and abs(s - 3 * np.log(2.0)) < 1e-12
+
+
+def test_early_stop_on_ties_at_the_free_column():
+    """Every entry equal (all reduced costs 0 from the column minima): each search reaches a
+    free column at distance 0 and stops there; the result is still a permutation of B with
+    exact duals."""
+    n = 500
+    rng = np.random.default_rng(4)
+    mask = rng.random((n, n)) < 0.05
+    mask[np.arange(n), rng.permutation(n)] = True
+    w = np.full((n, n), 7, dtype=np.int64)
+    rp, col, wv = _csr(mask, w)
+    perm, s, al, be = api.sa_solve_reduced(rp, col, wv)
+    _check(mask, w, perm, s, al, be)
