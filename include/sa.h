@@ -228,16 +228,33 @@ sa_status sa_solve_reduced(const sa_csr* b, int32_t* perm, double* sum_log_w, do
  * sa_solve_reduced_warm: sa_solve_reduced started from given column duals instead of the
  * column minima: the same exact optimum (ties may pick another optimal permutation) and LP
  * duals.  Exact duals of a nearby instance (sa_assign's re-solve after its certificate
- * added entries) make it fast.  The scaling's approximate duals v/p (sa_assign's first
- * solve) return duals that also hold on the rest of A, so its certificate rarely adds
- * entries, but they make nearly every entry of B almost tight and can make the solve much
- * slower than the cold start (measured 22.5 s against 26 ms on a Zipf-weighted B of
- * n = 2048).
+ * added entries) make it fast.  The scaling's approximate duals v/p make nearly every
+ * entry of B almost tight and can make the solve much slower than the cold start
+ * (measured 22.5 s against 26 ms on a Zipf-weighted B of n = 2048): for duals near v/p
+ * use sa_solve_reduced_near.
  *   beta0  host FP64[n] in: maximisation-form column duals (natural log units); a
  *          non-finite entry falls back to that column's minimum cost.
  *   perm, sum_log_w, alpha, beta  as sa_solve_reduced.  Host only.
  */
 sa_status sa_solve_reduced_warm(const sa_csr* b, const double* beta0, int32_t* perm, double* sum_log_w,
+                                double* alpha, double* beta);
+
+/*
+ * sa_solve_reduced_near: the optimum of B as sa_solve_reduced computes it (from the column
+ * minima), then, of all LP-optimal duals of B for that assignment, the one with the
+ * componentwise largest beta <= beta0.  With the assignment sigma fixed, optimality reads
+ * alpha_i = log w_{i sigma(i)} - beta_{sigma(i)} and
+ * beta_{sigma(i)} - beta_j <= log w_{i sigma(i)} - log w_ij on every entry (i, j) of B,
+ * difference constraints whose largest solution below beta0 is a shortest-path labelling
+ * (Dijkstra over the columns).  With beta0 = the scaling's v/p (Sec. 4.2: x_ij(p) <= 1
+ * makes (u/p, v/p) nearly feasible on all of A) the returned duals also tend to hold on
+ * the rest of A, which is what sa_assign's certificate checks; sa_assign solves its first
+ * B this way.
+ *   beta0  host FP64[n] in: maximisation-form column duals to stay below; a non-finite
+ *          entry leaves that column's dual where the cold solve put it.
+ *   perm, sum_log_w, alpha, beta  as sa_solve_reduced.  Host only.
+ */
+sa_status sa_solve_reduced_near(const sa_csr* b, const double* beta0, int32_t* perm, double* sum_log_w,
                                 double* alpha, double* beta);
 
 /* Statistics of sa_solve_reduced_gpu. */

@@ -108,6 +108,7 @@ SIGNATURES = {
                                 ctypes.c_int32, ctypes.POINTER(sa_csr), _DP]),
     "sa_solve_reduced": (ctypes.c_int, [ctypes.POINTER(sa_csr), _I32P, _DP, _DP, _DP]),
     "sa_solve_reduced_warm": (ctypes.c_int, [ctypes.POINTER(sa_csr), _DP, _I32P, _DP, _DP, _DP]),
+    "sa_solve_reduced_near": (ctypes.c_int, [ctypes.POINTER(sa_csr), _DP, _I32P, _DP, _DP, _DP]),
     "sa_solve_reduced_gpu": (ctypes.c_int, [_VP, ctypes.POINTER(sa_csr), _DP, _I32P, _DP, _DP, _DP,
                                             ctypes.POINTER(sa_auction_info)]),
     "sa_certify": (ctypes.c_int, [_VP, ctypes.POINTER(sa_matrix), _DP, _DP, ctypes.c_double, _I64P,

@@ -141,9 +141,13 @@ def sa_prune(ctx: Context, w, p, u, v, t=0.0, guard=True):
     return rp, col, wv, ub.value
 
 
-def sa_solve_reduced(row_ptr, col, w, n=None, beta0=None):
+def sa_solve_reduced(row_ptr, col, w, n=None, beta0=None, near=None):
     """Exact solve of a CSR instance: (perm, sum_log_w, alpha, beta).  beta0: starting
-    column duals in maximisation form (e.g. the scaling's v/p), else the column minima."""
+    column duals in maximisation form, else the column minima.  near: solve from the column
+    minima, then return the optimal duals with the largest beta <= near (e.g. the
+    scaling's v/p)."""
+    if beta0 is not None and near is not None:
+        raise ValueError("give beta0 or near, not both")
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
     w = np.ascontiguousarray(w, dtype=np.int32)
@@ -154,7 +158,13 @@ def sa_solve_reduced(row_ptr, col, w, n=None, beta0=None):
     s = ctypes.c_double()
     al = np.zeros(n)
     be = np.zeros(n)
-    if beta0 is None:
+    if near is not None:
+        b0 = np.ascontiguousarray(near, dtype=np.float64)
+        if b0.shape != (n,):
+            raise ValueError("near must have n entries")
+        check(lib().sa_solve_reduced_near(ctypes.byref(c), b0.ctypes.data_as(L._DP), perm.ctypes.data_as(L._I32P),
+                                          ctypes.byref(s), al.ctypes.data_as(L._DP), be.ctypes.data_as(L._DP)))
+    elif beta0 is None:
         check(lib().sa_solve_reduced(ctypes.byref(c), perm.ctypes.data_as(L._I32P), ctypes.byref(s),
                                      al.ctypes.data_as(L._DP), be.ctypes.data_as(L._DP)))
     else:

@@ -163,6 +163,24 @@ static sa_status solve_csr(const sa_csr& b, int32_t* perm, double* sum_log_w, do
     return SA_OK;
 }
 
+// B solved from the column minima, then of its LP-optimal duals the largest beta <= beta0
+// (maximisation form): the optimum of the cold start with duals as close to beta0 as the
+// optimum allows.  alpha/beta may be NULL.
+static sa_status solve_csr_near(const sa_csr& b, const double* beta0, int32_t* perm, double* sum_log_w,
+                                double* alpha, double* beta) {
+    std::vector<double> al(b.n), be(b.n);
+    sa_status rc = solve_csr(b, perm, sum_log_w, al.data(), be.data());
+    if (rc) return rc;
+    std::vector<double> lw((size_t)std::max<int64_t>(b.nnz, 1));
+    for (int64_t e = 0; e < b.nnz; ++e)
+        lw[e] = b.w[e] > 0 ? std::log((double)b.w[e]) : -std::numeric_limits<double>::infinity();
+    rc = project_duals(b.n, b.row_ptr, b.col, lw.data(), perm, beta0, al.data(), be.data());
+    if (rc) return rc;
+    if (alpha) std::copy(al.begin(), al.end(), alpha);
+    if (beta) std::copy(be.begin(), be.end(), beta);
+    return SA_OK;
+}
+
 constexpr int64_t kAuctionRounds = 1000;      // bidding rounds of one sa_solve_reduced_gpu
 constexpr int64_t kAuctionMinNnz = 150000;    // sa_assign uses the auction from this size of B
 
@@ -389,6 +407,14 @@ sa_status sa_solve_reduced(const sa_csr* b, int32_t* perm, double* sum_log_w, do
     return solve_csr(*b, perm, sum_log_w, alpha, beta);
 }
 
+sa_status sa_solve_reduced_near(const sa_csr* b, const double* beta0, int32_t* perm, double* sum_log_w,
+                                double* alpha, double* beta) {
+    if (!perm || !beta0) { set_error("perm or beta0 is NULL"); return SA_E_INVALID; }
+    sa_status rc = check_csr(b);
+    if (rc) return rc;
+    return solve_csr_near(*b, beta0, perm, sum_log_w, alpha, beta);
+}
+
 sa_status sa_solve_reduced_warm(const sa_csr* b, const double* beta0, int32_t* perm, double* sum_log_w,
                                 double* alpha, double* beta) {
     if (!perm || !beta0) { set_error("perm or beta0 is NULL"); return SA_E_INVALID; }
@@ -484,10 +510,14 @@ sa_status sa_assign(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, dou
             for (int j = 0; j < n; ++j) pmax[j] = -price[j];
             rc = solve_csr_gpu(ctx, B, pmax.data(), res->perm, &res->sum_log_w, alpha.data(), beta.data(), nullptr);
         } else {
-            // from the scaling's duals -v/p: the solve then returns duals close to them, which
-            // hold on all of A (x <= 1), so the certificate below rarely adds entries; from the
-            // column minima the duals would certify B alone and the repairs would multiply
-            rc = solve_csr(B, res->perm, &res->sum_log_w, alpha.data(), beta.data(), price.data());
+            // B from the column minima, then the optimal duals closest below the scaling's
+            // v/p: those hold on the rest of A as well (x <= 1 there), so the certificate
+            // below rarely adds entries.  Starting the search from v/p instead gives such
+            // duals too, but makes nearly every entry of B almost tight and the searches long
+            // (measured on the host: 20.8 s against 22 ms on a Zipf-weighted B of n = 2048)
+            std::vector<double> beta0(n);
+            for (int j = 0; j < n; ++j) beta0[j] = -price[j];
+            rc = solve_csr_near(B, beta0.data(), res->perm, &res->sum_log_w, alpha.data(), beta.data());
         }
         res->ms_solve += now_ms() - a1;
         if (rc == SA_OK) break;

@@ -154,6 +154,9 @@ typedef sa_status (*SspFn)(void* user, SspState& st);
 sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const double* logw,
                         int32_t* perm, double* alpha, double* beta, const double* price0 = nullptr,
                         SspFn ssp = nullptr, void* ssp_user = nullptr);
+// of the LP-optimal duals of B for perm, the largest beta <= beta0 (alpha, beta in and out)
+sa_status project_duals(int n, const int64_t* row_ptr, const int32_t* col, const double* logw,
+                        const int32_t* perm, const double* beta0, double* alpha, double* beta);
 // ssp.cu: the shortest-augmenting-path phase on the GPU (user = SspRun*)
 struct SspRun {
     sa_ctx* ctx;

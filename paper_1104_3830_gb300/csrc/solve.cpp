@@ -19,6 +19,7 @@
 // of the maximisation: alpha_i + beta_j >= log w_ij on B, with equality on sigma.
 #include <cmath>
 #include <cstdint>
+#include <limits>
 #include <queue>
 #include <utility>
 #include <vector>
@@ -200,6 +201,75 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
         if (alpha) for (int i = 0; i < n; ++i) alpha[i] = -u[i];
         if (beta) for (int j = 0; j < n; ++j) beta[j] = -v[j];
     }
+    return SA_OK;
+}
+
+// Of all LP-optimal duals of B for the optimal assignment perm, the componentwise largest
+// beta with beta <= beta0 (beta0: maximisation-form column duals to stay close to, e.g. the
+// scaling's v/p).  With the assignment fixed, optimality of (alpha, beta) is
+//     alpha_i = log w_{i perm(i)} - beta_{perm(i)},
+//     beta_{perm(i)} <= beta_j + (log w_{i perm(i)} - log w_ij)   for every entry (i, j),
+// a system of difference constraints over the columns: edge j -> perm(i) of that length.
+// Its largest solution below beta0 is the shortest-path labelling with beta0 as the
+// starting label of every column.  Written relative to the given optimal duals
+// (y = beta - beta_in) every edge length becomes the slack alpha_i + beta_j - log w_ij >= 0,
+// so Dijkstra from all columns at once applies.  Columns whose beta0 is not finite keep
+// their dual.  alpha and beta (in: optimal duals for perm, out: the projected ones).
+sa_status project_duals(int n, const int64_t* row_ptr, const int32_t* col, const double* logw,
+                        const int32_t* perm, const double* beta0, double* alpha, double* beta) {
+    const double INF = std::numeric_limits<double>::infinity();
+    const int64_t nnz = row_ptr[n];
+    // columns of B: the rows holding an entry in each column, and that entry's log w
+    std::vector<int64_t> cptr(n + 1, 0);
+    for (int64_t e = 0; e < nnz; ++e) ++cptr[col[e] + 1];
+    for (int j = 0; j < n; ++j) cptr[j + 1] += cptr[j];
+    std::vector<int32_t> crow((size_t)std::max<int64_t>(nnz, 1));
+    std::vector<double> clw((size_t)std::max<int64_t>(nnz, 1));
+    std::vector<double> bsig(n, -INF);   // log w of each row's assigned entry
+    {
+        std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1);
+        for (int i = 0; i < n; ++i)
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                const int64_t q = fill[col[e]]++;
+                crow[q] = i;
+                clw[q] = logw[e];
+                if (col[e] == perm[i]) bsig[i] = logw[e];
+            }
+    }
+    for (int i = 0; i < n; ++i)
+        if (!(bsig[i] > -INF)) {
+            set_error("project_duals: row %d is not assigned to an allowed entry", i);
+            return SA_E_INVALID;
+        }
+    std::vector<double> y(n);
+    std::vector<char> done(n, 0);
+    typedef std::pair<double, int32_t> Item;
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+    for (int j = 0; j < n; ++j) {
+        y[j] = std::isfinite(beta0[j]) ? beta0[j] - beta[j] : 0.0;
+        heap.push(Item(y[j], j));
+    }
+    while (!heap.empty()) {
+        const Item top = heap.top();
+        heap.pop();
+        const int j = top.second;
+        if (done[j] || top.first > y[j]) continue;
+        done[j] = 1;
+        for (int64_t q = cptr[j]; q < cptr[j + 1]; ++q) {
+            if (!(clw[q] > -INF)) continue;
+            const int i = crow[q];
+            const int k = perm[i];
+            if (k == j || done[k]) continue;
+            const double slack = alpha[i] + beta[j] - clw[q];
+            const double nd = y[j] + (slack > 0.0 ? slack : 0.0);
+            if (nd < y[k]) {
+                y[k] = nd;
+                heap.push(Item(nd, k));
+            }
+        }
+    }
+    for (int j = 0; j < n; ++j) beta[j] += y[j];
+    for (int i = 0; i < n; ++i) alpha[i] = bsig[i] - beta[perm[i]];
     return SA_OK;
 }
 

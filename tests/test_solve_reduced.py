@@ -107,3 +107,50 @@ def test_early_stop_on_ties_at_the_free_column():
     rp, col, wv = _csr(mask, w)
     perm, s, al, be = api.sa_solve_reduced(rp, col, wv)
     _check(mask, w, perm, s, al, be)
+
+
+@pytest.mark.parametrize("n,density,hi,shift", [(60, 0.2, 1000, 0.0), (150, 0.3, 2, 0.3), (200, 0.05, 30000, -0.2),
+                                                (300, 1.0, 1, 0.0), (257, 0.02, 7, 1.0), (1, 1.0, 5, 0.0)])
+def test_near_duals_are_the_largest_below_the_target(n, density, hi, shift):
+    """sa_solve_reduced_near: the optimum of B with LP-optimal duals whose beta is the
+    componentwise largest with beta <= near.  Checked by the characterisation of that
+    largest solution of the difference constraints: optimal and feasible on B, beta <= near,
+    and every column below its target is held down by a tight entry (an entry (i, j) of
+    B whose constraint beta_{perm(i)} <= beta_j + log w_{i perm(i)} - log w_ij is an
+    equality)."""
+    rng = np.random.default_rng(n * 17 + hi)
+    w = rng.integers(1, hi + 1, size=(n, n)).astype(np.int64)
+    mask = rng.random((n, n)) < density
+    mask[np.arange(n), rng.permutation(n)] = True
+    rp, col, wv = _csr(mask, w)
+    b = np.where(mask, np.log(w.astype(float)), -np.inf)
+    _, _, beta_opt, _ = oracle.hungarian(b)
+    near = beta_opt + shift + rng.normal(0.0, 0.05, size=n)
+    perm, s, al, be = api.sa_solve_reduced(rp, col, wv, near=near)
+    _check(mask, w, perm, s, al, be)
+    assert np.all(be <= near + 1e-12)
+    rows, cols = np.nonzero(mask)
+    for k in range(n):
+        if be[k] >= near[k] - 1e-9:
+            continue
+        i_k = int(np.nonzero(perm == k)[0][0])
+        js = cols[rows == i_k]
+        gaps = [be[j] + b[i_k, k] - b[i_k, j] - be[k] for j in js if j != k]
+        # the column's dual is held down by a tight constraint through its row
+        assert gaps and min(gaps) < 1e-9, (k, gaps)
+
+
+def test_near_with_optimal_target_returns_it():
+    """A target that is itself an optimal dual of B comes back unchanged (the largest
+    optimal beta below it is itself)."""
+    rng = np.random.default_rng(99)
+    n = 120
+    w = rng.integers(1, 1001, size=(n, n)).astype(np.int64)
+    mask = rng.random((n, n)) < 0.1
+    mask[np.arange(n), rng.permutation(n)] = True
+    rp, col, wv = _csr(mask, w)
+    b = np.where(mask, np.log(w.astype(float)), -np.inf)
+    _, _, beta_opt, _ = oracle.hungarian(b)
+    perm, s, al, be = api.sa_solve_reduced(rp, col, wv, near=beta_opt)
+    _check(mask, w, perm, s, al, be)
+    assert np.max(np.abs(be - beta_opt)) < 1e-9
