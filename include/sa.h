@@ -322,10 +322,12 @@ typedef struct {
 
 /*
  * sa_assign: scale (sa_scale), prune at t (sa_prune, guard on), solve B
- * (sa_solve_reduced; sa_solve_reduced_gpu from the scaling's duals when the environment
- * sets SA_SOLVE_GPU=1 at sa_create and B has at least 150000 entries), then certify on A (sa_certify, tau = 1e-9) and
- * re-solve with the violating entries added until none is left; the result is optimal
- * for A.  If B has no perfect matching, re-prune at t/16 (finally t = 0, i.e. all of A).
+ * (sa_solve_reduced_near toward the scaling's duals v/p; sa_solve_reduced_gpu from those
+ * duals when the environment sets SA_SOLVE_GPU=1 at sa_create and B has at least 150000
+ * entries), then certify on A (sa_certify, tau = 1e-9) and re-solve from the last duals
+ * with the violating entries added until none is left (SA_E_NOT_CONVERGED if that does
+ * not settle); the result is optimal for A.  If B has no perfect matching, re-prune at
+ * t/16 (finally t = 0, i.e. all of A).
  */
 sa_status sa_assign(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* opts, double t,
                     sa_assign_result* res);
@@ -423,7 +425,10 @@ void sa_server_destroy(sa_server* s);
  * Returns SA_E_BUDGET if the request alone exceeds the budget. */
 sa_status sa_submit(sa_server* s, const void* host_w, sa_wtype wtype, int32_t n, uint64_t* ticket);
 
-/* SA_PENDING until the request is done; then SA_OK (or its error) with *out filled. */
+/* SA_PENDING until the request is done; then SA_OK (or its error) with *out filled.  Every
+ * finished request's permutation is the certified optimum of its matrix, as from sa_assign
+ * (small requests: batched scaling, then sa_solve_reduced_near toward v/p, the certificate
+ * and its repairs; SA_E_NOT_CONVERGED if the repairs do not settle). */
 sa_status sa_poll(sa_server* s, uint64_t ticket, sa_result* out);
 void sa_result_release(sa_server* s, uint64_t ticket);
 

@@ -115,28 +115,40 @@ sa_status upload(Request* r, cudaStream_t st, void** d_w, int64_t* ld) {
 // prune + solve + certify one scaled instance (the tail of sa_assign)
 sa_status finish_small(sa_ctx* ctx, Request* r, const sa_matrix* a, const double* d_u, const double* d_v,
                        double p) {
+    // the scaling's column duals v/p: B is solved from the column minima and then given the
+    // optimal duals closest below them, which hold on the rest of A as well (x <= 1 there),
+    // so the certificate rarely adds entries
+    std::vector<double> beta0(r->n);
+    SA_CUDA(cudaMemcpyAsync(beta0.data(), d_v, sizeof(double) * r->n, cudaMemcpyDeviceToHost, ctx->stream));
+    SA_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (double& x : beta0) x /= p;
     sa_csr B{};
     double log_ub = 0;
     sa_status rc = sa_prune(ctx, a, p, d_u, d_v, 0.0, 1, &B, &log_ub);
     if (rc) return rc;
     std::vector<double> al(r->n), be(r->n);
     r->perm.assign(r->n, -1);
-    rc = sa_solve_reduced(&B, r->perm.data(), &r->sum_log_w, al.data(), be.data());
+    rc = sa_solve_reduced_near(&B, beta0.data(), r->perm.data(), &r->sum_log_w, al.data(), be.data());
     double t = 1.0 / r->n;
     while (rc == SA_E_NO_PERFECT_MATCHING && t > 0) {
         sa_csr_free(&B);
         t = t / 16 < 1e-300 ? 0.0 : t / 16;
         rc = sa_prune(ctx, a, p, d_u, d_v, t, 1, &B, nullptr);
         if (rc) return rc;
-        rc = sa_solve_reduced(&B, r->perm.data(), &r->sum_log_w, al.data(), be.data());
+        rc = sa_solve_reduced_near(&B, beta0.data(), r->perm.data(), &r->sum_log_w, al.data(), be.data());
     }
     if (rc) { sa_csr_free(&B); return rc; }
     r->gamma = std::exp(log_ub - r->sum_log_w);
+    bool certified = false;
     for (int iter = 0; iter < 64; ++iter) {
         int64_t nv = 0;
         sa_csr add{};
         rc = sa_certify(ctx, a, al.data(), be.data(), 1e-9, &nv, 1 << 16, &add);
-        if (rc || nv == 0) { sa_csr_free(&add); break; }
+        if (rc || nv == 0) {
+            certified = rc == SA_OK;
+            sa_csr_free(&add);
+            break;
+        }
         // merge and re-solve
         std::vector<int64_t> rp(r->n + 1, 0);
         std::vector<int32_t> cols, ws;
@@ -156,10 +168,16 @@ sa_status finish_small(sa_ctx* ctx, Request* r, const sa_matrix* a, const double
         memcpy(B.row_ptr, rp.data(), 8 * (r->n + 1));
         memcpy(B.col, cols.data(), 4 * cols.size());
         memcpy(B.w, ws.data(), 4 * ws.size());
-        rc = sa_solve_reduced(&B, r->perm.data(), &r->sum_log_w, al.data(), be.data());
+        // from the last optimal duals: only the added entries break their optimality
+        const std::vector<double> prev(be);
+        rc = sa_solve_reduced_warm(&B, prev.data(), r->perm.data(), &r->sum_log_w, al.data(), be.data());
         if (rc) break;
     }
     sa_csr_free(&B);
+    if (rc == SA_OK && !certified) {
+        sa::set_error("duality repair did not settle");
+        rc = SA_E_NOT_CONVERGED;
+    }
     return rc;
 }
 
