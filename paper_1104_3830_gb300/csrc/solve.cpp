@@ -117,30 +117,53 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
         const sa_status rc = ssp(ssp_user, st);
         if (rc) return rc;
     }
-    std::vector<double> dist(n, INF), pcost(n, INF);   // pcost: cost of the entry (pred, j)
-    std::vector<int32_t> pred(n, -1), stamp(n, -1), done(n, -1), scanned;
+    int nfree = 0;
+    for (int i = 0; i < n; ++i) nfree += rmatch[i] < 0;
+    // the searches read a compacted copy of B: allowed entries only, with their costs
+    std::vector<int64_t> srp(n + 1, 0);
+    std::vector<int32_t> scol;
+    std::vector<double> scost;
+    if (nfree > 0) {
+        scol.reserve((size_t)row_ptr[n]);
+        scost.reserve((size_t)row_ptr[n]);
+        for (int i = 0; i < n; ++i) {
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+                if (logw[e] > -INF) {
+                    scol.push_back(col[e]);
+                    scost.push_back(-logw[e]);
+                }
+            srp[i + 1] = (int64_t)scol.size();
+        }
+    }
+    // per column and search: state 2*epoch once reached (dist, pred, pcost valid), 2*epoch+1
+    // once scanned; pcost is the cost of the entry (pred, j)
+    std::vector<double> dist(n, INF), pcost(n, INF);
+    std::vector<int32_t> pred(n, -1), scanned;
+    std::vector<int64_t> state(n, 0);
     scanned.reserve(n);
     typedef std::pair<double, int32_t> Item;
-    int epoch = 0;
+    std::vector<Item> heapbuf;
+    int64_t epoch = 0;
     for (int r = 0; r < n; ++r) {
         if (rmatch[r] >= 0) continue;
         ++epoch;
+        const int64_t reached = 2 * epoch, finished = 2 * epoch + 1;
         scanned.clear();
-        std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+        heapbuf.clear();
+        std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap(std::greater<Item>(), std::move(heapbuf));
         // the nearest free column reached so far: it goes to no heap, and the search ends
         // as soon as no column in the heap is strictly nearer (Dijkstra's stopping rule at
         // the first target; on ties it saves scanning every matched column at that distance)
         int sink = -1;
         double dmin = INF;
-        for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-            if (!(logw[e] > -INF)) continue;
-            const int j = col[e];
-            const double d = -logw[e] - v[j];
-            if (stamp[j] != epoch || d < dist[j]) {
-                stamp[j] = epoch;
+        for (int64_t e = srp[r]; e < srp[r + 1]; ++e) {
+            const int j = scol[e];
+            const double d = scost[e] - v[j];
+            if (state[j] != reached || d < dist[j]) {
+                state[j] = reached;
                 dist[j] = d;
                 pred[j] = r;
-                pcost[j] = -logw[e];
+                pcost[j] = scost[e];
                 if (cmatch[j] < 0) {
                     if (d < dmin) { dmin = d; sink = j; }
                 } else {
@@ -149,31 +172,34 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
             }
         }
         while (!heap.empty()) {
-            Item top = heap.top();
+            const Item top = heap.top();
             if (top.first >= dmin) break;
             heap.pop();
             const int j = top.second;
-            if (done[j] == epoch || top.first > dist[j]) continue;
-            done[j] = epoch;
+            if (state[j] == finished || top.first > dist[j]) continue;
+            state[j] = finished;
             scanned.push_back(j);
             const int i = cmatch[j];
             // reduced cost of the assigned entry (i, j); zero-length step through row i
             const double ui = mcost[i] - v[j];
-            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-                if (!(logw[e] > -INF)) continue;
-                const int k = col[e];
-                if (done[k] == epoch) continue;
-                const double nd = dist[j] + (-logw[e] - v[k]) - ui;
-                if (stamp[k] != epoch || nd < dist[k]) {
-                    stamp[k] = epoch;
-                    dist[k] = nd;
-                    pred[k] = i;
-                    pcost[k] = -logw[e];
-                    if (cmatch[k] < 0) {
-                        if (nd < dmin) { dmin = nd; sink = k; }
-                    } else if (nd < dmin) {
-                        heap.push(Item(nd, k));
-                    }
+            const double dj = dist[j];
+            for (int64_t e = srp[i]; e < srp[i + 1]; ++e) {
+                const int k = scol[e];
+                const double nd = dj + (scost[e] - v[k]) - ui;
+                // a column not nearer than the nearest free one is never scanned and keeps
+                // its price: its label does not matter
+                if (!(nd < dmin)) continue;
+                const int64_t sk = state[k];
+                if (sk == finished || (sk == reached && !(nd < dist[k]))) continue;
+                state[k] = reached;
+                dist[k] = nd;
+                pred[k] = i;
+                pcost[k] = scost[e];
+                if (cmatch[k] < 0) {
+                    dmin = nd;
+                    sink = k;
+                } else {
+                    heap.push(Item(nd, k));
                 }
             }
         }
