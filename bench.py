@@ -536,8 +536,9 @@ def run_serve(args):
 def run_reduced(args):
     """Reduced-solve form: B from the scaling (p = 1, 2, ..., 256) and prune (t = 1/n) of
     uniform int16 instances (weights in [1, 1000], the serving distribution), solved exactly
-    by the host solver from the column minima and from the scaling's duals (as sa_assign
-    starts it), and by the GPU path (sa_solve_reduced_gpu:
+    by the host solver from the column minima, from the scaling's duals, and from the
+    column minima with the duals then moved next to the scaling's (sa_solve_reduced_near,
+    as sa_assign solves B), and by the GPU path (sa_solve_reduced_gpu:
     GPU auction for the starting prices, host greedy pass and row reduction, each shortest
     augmenting path search on the GPU); wall time of each solve and the optimum (equal)."""
     import torch
@@ -555,6 +556,8 @@ def run_reduced(args):
         rp, col, wv, _ = api.sa_prune(ctx, d, ps[-1], u, v)
         vv = v.cpu().numpy() / ps[-1]
         api.sa_solve_reduced_gpu(ctx, rp, col, wv, price0=vv)   # warm-up (build, allocation)
+        tn = time.perf_counter()
+        _, s_n, _, _ = api.sa_solve_reduced(rp, col, wv, near=vv)      # host, sa_assign's way
         tw = time.perf_counter()
         _, s_w, _, _ = api.sa_solve_reduced(rp, col, wv, beta0=vv)     # host, from the scaling's duals
         t0 = time.perf_counter()
@@ -573,6 +576,7 @@ def run_reduced(args):
         t4 = time.perf_counter()
         s_o = float(bb[np.arange(n), ph].sum()) if st == 0 else float("nan")
         out.append({"n": n, "nnz": int(len(col)), "host_ms": (t1 - t0) * 1e3, "host_warm_ms": (t0 - tw) * 1e3,
+                    "host_near_ms": (tw - tn) * 1e3, "near_same_optimum": abs(s_n - s_h) <= 1e-9 + 1e-13 * abs(s_h),
                     "warm_same_optimum": abs(s_w - s_h) <= 1e-9 + 1e-13 * abs(s_h), "gpu_auction_ms": ai["auction_ms"],
                     "gpu_exact_phase_ms": ai["host_ms"], "gpu_total_ms": (t2 - t1) * 1e3,
                     "rounds": ai["rounds"], "phases": ai["phases"], "complete": ai["complete"],
