@@ -154,3 +154,36 @@ def test_near_with_optimal_target_returns_it():
     perm, s, al, be = api.sa_solve_reduced(rp, col, wv, near=beta_opt)
     _check(mask, w, perm, s, al, be)
     assert np.max(np.abs(be - beta_opt)) < 1e-9
+
+
+@pytest.mark.parametrize("case", ["uniform", "zipf", "planted", "tied", "few_values"])
+def test_near_duals_certify_all_of_a(case):
+    """The first solve of sa_assign on the host: B from the oracle's scaling and prune
+    (t = 1/n), solved by sa_solve_reduced_near toward v/p.  On these seeded workloads the
+    returned duals hold on all of A (no entry for the certificate to add), while the duals
+    of the plain solve from the column minima miss entries on the Zipf workload."""
+    from paper_1104_3830_gb300 import workloads as W
+    ps = [2.0 ** k for k in range(9)]
+    if case == "uniform":
+        w = W.uniform(160, 1, 1000, 31, dtype=np.int32)
+    elif case == "zipf":
+        w = W.zipf(300, 1.2, 30000, 603)
+    elif case == "planted":
+        w, _, _ = W.planted(200, 32)
+    elif case == "tied":
+        w, _, _ = W.planted(256, 33, tied_frac=0.05)
+    else:
+        w = W.uniform(150, 1, 3, 34, dtype=np.int32)
+    w = np.asarray(w).astype(np.int64)
+    b = oracle.log_weights(w)
+    u, v, _, _, _ = oracle.sinkhorn(b, ps, 1e-6, 2000)
+    m = oracle.prune_mask(b, ps[-1], u, v)
+    rp, col = oracle.prune_csr(m)
+    wv = w[m].astype(np.int32)
+    perm, s, al, be = api.sa_solve_reduced(rp, col, wv, near=v / ps[-1])
+    assert all(m[i, perm[i]] for i in range(len(perm)))
+    assert oracle.dual_violations(b, al, be, 1e-9)[0] == 0
+    assert oracle.perm_weight_exact(w, perm) == oracle.perm_weight_exact(w, oracle.hungarian(b)[0])
+    if case == "zipf":
+        _, _, alc, bec = api.sa_solve_reduced(rp, col, wv)
+        assert oracle.dual_violations(b, alc, bec, 1e-9)[0] > 0
