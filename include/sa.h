@@ -50,7 +50,7 @@ typedef enum {
     SA_E_NONFINITE = -6,          /* a row or column lost all mass (no support, Sec. 2.1) */
     SA_E_BUDGET = -7,             /* request larger than the server's memory budget */
     SA_E_TIMEOUT = -8,            /* a bounded device wait gave up (kernel returned early) */
-    SA_E_UNSUPPORTED = -9         /* valid request this build cannot run (e.g. n too large) */
+    SA_E_UNSUPPORTED = -9         /* valid request the library does not support (e.g. n too large) */
 } sa_status;
 
 typedef enum { SA_I16 = 0, SA_I32 = 1 } sa_wtype;

@@ -25,8 +25,9 @@ Every function follows a passage of Sharify, Gaubert and Grigori, arXiv:1104.383
                           symmetric embedding of A^(p)), dense FP64 solves
 
 Parity pins live in ``tests/test_oracle_*.py``.  Nothing is "parity unpinned" except
-the paper's Tables 1-3 and the printed digits of the 5x5 X(50), whose inputs are not
-reproducible.
+the paper's Tables 1-3 (their test matrices are not available here) and the printed
+digits of the 5x5 X(50) (p = 50 amplifies the rounding of the printed 3-decimal A beyond
+the printed digits).
 """
 from __future__ import annotations
 
