@@ -63,3 +63,31 @@ def test_host_only_entry_points_without_gpu(libsa):
     h = ctypes.c_void_p()
     st = lib.sa_create(ctypes.byref(h), 0, None)
     assert st != 0
+
+
+def test_host_solver_argument_errors(libsa):
+    """The host solve entry points report bad arguments as SA_E_INVALID (-1) with a message:
+    NULL instance, NULL perm, NULL beta0, a column index out of range, n <= 0."""
+    import numpy as np
+    from paper_1104_3830_gb300 import _lib as L
+    lib = L.lib()
+    rp = np.array([0, 2, 4], dtype=np.int64)
+    col = np.array([0, 1, 0, 1], dtype=np.int32)
+    w = np.array([1, 2, 3, 4], dtype=np.int32)
+    c = L.sa_csr(2, 4, rp.ctypes.data_as(L._I64P), col.ctypes.data_as(L._I32P), w.ctypes.data_as(L._I32P))
+    perm = np.zeros(2, dtype=np.int32)
+    b0 = np.zeros(2)
+    pp, bp = perm.ctypes.data_as(L._I32P), b0.ctypes.data_as(L._DP)
+    assert lib.sa_solve_reduced(None, pp, None, None, None) == -1
+    assert lib.sa_solve_reduced(ctypes.byref(c), None, None, None, None) == -1
+    for f in (lib.sa_solve_reduced_warm, lib.sa_solve_reduced_near):
+        assert f(ctypes.byref(c), None, pp, None, None, None) == -1
+        assert f(None, bp, pp, None, None, None) == -1
+        assert f(ctypes.byref(c), bp, pp, None, None, None) == 0
+        assert sorted(perm) == [0, 1]
+    bad = np.array([0, 1, 0, 2], dtype=np.int32)
+    cb = L.sa_csr(2, 4, rp.ctypes.data_as(L._I64P), bad.ctypes.data_as(L._I32P), w.ctypes.data_as(L._I32P))
+    assert lib.sa_solve_reduced_near(ctypes.byref(cb), bp, pp, None, None, None) == -1
+    assert b"out of range" in lib.sa_last_error()
+    c0 = L.sa_csr(0, 0, rp.ctypes.data_as(L._I64P), col.ctypes.data_as(L._I32P), w.ctypes.data_as(L._I32P))
+    assert lib.sa_solve_reduced_warm(ctypes.byref(c0), bp, pp, None, None, None) == -1
