@@ -32,13 +32,23 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
                         int32_t* perm, double* alpha, double* beta, const double* price0, SspFn ssp,
                         void* ssp_user) {
     const double INF = std::numeric_limits<double>::infinity();
+    // a compacted copy of B for every loop below: allowed entries only, with their costs
+    std::vector<int64_t> srp(n + 1, 0);
+    std::vector<int32_t> scol;
+    std::vector<double> scost;
+    scol.reserve((size_t)row_ptr[n]);
+    scost.reserve((size_t)row_ptr[n]);
+    for (int i = 0; i < n; ++i) {
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            if (logw[e] > -INF) {
+                scol.push_back(col[e]);
+                scost.push_back(-logw[e]);
+            }
+        srp[i + 1] = (int64_t)scol.size();
+    }
     std::vector<double> v(n, INF);
-    for (int i = 0; i < n; ++i)
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            if (!(logw[e] > -INF)) continue;
-            const double c = -logw[e];
-            if (c < v[col[e]]) v[col[e]] = c;
-        }
+    for (size_t e = 0; e < scol.size(); ++e)
+        if (scost[e] < v[scol[e]]) v[scol[e]] = scost[e];
     for (int j = 0; j < n; ++j)
         if (v[j] == INF) {
             set_error("reduced instance: column %d has no allowed entry", j);
@@ -53,10 +63,9 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
     for (int i = 0; i < n; ++i) {
         double best = INF, bc = INF;
         int bj = -1;
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            if (!(logw[e] > -INF)) continue;
-            const double h = -logw[e] - v[col[e]];
-            if (h < best) { best = h; bj = col[e]; bc = -logw[e]; }
+        for (int64_t e = srp[i]; e < srp[i + 1]; ++e) {
+            const double h = scost[e] - v[scol[e]];
+            if (h < best) { best = h; bj = scol[e]; bc = scost[e]; }
         }
         if (bj < 0) {
             set_error("reduced instance: row %d has no allowed entry", i);
@@ -81,15 +90,14 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
                 const int i = freel[k++];
                 double u1 = INF, u2 = INF, c1 = INF, c2 = INF;
                 int j1 = -1, j2 = -1;
-                for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-                    if (!(logw[e] > -INF)) continue;
-                    const int j = col[e];
-                    const double h = -logw[e] - v[j];
+                for (int64_t e = srp[i]; e < srp[i + 1]; ++e) {
+                    const int j = scol[e];
+                    const double h = scost[e] - v[j];
                     if (h < u1) {
                         u2 = u1; j2 = j1; c2 = c1;
-                        u1 = h; j1 = j; c1 = -logw[e];
+                        u1 = h; j1 = j; c1 = scost[e];
                     } else if (h < u2) {
-                        u2 = h; j2 = j; c2 = -logw[e];
+                        u2 = h; j2 = j; c2 = scost[e];
                     }
                 }
                 if (j1 < 0) break;   // no allowed entry: reported by the search below
@@ -116,24 +124,6 @@ sa_status sparse_assign(int n, const int64_t* row_ptr, const int32_t* col, const
         SspState st{n, row_ptr, col, logw, v.data(), rmatch.data(), cmatch.data(), mcost.data()};
         const sa_status rc = ssp(ssp_user, st);
         if (rc) return rc;
-    }
-    int nfree = 0;
-    for (int i = 0; i < n; ++i) nfree += rmatch[i] < 0;
-    // the searches read a compacted copy of B: allowed entries only, with their costs
-    std::vector<int64_t> srp(n + 1, 0);
-    std::vector<int32_t> scol;
-    std::vector<double> scost;
-    if (nfree > 0) {
-        scol.reserve((size_t)row_ptr[n]);
-        scost.reserve((size_t)row_ptr[n]);
-        for (int i = 0; i < n; ++i) {
-            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-                if (logw[e] > -INF) {
-                    scol.push_back(col[e]);
-                    scost.push_back(-logw[e]);
-                }
-            srp[i + 1] = (int64_t)scol.size();
-        }
     }
     // per column and search: state 2*epoch once reached (dist, pred, pcost valid), 2*epoch+1
     // once scanned; pcost is the cost of the entry (pred, j)
