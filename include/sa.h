@@ -365,7 +365,9 @@ typedef struct {
 /*
  * sa_algorithm1: the paper's preprocessing algorithm on a device matrix.  Each round
  * warm-starts the scaling from the previous round's potentials (scaled by the ratio of the
- * p values).  A round whose B holds no permutation counts as gamma = +inf.  Returns SA_OK
+ * p values); its B is solved exactly from the column minima (sa_solve_reduced), since
+ * gamma needs only B's optimal weight.  A round whose B holds no permutation counts as
+ * gamma = +inf.  Returns SA_OK
  * with gamma <= opt_ratio, or SA_E_NOT_CONVERGED after max_rounds (res filled with the
  * last round).  Unlike sa_assign the result is only certified to within gamma.
  */
