@@ -15,8 +15,9 @@
 // resolves concurrent relaxations; relaxations no shorter than the best free column found
 // so far are dropped.  A breadth-first pass over tight entries (relaxations that reproduce
 // the converged distances exactly) then gives every column on a shortest path a
-// predecessor, and the price update and the flip run on the device.  The host
-// reads only the frontier size per round and the sink per search; no kernel waits.
+// predecessor, and the price update and the flip run on the device.  The host queues the
+// rounds in batches of eight and reads only the frontier size after each batch and the sink
+// after each search; no kernel waits on another.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
