@@ -185,8 +185,10 @@ void small_worker(sa_server* s) {
     cudaSetDevice(s->device);
     cudaStream_t st;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    // without a context on the device the worker still takes its requests and fails each
+    // with the creation status, so that no request of its class stays pending
     sa_ctx* ctx = nullptr;
-    if (sa_create(&ctx, s->device, st) != SA_OK) return;
+    const sa_status crc = sa_create(&ctx, s->device, st);
     for (;;) {
         std::vector<Request*> group;
         {
@@ -201,6 +203,10 @@ void small_worker(sa_server* s) {
             group = admit(s, true, 256, lk);
         }
         if (group.empty()) continue;
+        if (crc != SA_OK) {
+            for (Request* r : group) finish(s, r, crc);
+            continue;
+        }
         const int k = (int)group.size();
         std::vector<void*> dw(k, nullptr);
         std::vector<int32_t> ns(k);
@@ -255,7 +261,7 @@ void small_worker(sa_server* s) {
             }
         }
     }
-    sa_destroy(ctx);
+    if (ctx) sa_destroy(ctx);
     cudaStreamDestroy(st);
 }
 
@@ -264,8 +270,8 @@ void large_worker(sa_server* s) {
     cudaStream_t st;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     sa_ctx* ctx = nullptr;
-    if (sa_create(&ctx, s->device, st) != SA_OK) return;
-    ctx->max_grid = s->large_grid;
+    const sa_status crc = sa_create(&ctx, s->device, st);   // failing: as in small_worker
+    if (crc == SA_OK) ctx->max_grid = s->large_grid;
     for (;;) {
         Request* r = nullptr;
         {
@@ -280,6 +286,10 @@ void large_worker(sa_server* s) {
             auto got = admit(s, false, 1, lk);
             if (got.empty()) continue;
             r = got[0];
+        }
+        if (crc != SA_OK) {
+            finish(s, r, crc);
+            continue;
         }
         void* dw = nullptr;
         int64_t ld = 0;
@@ -298,7 +308,7 @@ void large_worker(sa_server* s) {
         }
         finish(s, r, rc);
     }
-    sa_destroy(ctx);
+    if (ctx) sa_destroy(ctx);
     cudaStreamDestroy(st);
 }
 
