@@ -155,8 +155,10 @@ static sa_status solve_csr(const sa_csr& b, int32_t* perm, double* sum_log_w, do
     if (sum_log_w) {
         double s = 0.0;
         for (int i = 0; i < b.n; ++i) {
+            double best = -std::numeric_limits<double>::infinity();   // a repeated column: its best entry
             for (int64_t e = b.row_ptr[i]; e < b.row_ptr[i + 1]; ++e)
-                if (b.col[e] == perm[i]) { s += lw[e]; break; }
+                if (b.col[e] == perm[i] && lw[e] > best) best = lw[e];
+            s += best;
         }
         *sum_log_w = s;
     }
@@ -255,9 +257,12 @@ static sa_status solve_csr_gpu(sa_ctx* ctx, const sa_csr& b, const double* price
     info->auction_ms = t1 - t0;
     if (complete) {
         double s = 0.0;
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < n; ++i) {
+            double best = -INFINITY;   // a repeated column: its best entry
             for (int64_t e = b.row_ptr[i]; e < b.row_ptr[i + 1]; ++e)
-                if (b.col[e] == asg[i]) { s += lw[e]; break; }
+                if (b.col[e] == asg[i] && lw[e] > best) best = lw[e];
+            s += best;
+        }
         info->auction_sum_log_w = s;
     }
     // the exact solver from the auction's prices (its minimisation-form prices are -beta),

@@ -249,7 +249,7 @@ sa_status project_duals(int n, const int64_t* row_ptr, const int32_t* col, const
                 const int64_t q = fill[col[e]]++;
                 crow[q] = i;
                 clw[q] = logw[e];
-                if (col[e] == perm[i]) bsig[i] = logw[e];
+                if (col[e] == perm[i] && logw[e] > bsig[i]) bsig[i] = logw[e];   // repeated columns: the best
             }
     }
     for (int i = 0; i < n; ++i)

@@ -187,3 +187,19 @@ def test_near_duals_certify_all_of_a(case):
     if case == "zipf":
         _, _, alc, bec = api.sa_solve_reduced(rp, col, wv)
         assert oracle.dual_violations(b, alc, bec, 1e-9)[0] > 0
+
+
+def test_repeated_columns_in_a_row():
+    """A caller's CSR may list a column twice in a row with different weights: the solvers
+    then use the larger weight, and the near duals stay feasible on every listed entry."""
+    rp = np.array([0, 3, 5, 7], dtype=np.int64)
+    col = np.array([0, 0, 1, 1, 2, 2, 0], dtype=np.int32)
+    w = np.array([2, 9, 3, 5, 1, 4, 7], dtype=np.int32)
+    for kw in ({}, {"near": np.zeros(3)}, {"beta0": np.ones(3)}):
+        perm, s, al, be = api.sa_solve_reduced(rp, col, w, **kw)
+        assert sorted(perm) == [0, 1, 2]
+        lw = np.log(w.astype(float))
+        rows = np.repeat(np.arange(3), np.diff(rp))
+        assert np.all(al[rows] + be[col] >= lw - 1e-12)
+        # the best permutation: row0 -> col0 (9), row1 -> col1 (5), row2 -> col2 (4)
+        assert list(perm) == [0, 1, 2] and abs(s - np.log(9 * 5 * 4)) < 1e-12
