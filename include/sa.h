@@ -218,8 +218,9 @@ sa_status sa_prune(sa_ctx* ctx, const sa_matrix* a, double p, const double* d_u,
  *   sum_log_w  host out (may be NULL): sum_i log w_{i perm(i)}
  *   alpha,beta host FP64[n] out (may be NULL): LP duals, alpha_i + beta_j >= log w_ij on
  *              B with equality on the assignment
- * Returns SA_E_NO_PERFECT_MATCHING when B holds no permutation.  Host only: needs no
- * context and no GPU.
+ * Returns SA_E_NO_PERFECT_MATCHING when B holds no permutation.  A column listed more
+ * than once in a row counts with its largest weight; entries with w = 0 are forbidden.
+ * Host only: needs no context and no GPU.
  */
 sa_status sa_solve_reduced(const sa_csr* b, int32_t* perm, double* sum_log_w, double* alpha,
                            double* beta);
