@@ -83,6 +83,12 @@ struct StepArgs {
     int* sweeps_out;       // n_p
     double* resid_out;     // n_p
     int max_rows;
+    uint64_t wait_ns;      // limit of the grid barriers' and the sweeps' ring waits (the
+                           // waits for copies in flight before an exit keep kWaitTimeoutNs)
+    int l2_keep_stages;    // stages of each stripe read with the default L2 policy; the
+                           // others are read "evict first", so the kept ones stay in L2
+    unsigned extra_arrivals;   // testing hook: arrivals the first grid barrier waits for
+                               // beyond the grid (nothing provides them: it runs out)
 };
 
 
@@ -123,7 +129,8 @@ __device__ __forceinline__ void fence_proxy_async_all() {
     asm volatile("fence.proxy.async;" ::: "memory");
 }
 
-__device__ __forceinline__ bool step_grid_sync(unsigned* ctr, unsigned target, int* err, int* s_ok) {
+__device__ __forceinline__ bool step_grid_sync(unsigned* ctr, unsigned target, int* err, int* s_ok,
+                                               uint64_t wait_ns) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -135,7 +142,7 @@ __device__ __forceinline__ bool step_grid_sync(unsigned* ctr, unsigned target, i
             while (ld_acquire(ctr) < target) {
                 if ((++spins & 31u) == 0) {
                     if (*(volatile int*)err != 0) { ok = 0; break; }
-                    if (globaltimer_ns() - t0 > kWaitTimeoutNs) { atomicCAS(err, 0, kErrTimeout); ok = 0; break; }
+                    if (globaltimer_ns() - t0 > wait_ns) { atomicCAS(err, 0, kErrTimeout); ok = 0; break; }
                 }
                 __nanosleep(32);
             }
@@ -229,9 +236,18 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     // in slot v % ring_n.  The warp whose release completes a slot's count refills it with
     // ring index v + ring_n: no thread waits to issue a copy.
     const int nst = (nrows + 1) / 2;
+    // Stage read at ring index v: the sweeps of an epoch alternate direction over the stripe,
+    // so the rows a sweep reads last -- the ones most likely still in L2 (K is about twice
+    // the L2 at n = 8192) -- are the rows the next sweep reads first.  The first sweep of an
+    // epoch runs backwards: the evaluation of K wrote the stripe forwards.
+    auto stage_of = [&](uint32_t v) -> int {
+        const int g = (int)(v % (uint32_t)nst);
+        return ((v / (uint32_t)nst) & 1u) ? g : nst - 1 - g;
+    };
     auto issue_index = [&](uint32_t v) {   // one thread
         const uint32_t slot = v % (uint32_t)ring_n;
-        const int q0 = 2 * (int)(v % (uint32_t)nst);
+        const int stg = stage_of(v);
+        const int q0 = 2 * stg;
         const int nr = min(2, nrows - q0);
         const void* src;
         unsigned bytes;
@@ -244,7 +260,12 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
         }
         iss_cnt[slot] += 1;
         mbar_arrive_expect_tx(&mbar[slot], bytes);
-        bulk_g2s(sbase + (size_t)slot * slot_bytes, src, bytes, &mbar[slot]);
+        // K is larger than L2: the first l2_keep_stages stages of every stripe keep the
+        // default policy and stay resident from sweep to sweep, the rest stream through
+        if ((SP && sparse) || stg < A.l2_keep_stages)
+            bulk_g2s(sbase + (size_t)slot * slot_bytes, src, bytes, &mbar[slot]);
+        else
+            bulk_g2s_hint(sbase + (size_t)slot * slot_bytes, src, bytes, &mbar[slot], l2_policy_evict_first());
     };
     auto prefetch_stage = [&](int g) {   // one thread: the K rows of stage g into L2
         const int q0 = 2 * g;
@@ -272,7 +293,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     };
     auto gsync = [&]() -> bool {
         ++nbar;
-        return step_grid_sync(A.bar, nbar * (unsigned)G, A.err, &s_ok);
+        return step_grid_sync(A.bar, nbar * (unsigned)G + A.extra_arrivals, A.err, &s_ok, A.wait_ns);
     };
 
     int cidx[CH];
@@ -484,7 +505,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
             if (!DIR && tid == 0 && nrows > 0)
                 for (uint32_t v = 0; v < (uint32_t)ring_n; ++v) issue_index(v);
             if (DIR && tid == 0)
-                for (int g = 0; g < min(kStepPrefetch, nst); ++g) prefetch_stage(g);   // none at 0
+                for (int g = 0; g < min(kStepPrefetch, nst); ++g) prefetch_stage(stage_of((uint32_t)g));   // none at 0
             bool done = false, reanchor = false;
             while (!done && !reanchor) {
                 SA_STEP_STAMP(0);
@@ -524,16 +545,16 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                     return a0 + a1;
                 };
                 auto produce = [&](int g) {
-                    const int q0 = 2 * g;
-                    const bool two = q0 + 1 < nrows;
                     const uint32_t v = its + g;
+                    const int q0 = 2 * stage_of(v);
+                    const bool two = q0 + 1 < nrows;
                     const uint32_t rn = (uint32_t)ring_n;
                     if (DIR) {
                         // rows of stage g + P into L2 (the stage after the last wraps to the
                         // next sweep's first)
-                        if (tid == 0) prefetch_stage((g + kStepPrefetch) % nst);
-                    } else if (!mbar_wait(&mbar[v % rn], (v / rn) & 1u, A.err, kWaitTimeoutNs)) {
-                        s_flag = 1;
+                        if (tid == 0) prefetch_stage(stage_of(v + kStepPrefetch));
+                    } else if (!mbar_wait(&mbar[v % rn], (v / rn) & 1u, A.err, A.wait_ns)) {
+                        s_flag = 1;   // this thread's copy is not in: its warp never releases the slot
                     }
                     const float sp0 = row_partial(row_of(v, q0, 0), q0);
                     const float sp1 = two ? row_partial(row_of(v, q0, 1), q0 + 1) : 0.0f;
@@ -547,12 +568,14 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                     }
                 };
                 auto consume = [&](int g) -> bool {
-                    const int q0 = 2 * g;
-                    const bool two = q0 + 1 < nrows;
                     const uint32_t v = its + g;
+                    const int q0 = 2 * stage_of(v);
+                    const bool two = q0 + 1 < nrows;
                     const uint32_t gs = gbase + g;
-                    if (!mbar_wait(&mrow[gs % NRED], (gs / NRED) & 1u, A.err, kWaitTimeoutNs)) s_flag = 1;
-                    if (s_flag) return false;
+                    if (!mbar_wait(&mrow[gs % NRED], (gs / NRED) & 1u, A.err, A.wait_ns)) s_flag = 1;
+                    // warp-uniform: a warp either releases the stage (every lane got its copy
+                    // and every partial) or leaves the pass as a whole
+                    if (__any_sync(0xffffffffu, *(volatile int*)&s_flag != 0)) return false;
                     float ss[2];
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
@@ -644,16 +667,18 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                     const int grp = tid >> 6;
                     KahanS acc;
                     if (j < c1) {
+                        // every load of a batch is issued before the first is used: one L2
+                        // round trip per 24 partial rows (FG * 24 >= 192 rows at 512 threads)
                         const float* pj = A.part + j;
-                        for (int g0 = grp; g0 < G; g0 += FG * 16) {
-                            float a[16];
+                        for (int g0 = grp; g0 < G; g0 += FG * 24) {
+                            float a[24];
 #pragma unroll
-                            for (int x = 0; x < 16; ++x) {
+                            for (int x = 0; x < 24; ++x) {
                                 const int g = g0 + x * FG;
                                 a[x] = g < G ? __ldcg(pj + (size_t)g * A.npad) : 0.0f;
                             }
 #pragma unroll
-                            for (int x = 0; x < 16; ++x) acc.add(a[x]);
+                            for (int x = 0; x < 24; ++x) acc.add(a[x]);
                         }
                     }
                     redp[grp * 64 + (tid & 63)] = (double)acc.s - (double)acc.c;
@@ -695,6 +720,16 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 if (!gsync()) { drain(); return; }
                 SA_STEP_STAMP(3);
                 // ---------------- decision (identical in every block) ----------------
+                // the next sweep's column factors are loaded while the residual word is
+                // read (one L2 round trip for both); the old ones are dead once the partials
+                // are written, and a new epoch resets them if the step ends here
+                if (!(SP && sparse)) {
+#pragma unroll
+                    for (int kk = 0; kk < CH; ++kk)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            cf[4 * kk + e] = e < nval[kk] ? __ldcg(A.Cf + cidx[kk] * 4 + e) : 0.0f;
+                }
                 if (tid == 0) {
                     s_res = __uint_as_float(ld_acquire((const unsigned*)rmax_word));
                     int ra = 0;
@@ -718,12 +753,6 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                     if (SP && sparse) {
                         for (int j = tid; j < n; j += NT) c_s[j] = __ldcg(A.Cf + j);
                         __syncthreads();
-                    } else {
-#pragma unroll
-                        for (int kk = 0; kk < CH; ++kk)
-#pragma unroll
-                            for (int e = 0; e < 4; ++e)
-                                cf[4 * kk + e] = e < nval[kk] ? __ldcg(A.Cf + cidx[kk] * 4 + e) : 0.0f;
                     }
                 }
                 SA_STEP_STAMP(4);
@@ -820,6 +849,10 @@ sa_status launch_step(sa_ctx* ctx, const StepArgs& args, size_t smem, int* grid_
     }
     *grid_out = G;
     StepArgs a = args;
+    // stages of each stripe that stay L2-resident: the context's byte budget over the grid
+    const size_t stage_bytes = 2 * (size_t)args.row_bytes;
+    const size_t keep = ctx->step_l2_bytes / ((size_t)G * stage_bytes);
+    a.l2_keep_stages = (int)std::min<size_t>(keep, (size_t)args.n);
     void* params[] = {&a};
     SA_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(NT), params, smem, ctx->stream));
     count_launch();
@@ -941,6 +974,8 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     args.sweeps_out = sweeps_out;
     args.resid_out = resid_out;
     args.max_rows = step_max_rows(ctx, n);
+    args.wait_ns = ctx->wait_ns;
+    args.extra_arrivals = ctx->test_unreachable_barrier ? 1u : 0u;
     const size_t smem = step_smem_bytes(cfg.nt, region, args.max_rows);
     int G = ctx->max_grid > 0 ? std::min(G_max, ctx->max_grid) : G_max;
     cudaEvent_t ev0, ev1;
