@@ -141,6 +141,40 @@ typedef struct sa_ctx sa_ctx;
 sa_status sa_create(sa_ctx** ctx, int device, void* cuda_stream);
 void sa_destroy(sa_ctx* ctx);
 
+/* Options of a context (deployment settings; the paper has no counterpart).  Each applies
+ * to the calls made on the context after it is set. */
+typedef enum {
+    SA_OPT_WAIT_LIMIT_NS = 0, /* limit in ns of each grid barrier and ring wait of the STEP
+                                 kernel's evaluations of K and sweeps (default 2e9, i.e. 2 s;
+                                 >= 0; a wait checks its clock every few dozen polls, so a
+                                 wait shorter than that never runs out).  A wait that runs out makes the kernel record the
+                                 failure, wait (up to 2 s) for its own copies in flight and
+                                 return: the call returns SA_E_TIMEOUT and the context stays
+                                 usable.  The other kernels keep 2 s. */
+    SA_OPT_SOLVE_GPU = 1,     /* 1: sa_assign solves a B of at least 150000 entries with
+                                 sa_solve_reduced_gpu from the scaling's duals; 0 (default):
+                                 on the host with sa_solve_reduced_near */
+    SA_OPT_STEP_SPARSE = 2,   /* 1: the STEP kernel may sweep only the entries >= 2^-70 of
+                                 their row when K is sparse enough; 0 (default): dense */
+    SA_OPT_MAX_GRID = 3,      /* cap on the blocks of the persistent kernels (0, the
+                                 default: one or two per SM) */
+    SA_OPT_FUSED_THREADS = 4, /* threads per block of the FUSED kernel for rows of 513 to
+                                 1024 chunks of 16 bytes: 256 or 512 (default) */
+    SA_OPT_STEP_L2_BYTES = 5, /* bytes of the STEP kernel's per-step matrix K that its sweeps
+                                 read with the default L2 policy (default 48 MiB); the rest of
+                                 K is read "evict first", so that this part stays in L2 from
+                                 one sweep to the next.  A value >= the size of K reads all of
+                                 it with the default policy.  Speed only: results are equal. */
+    SA_OPT_TEST_UNREACHABLE_BARRIER = 6  /* testing hook for failure handling without a
+                                 device fault (not part of the method): 1 makes the STEP
+                                 kernel's first grid barrier wait for one arrival more than its
+                                 grid provides, so the wait runs out after SA_OPT_WAIT_LIMIT_NS
+                                 and the call returns SA_E_TIMEOUT; 0 (default) off */
+} sa_option;
+
+/* Set one option; SA_E_INVALID for an unknown option or a value out of range. */
+sa_status sa_set_option(sa_ctx* ctx, sa_option opt, int64_t value);
+
 /* Message of the calling thread's most recent failure ("" if none). */
 const char* sa_last_error(void);
 
@@ -158,8 +192,10 @@ int64_t sa_kernel_launches(void);
  *   d_u, d_v  device FP64[n], caller-owned.  Read as the warm start when
  *             opts->resume_from > 0; written with the potentials at the last p run.
  *   info      may be NULL.
- * Returns SA_OK, SA_E_NOT_CONVERGED (potentials still written), SA_E_NONFINITE, or an
- * argument/CUDA error.  Synchronises the context stream.
+ * Returns SA_OK, SA_E_NOT_CONVERGED (potentials still written), SA_E_NONFINITE,
+ * SA_E_TIMEOUT, or an argument/CUDA error.  On any error other than SA_E_NOT_CONVERGED a
+ * warm start (resume_from > 0) is left in d_u, d_v as it was given; after a cold start
+ * their contents are then unspecified.  Synchronises the context stream.
  */
 sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* opts, double* d_u,
                    double* d_v, sa_scale_info* info);
@@ -170,9 +206,9 @@ sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* opts, d
  * device memory when they scale -- callers whose memory is planned up front (a fixed
  * budget or a pre-sized pool) and callers that cannot afford the device-wide
  * synchronisation that cudaMalloc/cudaFree bring.  The fused kernel's scratch (column
- * partials, FP32 head and factor of v, schedule, barrier and status words) then lives
- * in a static device array of the library, about 2.6 MiB, which every GPU that loads the
- * library holds until the process exits.  The caller still passes the matrix, the
+ * partials, FP32 head and factor of v, schedule, barrier and status words, a copy of a
+ * warm start) then lives in a static device array of the library, about 2.7 MiB, which
+ * every GPU that loads the library holds until the process exits.  The caller still passes the matrix, the
  * potentials d_u, d_v (device FP64[n], as for sa_scale) and a CUDA stream (NULL: the
  * legacy default stream); the device is the calling thread's current device.
  *   Limits: n <= 4096, at most 64 p steps, MIXED or FP32 precision, and a layout the
@@ -184,6 +220,8 @@ sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* opts, d
  *   clears what must start at zero, but calls whose work overlaps on the GPU race on
  *   the array, so serialise them (one stream, or events).
  *   Synchronises the stream before returning; info->kernel_ms is 0 (no events are made).
+ *   A failure after the arguments were accepted leaves a warm start (resume_from > 0) in
+ *   d_u, d_v as it was given; a step the kernel did not finish reports a NaN residual.
  *   It calls no cudaMalloc, cudaFree, cudaHostAlloc or other allocating routine.
  */
 sa_status sa_scale_noalloc(const sa_matrix* a, const sa_scale_opts* opts, void* cuda_stream,
@@ -324,8 +362,8 @@ typedef struct {
 /*
  * sa_assign: scale (sa_scale), prune at t (sa_prune, guard on), solve B
  * (sa_solve_reduced_near toward the scaling's duals v/p; sa_solve_reduced_gpu from those
- * duals when the environment sets SA_SOLVE_GPU=1 at sa_create and B has at least 150000
- * entries), then certify on A (sa_certify, tau = 1e-9) and re-solve from the last duals
+ * duals when the context's SA_OPT_SOLVE_GPU is 1 and B has at least 150000 entries),
+ * then certify on A (sa_certify, tau = 1e-9) and re-solve from the last duals
  * with the violating entries added until none is left (SA_E_NOT_CONVERGED if that does
  * not settle); the result is optimal for A.  If B has no perfect matching, re-prune at
  * t/16 (finally t = 0, i.e. all of A).
@@ -419,7 +457,12 @@ typedef struct {
     double t_submit, t_start, t_done;  /* seconds on the server's monotonic clock */
 } sa_result;
 
-/* Start a server on `device` with a device-memory budget for resident requests. */
+/* Start a server on `device` with a device-memory budget for resident requests.  Each
+ * admitted request is charged an upper bound of the device memory it can hold while it
+ * runs (sa_server_request_bytes), and is admitted only while the charges of the requests
+ * on the device stay within hbm_budget.  Outside the budget the server holds only its
+ * workers' small persistent state: per small-request worker (two) a context workspace of a
+ * few MiB, and a CUDA stream per worker. */
 sa_status sa_server_create(sa_server** s, int device, size_t hbm_budget, const sa_scale_opts* opts,
                            int32_t solver_threads);
 void sa_server_destroy(sa_server* s);
@@ -437,6 +480,19 @@ void sa_result_release(sa_server* s, uint64_t ticket);
 
 /* Server clock (seconds), the one t_submit/t_start/t_done use. */
 double sa_server_now(const sa_server* s);
+
+/* Bytes of the budget an n x n request of this weight type is charged: its matrix (16-byte
+ * row pitch) plus, for n <= 512, its potentials, the reduced instance's device arrays (8
+ * bytes per kept entry, at most n^2) and 1 MiB; for larger n, everything sa_assign can
+ * allocate (the per-step matrix K of 4 n ceil(n/4)*4 bytes, the reduced instance's device
+ * arrays up to 8 n^2 bytes, column partials, vectors).  0 for bad arguments. */
+size_t sa_server_request_bytes(const sa_server* s, sa_wtype wtype, int32_t n);
+
+/* Testing hook for failure handling without a device fault (not part of the method): the
+ * next `count` device allocations made by the server's request paths fail as if the device
+ * were out of memory, without allocating; the requests concerned finish with SA_E_NOMEM.
+ * Process-wide; 0 clears it. */
+void sa_debug_fail_allocs(int32_t count);
 
 #ifdef __cplusplus
 }

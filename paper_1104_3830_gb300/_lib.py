@@ -20,6 +20,8 @@ SA_OK, SA_PENDING = 0, 1
 SA_E_INVALID, SA_E_NOMEM, SA_E_CUDA, SA_E_NOT_CONVERGED = -1, -2, -3, -4
 SA_E_NO_PERFECT_MATCHING, SA_E_NONFINITE, SA_E_BUDGET, SA_E_TIMEOUT, SA_E_UNSUPPORTED = -5, -6, -7, -8, -9
 SA_I16, SA_I32 = 0, 1
+OPTION = {"wait_limit_ns": 0, "solve_gpu": 1, "step_sparse": 2, "max_grid": 3, "fused_threads": 4, "step_l2_bytes": 5,
+          "test_unreachable_barrier": 6}
 PREC = {"mixed": 0, "fp32": 1, "fp64": 2}
 KERNEL = {"auto": 0, "fused": 1, "plain": 2, "step": 3, "newton": 4}
 STATUS_NAMES = {0: "SA_OK", 1: "SA_PENDING", -1: "SA_E_INVALID", -2: "SA_E_NOMEM", -3: "SA_E_CUDA",
@@ -96,6 +98,7 @@ _VP, _DP, _I32P, _I64P = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctype
 SIGNATURES = {
     "sa_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p]),
     "sa_destroy": (None, [_VP]),
+    "sa_set_option": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int64]),
     "sa_last_error": (ctypes.c_char_p, []),
     "sa_version": (ctypes.c_char_p, []),
     "sa_kernel_launches": (ctypes.c_int64, []),
@@ -131,6 +134,8 @@ SIGNATURES = {
     "sa_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(sa_result)]),
     "sa_result_release": (None, [_VP, ctypes.c_uint64]),
     "sa_server_now": (ctypes.c_double, [_VP]),
+    "sa_server_request_bytes": (ctypes.c_size_t, [_VP, ctypes.c_int, ctypes.c_int32]),
+    "sa_debug_fail_allocs": (None, [ctypes.c_int32]),
 }
 
 

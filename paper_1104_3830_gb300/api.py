@@ -47,6 +47,12 @@ def sa_destroy(ctx: Context) -> None:
     ctx.close()
 
 
+def sa_set_option(ctx: Context, name: str, value: int) -> None:
+    """sa_set_option by name: wait_limit_ns, solve_gpu, step_sparse, max_grid, fused_threads,
+    step_l2_bytes, test_unreachable_barrier."""
+    check(lib().sa_set_option(ctx.handle, L.OPTION[name], int(value)))
+
+
 def sa_last_error() -> str:
     return lib().sa_last_error().decode(errors="replace")
 

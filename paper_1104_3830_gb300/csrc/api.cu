@@ -47,8 +47,30 @@ sa_status Workspace::reserve(size_t bytes) {
     size = want;
     return SA_OK;
 }
+void Workspace::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    size = 0;
+}
 Workspace::~Workspace() {
     if (ptr) cudaFree(ptr);
+}
+
+size_t assign_device_bound(int num_sms, int n) {
+    const size_t nn = (size_t)n;
+    const size_t ldk = align_up(nn, 4);
+    const size_t npad = align_up(nn, 32);
+    return 4 * nn * ldk                        // K (STEP, NEWTON)
+           + 8 * nn * nn                       // prune: device column and weight arrays
+           + 2 * (size_t)num_sms * npad * 4    // column partials, two blocks per SM
+           + 512 * nn                          // per-row and per-column vectors of every stage
+           + ((size_t)4 << 20);                // schedule, flags, certificate additions
+}
+
+void release_buffers(sa_ctx* ctx) {
+    ctx->ws.release();
+    ctx->input.release();
+    ctx->keep.release();
 }
 sa_status PinnedBuf::reserve(size_t bytes) {
     if (bytes <= size) return SA_OK;
@@ -306,16 +328,45 @@ sa_status sa_create(sa_ctx** ctx, int device, void* cuda_stream) {
     if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDeviceProperties"); }
     c->num_sms = prop.multiProcessorCount;
     c->smem_optin = prop.sharedMemPerBlockOptin;
-    if (const char* wv = getenv("SA_FUSED_NT")) {
-        const int v = atoi(wv);
-        if (v == 256 || v == 512) c->fused_nt = v;
-    }
-    if (const char* e = getenv("SA_STEP_SPARSE")) c->step_sparse = atoi(e) != 0;
-    if (const char* e = getenv("SA_MAX_GRID")) c->max_grid = std::max(0, atoi(e));
-    if (const char* e = getenv("SA_SOLVE_GPU")) c->solve_gpu = atoi(e) != 0;
     if (!prop.cooperativeLaunch) { delete c; set_error("device lacks cooperative launch"); return SA_E_UNSUPPORTED; }
     *ctx = c;
     return SA_OK;
+}
+
+sa_status sa_set_option(sa_ctx* ctx, sa_option opt, int64_t value) {
+    if (!ctx) { set_error("null context"); return SA_E_INVALID; }
+    switch (opt) {
+    case SA_OPT_WAIT_LIMIT_NS:
+        if (value < 0) { set_error("wait limit must be >= 0 ns"); return SA_E_INVALID; }
+        ctx->wait_ns = (uint64_t)value;
+        return SA_OK;
+    case SA_OPT_SOLVE_GPU:
+        if (value != 0 && value != 1) { set_error("SA_OPT_SOLVE_GPU takes 0 or 1"); return SA_E_INVALID; }
+        ctx->solve_gpu = (int)value;
+        return SA_OK;
+    case SA_OPT_STEP_SPARSE:
+        if (value != 0 && value != 1) { set_error("SA_OPT_STEP_SPARSE takes 0 or 1"); return SA_E_INVALID; }
+        ctx->step_sparse = (int)value;
+        return SA_OK;
+    case SA_OPT_MAX_GRID:
+        if (value < 0 || value > (1 << 20)) { set_error("grid cap out of range"); return SA_E_INVALID; }
+        ctx->max_grid = (int)value;
+        return SA_OK;
+    case SA_OPT_STEP_L2_BYTES:
+        if (value < 0) { set_error("SA_OPT_STEP_L2_BYTES must be >= 0"); return SA_E_INVALID; }
+        ctx->step_l2_bytes = (size_t)value;
+        return SA_OK;
+    case SA_OPT_TEST_UNREACHABLE_BARRIER:
+        if (value != 0 && value != 1) { set_error("SA_OPT_TEST_UNREACHABLE_BARRIER takes 0 or 1"); return SA_E_INVALID; }
+        ctx->test_unreachable_barrier = (int)value;
+        return SA_OK;
+    case SA_OPT_FUSED_THREADS:
+        if (value != 256 && value != 512) { set_error("SA_OPT_FUSED_THREADS takes 256 or 512"); return SA_E_INVALID; }
+        ctx->fused_nt = (int)value;
+        return SA_OK;
+    }
+    set_error("unknown option %d", (int)opt);
+    return SA_E_INVALID;
 }
 
 void sa_destroy(sa_ctx* ctx) {
@@ -338,11 +389,6 @@ sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, doub
     if (!info) info = &tmp;
     memset(info, 0, sizeof(*info));
     const int n = a->n;
-    // library units: log2
-    if (o->resume_from > 0) {
-        launch_scale_vec(d_u, n, kLog2e, ctx->stream);
-        launch_scale_vec(d_v, n, kLog2e, ctx->stream);
-    }
     sa_kernel kind = o->kernel;
     if (o->prec == SA_PREC_FP64) kind = SA_KERNEL_PLAIN;
     else if (kind == SA_KERNEL_AUTO) {
@@ -361,6 +407,16 @@ sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, doub
         set_error("newton kernel needs SA_PREC_MIXED, a 16-byte aligned base and ld*sizeof(w) %% 16 == 0");
         return SA_E_UNSUPPORTED;
     }
+    // library units: log2.  A warm start is kept so that a failure leaves the caller's
+    // potentials as they were given.
+    if (o->resume_from > 0) {
+        if ((rc = ctx->keep.reserve(2 * (size_t)n * sizeof(double)))) return rc;
+        double* keep = (double*)ctx->keep.ptr;
+        SA_CUDA(cudaMemcpyAsync(keep, d_u, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        SA_CUDA(cudaMemcpyAsync(keep + n, d_v, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        launch_scale_vec(d_u, n, kLog2e, ctx->stream);
+        launch_scale_vec(d_v, n, kLog2e, ctx->stream);
+    }
     if (kind == SA_KERNEL_NEWTON) rc = scale_newton(ctx, a, o, d_u, d_v, info);
     else if (kind == SA_KERNEL_STEP) rc = scale_step(ctx, a, o, d_u, d_v, info);
     else if (kind == SA_KERNEL_FUSED) rc = scale_fused(ctx, a, o, d_u, d_v, info);
@@ -370,6 +426,11 @@ sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, doub
         launch_scale_vec(d_v, n, kLn2, ctx->stream);
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sa_scale");
+    } else if (o->resume_from > 0) {
+        const double* keep = (const double*)ctx->keep.ptr;
+        cudaMemcpyAsync(d_u, keep, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream);
+        cudaMemcpyAsync(d_v, keep + n, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
     }
     return rc;
 }

@@ -41,6 +41,7 @@ struct Workspace {
     void* ptr = nullptr;
     size_t size = 0;
     sa_status reserve(size_t bytes);
+    void release();          // give the memory back to the device
     ~Workspace();
 };
 
@@ -58,14 +59,18 @@ struct sa_ctx {
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     size_t smem_optin = 0;
-    int max_grid = 0;        // cap on the persistent kernels' grid (0: all SMs); set by the
-                             // server, or SA_MAX_GRID in the environment
+    // options (sa_set_option)
+    int max_grid = 0;        // cap on the persistent kernels' grid (0: all SMs)
     int fused_nt = 512;      // threads per block of the fused kernel when 512 < chunks <= 1024
-                             // (256 or 512; SA_FUSED_NT in the environment overrides)
-    int step_sparse = 0;     // step kernel: allow sparse epochs (SA_STEP_SPARSE=1 enables)
-    int solve_gpu = 0;       // sa_assign: reduced solve through the GPU auction (SA_SOLVE_GPU=1)
+    int step_sparse = 0;     // step kernel: allow sparse epochs
+    int solve_gpu = 0;       // sa_assign: large reduced instances through the GPU path
+    uint64_t wait_ns = sa::kWaitTimeoutNs;   // step kernel: limit of its barrier and ring waits
+    size_t step_l2_bytes = (size_t)48 << 20;  // step kernel: bytes of K read with the default L2
+                                              // policy (the rest "evict first")
+    int test_unreachable_barrier = 0;         // testing hook (SA_OPT_TEST_UNREACHABLE_BARRIER)
     sa::Workspace ws;        // scratch for sweeps, prune, certify
     sa::Workspace input;     // device copy of host inputs (sa_assign_host)
+    sa::Workspace keep;      // sa_scale: the caller's warm-start potentials, restored on failure
     sa::PinnedBuf pinned;    // staging for small device->host results
 };
 
@@ -172,5 +177,15 @@ sa_status auction_device(sa_ctx* ctx, int n, const int64_t* d_rp, const int32_t*
 
 // csr helpers (api.cu)
 sa_status csr_alloc(sa_csr* c, int n, int64_t nnz);
+
+// Upper bound of the device memory sa_assign allocates for an n x n matrix besides the
+// matrix itself, on a device of num_sms SMs: the largest scaling workspace (the per-step
+// matrix K, 4 n ceil(n/4)*4 bytes, of the STEP and NEWTON kernels; column partials of up
+// to two blocks per SM), the prune's device CSR arrays (8 bytes per kept entry, at most
+// n^2 when the re-prune reaches t = 0), the potentials and the certificate's buffers.
+size_t assign_device_bound(int num_sms, int n);
+// Give a context's device buffers (workspace, input copy, warm-start copy) back to the
+// device; they are allocated again by the next call that needs them.
+void release_buffers(sa_ctx* ctx);
 
 }  // namespace sa

@@ -1,9 +1,11 @@
 // server.cpp -- continuous-batching server for assignment requests (sa_submit/sa_poll).
 //
 // Requests of mixed size arrive at any time.  A request is admitted when the device
-// memory it needs (its int16/int32 matrix plus potentials) fits in the budget next to
-// the requests already resident, so new work joins while earlier work is still on the
-// GPU.  Worker threads, each with its own CUDA stream and library context, run admitted
+// memory it can need (its int16/int32 matrix, potentials, the scaling workspace and the
+// reduced instance's device arrays, bounded from above) fits in the budget next to the
+// requests already resident, so new work joins while earlier work is still on the GPU.
+// A large request's worker gives its context's buffers back to the device when the
+// request finishes, with its share of the budget.  Worker threads, each with its own CUDA stream and library context, run admitted
 // requests concurrently on the device:
 //  - small requests (n <= 512) are drained from the queue in groups and scaled together
 //    by one sa_batch_scale launch, then pruned, solved and certified one by one;
@@ -11,6 +13,7 @@
 //    solve, duality repair) on a worker of their own.
 // Every kernel launch is finite; results are kept until sa_result_release.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -58,6 +61,7 @@ struct sa_server {
     uint64_t next_ticket = 1;
     std::chrono::steady_clock::time_point t0;
     int large_grid = 0;
+    int num_sms = 0;
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -66,10 +70,33 @@ struct sa_server {
 
 namespace {
 
-size_t request_bytes(int n, sa_wtype wt) {
+// Test hook (sa_debug_fail_allocs): this many of the next device allocations of the
+// request paths fail as if the device were out of memory, without allocating.
+std::atomic<int> g_fail_allocs{0};
+
+cudaError_t srv_alloc(void** p, size_t bytes, cudaStream_t st) {
+    int k = g_fail_allocs.load();
+    while (k > 0) {
+        if (g_fail_allocs.compare_exchange_weak(k, k - 1)) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
+
+// Device bytes a request can hold while it runs (an upper bound).  Small requests: the
+// matrix, the potentials, the reduced instance's device arrays (8 bytes per kept entry,
+// at most n^2) and the batch launch's tables.  Large ones: the matrix and everything
+// sa_assign allocates (sa::assign_device_bound).  What is not counted is each worker
+// context's small persistent state: the small workers' workspaces (a few MiB for
+// n <= 512) and the CUDA streams.
+size_t request_bytes(int n, sa_wtype wt, int num_sms) {
     const size_t sz = wt == SA_I16 ? 2 : 4;
     const size_t ld = sa::align_up((size_t)n * sz, 16) / sz;
-    return ld * n * sz + 2 * sizeof(double) * n + (1 << 20);   // matrix, potentials, workspace share
+    const size_t matrix = ld * n * sz;
+    if (n <= kSmallMax) return matrix + 2 * sizeof(double) * n + 8 * (size_t)n * n + 64 + (1 << 20);
+    return matrix + sa::assign_device_bound(num_sms, n);
 }
 
 // Take requests from the head of the queue while they fit the budget.  small_only picks
@@ -106,7 +133,7 @@ void finish(sa_server* s, Request* r, sa_status st) {
 sa_status upload(Request* r, cudaStream_t st, void** d_w, int64_t* ld) {
     const size_t sz = r->wtype == SA_I16 ? 2 : 4;
     *ld = (int64_t)(sa::align_up((size_t)r->n * sz, 16) / sz);
-    SA_CUDA(cudaMallocAsync(d_w, (size_t)(*ld) * r->n * sz, st));
+    SA_CUDA(srv_alloc(d_w, (size_t)(*ld) * r->n * sz, st));
     SA_CUDA(cudaMemcpy2DAsync(*d_w, (size_t)(*ld) * sz, r->host.data(), (size_t)r->n * sz, (size_t)r->n * sz, r->n,
                               cudaMemcpyHostToDevice, st));
     return SA_OK;
@@ -219,20 +246,26 @@ void small_worker(sa_server* s) {
             offs[q] = tot;
             tot += group[q]->n;
         }
-        void** d_ptrs = nullptr;
-        int32_t* d_n = nullptr;
-        int64_t *d_ld = nullptr, *d_off = nullptr;
+        // d_uv (k * 16 n bytes in all) is within the group's charge: 16 n of each request
+        // the group's tables (pointers, sizes, pitches, offsets) in one buffer, then the
+        // potentials; every allocation and copy is checked, and a failure fails the group
+        const size_t tab = sa::align_up(8 * (size_t)k, 256);
+        unsigned char* d_tab = nullptr;
         double* d_uv = nullptr;
         if (rc == SA_OK) {
-            cudaMallocAsync((void**)&d_ptrs, 8 * k, st);
-            cudaMallocAsync((void**)&d_n, 4 * k, st);
-            cudaMallocAsync((void**)&d_ld, 8 * k, st);
-            cudaMallocAsync((void**)&d_off, 8 * k, st);
-            cudaMallocAsync((void**)&d_uv, 16 * tot, st);
-            cudaMemcpyAsync(d_ptrs, dw.data(), 8 * k, cudaMemcpyHostToDevice, st);
-            cudaMemcpyAsync(d_n, ns.data(), 4 * k, cudaMemcpyHostToDevice, st);
-            cudaMemcpyAsync(d_ld, lds.data(), 8 * k, cudaMemcpyHostToDevice, st);
-            cudaMemcpyAsync(d_off, offs.data(), 8 * k, cudaMemcpyHostToDevice, st);
+            cudaError_t e = srv_alloc((void**)&d_tab, 4 * tab, st);
+            if (e == cudaSuccess) e = srv_alloc((void**)&d_uv, 16 * (size_t)tot, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab, dw.data(), 8 * k, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab + tab, ns.data(), 4 * k, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab + 2 * tab, lds.data(), 8 * k, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab + 3 * tab, offs.data(), 8 * k, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) rc = sa::cuda_fail(e, "server: group tables");
+        }
+        if (rc == SA_OK) {
+            void** d_ptrs = (void**)d_tab;
+            int32_t* d_n = (int32_t*)(d_tab + tab);
+            int64_t* d_ld = (int64_t*)(d_tab + 2 * tab);
+            int64_t* d_off = (int64_t*)(d_tab + 3 * tab);
             std::vector<int32_t> sw(k), stt(k);
             rc = sa_batch_scale(ctx, k, (const void* const*)d_ptrs, d_n, d_ld, d_off, group[0]->wtype, &s->opts, d_uv,
                                 d_uv + tot, sw.data(), stt.data());
@@ -246,19 +279,19 @@ void small_worker(sa_server* s) {
                     rq = finish_small(ctx, r, &a, d_uv + offs[q], d_uv + tot + offs[q], p);
                 }
                 cudaFreeAsync(dw[q], st);
+                cudaStreamSynchronize(st);
                 finish(s, r, rq);
             }
-            cudaFreeAsync(d_ptrs, st);
-            cudaFreeAsync(d_n, st);
-            cudaFreeAsync(d_ld, st);
-            cudaFreeAsync(d_off, st);
+            cudaFreeAsync(d_tab, st);
             cudaFreeAsync(d_uv, st);
             cudaStreamSynchronize(st);
         } else {
-            for (int q = 0; q < k; ++q) {
+            if (d_tab) cudaFreeAsync(d_tab, st);
+            if (d_uv) cudaFreeAsync(d_uv, st);
+            for (int q = 0; q < k; ++q)
                 if (dw[q]) cudaFreeAsync(dw[q], st);
-                finish(s, group[q], rc);
-            }
+            cudaStreamSynchronize(st);
+            for (int q = 0; q < k; ++q) finish(s, group[q], rc);
         }
     }
     if (ctx) sa_destroy(ctx);
@@ -303,9 +336,11 @@ void large_worker(sa_server* s) {
             r->sum_log_w = res.sum_log_w;
             r->gamma = res.gamma;
             r->sweeps = res.scale.sweeps_total;
-            cudaFreeAsync(dw, st);
-            cudaStreamSynchronize(st);
         }
+        if (dw) cudaFreeAsync(dw, st);
+        cudaStreamSynchronize(st);
+        // the request's share of the budget covered the context's buffers: give them back
+        sa::release_buffers(ctx);
         finish(s, r, rc);
     }
     if (ctx) sa_destroy(ctx);
@@ -337,7 +372,12 @@ sa_status sa_server_create(sa_server** out, int device, size_t hbm_budget, const
     s->t0 = std::chrono::steady_clock::now();
     const int large = std::max(1, solver_threads > 0 ? solver_threads : 2);
     cudaDeviceProp prop;
-    cudaGetDeviceProperties(&prop, device);
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete s;
+        sa::set_error("cudaGetDeviceProperties failed for device %d", device);
+        return SA_E_CUDA;
+    }
+    s->num_sms = prop.multiProcessorCount;
     s->large_grid = std::max(8, prop.multiProcessorCount / large);
     for (int q = 0; q < 2; ++q) s->workers.emplace_back(small_worker, s);
     for (int q = 0; q < large; ++q) s->workers.emplace_back(large_worker, s);
@@ -364,7 +404,7 @@ sa_status sa_submit(sa_server* s, const void* host_w, sa_wtype wtype, int32_t n,
     auto r = std::make_unique<Request>();
     r->n = n;
     r->wtype = wtype;
-    r->dev_bytes = request_bytes(n, wtype);
+    r->dev_bytes = request_bytes(n, wtype, s->num_sms);
     if (r->dev_bytes > s->budget) {
         sa::set_error("request of n=%d needs %zu bytes, over the %zu byte budget", n, r->dev_bytes, s->budget);
         return SA_E_BUDGET;
@@ -409,5 +449,12 @@ void sa_result_release(sa_server* s, uint64_t ticket) {
 }
 
 double sa_server_now(const sa_server* s) { return s ? s->now() : 0.0; }
+
+size_t sa_server_request_bytes(const sa_server* s, sa_wtype wtype, int32_t n) {
+    if (!s || n <= 0 || (wtype != SA_I16 && wtype != SA_I32)) return 0;
+    return request_bytes(n, wtype, s->num_sms);
+}
+
+void sa_debug_fail_allocs(int32_t count) { g_fail_allocs.store(count > 0 ? count : 0); }
 
 }  // extern "C"

@@ -813,10 +813,11 @@ void launch_split_v(const double* V, float* Vh, float* Vc, int n, cudaStream_t s
 // Allocation-free variant of the fused scaling (sa_scale_noalloc).
 //
 // Some callers cannot allocate device memory at the point where they need a scaling:
-// code running while a CUDA graph is being captured, or inside a host callback, or
-// under an allocator that must not grow, or with a memory budget that is fixed up front.
-// For them the scratch of the fused kernel (column partials, the FP32 head/factor of V,
-// the schedule, barrier and status words) lives in this file-scope device array instead
+// their device memory is planned up front (a fixed budget, a pre-sized pool, an
+// allocator that must not grow), or they cannot take the device-wide synchronisation
+// that cudaMalloc and cudaFree bring.  For them the scratch of the fused kernel (column
+// partials, the FP32 head/factor of V, the schedule, barrier and status words, and a copy
+// of the caller's warm-start potentials) lives in this file-scope device array instead
 // of a context workspace.  Every device that loads the library holds the array until
 // the process exits.  All calls share it: two calls whose work overlaps on the GPU race
 // on it and must be serialised by the caller (one stream, or events).
@@ -830,7 +831,7 @@ constexpr int kNoAllocMaxSteps = 64;    // longest p schedule accepted
 constexpr size_t kNoAllocPartFloats = (size_t)kNoAllocMaxGrid * kNoAllocMaxN;
 constexpr size_t kNoAllocBytes =
     kNoAllocPartFloats * 4 + 2 * (size_t)kNoAllocMaxN * 4 + 2 * (size_t)kNoAllocMaxSteps * 8 +
-    (size_t)kNoAllocMaxSteps * 4 + 256 * 4;   // about 2.6 MiB
+    (size_t)kNoAllocMaxSteps * 4 + 256 * 4 + 2 * (size_t)kNoAllocMaxN * 8;   // about 2.7 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -922,13 +923,28 @@ extern "C" sa_status sa_scale_noalloc(const sa_matrix* a, const sa_scale_opts* o
     int* err = (int*)(words + 2);
     int* fallback = (int*)(words + 3);
     float* rmax = (float*)(words + 4);
+    double* keep_u = (double*)(words + 256);   // the caller's warm start, restored on failure
+    double* keep_v = keep_u + kNoAllocMaxN;
     if ((size_t)npad * kNoAllocMaxGrid > kNoAllocPartFloats) { set_error("scratch too small"); return SA_E_UNSUPPORTED; }
-    // the previous call's contents stay in the array: clear what must start at zero
+    const int k0 = o->resume_from;
+    // a failure after this point puts the caller's potentials back as they were given
+    auto restore = [&](sa_status rc) -> sa_status {
+        if (k0 > 0) {
+            cudaMemcpyAsync(d_u, keep_u, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(d_v, keep_v, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            cudaStreamSynchronize(st);
+        }
+        return rc;
+    };
+    // the previous call's contents stay in the array: clear what must start at zero, and
+    // mark every step's residual unknown (NaN) until the kernel writes it
     SA_CUDA(cudaMemcpyAsync(P, o->p, o->n_p * sizeof(double), cudaMemcpyHostToDevice, st));
     SA_CUDA(cudaMemsetAsync(words, 0, 8 * sizeof(unsigned), st));
     SA_CUDA(cudaMemsetAsync(sweeps_out, 0, o->n_p * sizeof(int), st));
-    const int k0 = o->resume_from;
+    SA_CUDA(cudaMemsetAsync(resid_out, 0xFF, o->n_p * sizeof(double), st));
     if (k0 > 0) {
+        SA_CUDA(cudaMemcpyAsync(keep_u, d_u, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        SA_CUDA(cudaMemcpyAsync(keep_v, d_v, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         launch_scale_vec(d_u, n, kLog2e, st);
         launch_scale_vec(d_v, n, kLog2e, st);
         if (!o->warm_keep_v) launch_scale_vec(d_v, n, o->p[k0] / o->p[k0 - 1], st);
@@ -979,7 +995,7 @@ extern "C" sa_status sa_scale_noalloc(const sa_matrix* a, const sa_scale_opts* o
                                      : launch_fused<int32_t, 512, 2, 5, kRowsPerSync>(&ctx, args, smem, &G);
     else rc = i16 ? launch_fused<int16_t, 512, 2, 4, kRowsPerSync>(&ctx, args, smem, &G)
                   : launch_fused<int32_t, 512, 2, 4, kRowsPerSync>(&ctx, args, smem, &G);
-    if (rc) return rc;
+    if (rc) return restore(rc);
     // results through pageable host memory (no pinned allocation)
     int h_words[4] = {0, 0, 0, 0};
     int h_sw[kNoAllocMaxSteps];
@@ -991,7 +1007,8 @@ extern "C" sa_status sa_scale_noalloc(const sa_matrix* a, const sa_scale_opts* o
     launch_scale_vec(d_v, n, kLn2, st);
     SA_CUDA(cudaStreamSynchronize(st));
     int64_t total = 0;
-    int conv = 1;
+    // a step the kernel did not finish keeps its NaN residual, so it never counts as converged
+    int conv = h_words[2] == 0;
     for (int k = k0; k < o->n_p; ++k) {
         total += h_sw[k];
         if (!(h_rs[k] <= o->tol)) conv = 0;
@@ -1007,8 +1024,8 @@ extern "C" sa_status sa_scale_noalloc(const sa_matrix* a, const sa_scale_opts* o
         info->kernel_used = SA_KERNEL_FUSED;
         info->kernel_ms = 0.0;
     }
-    if (h_words[2] == kErrTimeout) { set_error("sa_scale_noalloc: a bounded device wait timed out"); return SA_E_TIMEOUT; }
-    if (h_words[2] == kErrNonfinite) { set_error("sa_scale_noalloc: a row or column lost all mass"); return SA_E_NONFINITE; }
+    if (h_words[2] == kErrTimeout) { set_error("sa_scale_noalloc: a bounded device wait timed out"); return restore(SA_E_TIMEOUT); }
+    if (h_words[2] == kErrNonfinite) { set_error("sa_scale_noalloc: a row or column lost all mass"); return restore(SA_E_NONFINITE); }
     return conv ? SA_OK : SA_E_NOT_CONVERGED;
 }
 

@@ -63,6 +63,7 @@ def test_host_only_entry_points_without_gpu(libsa):
     h = ctypes.c_void_p()
     st = lib.sa_create(ctypes.byref(h), 0, None)
     assert st != 0
+    assert lib.sa_set_option(None, L.OPTION["wait_limit_ns"], 1000) == -1
 
 
 def test_host_solver_argument_errors(libsa):

@@ -106,17 +106,18 @@ def test_no_perfect_matching(ctx):
     assert e.value.status == -5
 
 
-def test_assign_through_gpu_auction_matches(ctx, monkeypatch):
-    """sa_assign with SA_SOLVE_GPU=1 returns the same certified optimum (at p = 1 about half
-    of the entries pass t = 1/n, so B is above the auction's 150000-entry threshold)."""
+def test_assign_through_gpu_auction_matches(ctx):
+    """sa_assign with the context option SA_OPT_SOLVE_GPU = 1 returns the same certified
+    optimum (at p = 1 about half of the entries pass t = 1/n, so B is above the GPU path's
+    150000-entry threshold)."""
     n = 1000
     w = W.uniform(n, 1, 1000, 1702, dtype=np.int16)
     d = api.to_device(w)
     ps = [1.0]
     r1 = api.sa_assign(ctx, d, ps, 1e-6, 20000)
-    monkeypatch.setenv("SA_SOLVE_GPU", "1")
     c2 = api.sa_create(0)
     try:
+        api.sa_set_option(c2, "solve_gpu", 1)
         r2 = api.sa_assign(c2, d, ps, 1e-6, 20000)
     finally:
         c2.close()

@@ -81,15 +81,90 @@ def test_mixed_stream_is_exact_and_matches_alone(lib):
 
 
 def test_budget_is_enforced(lib):
-    h, o = make_server(lib, 64 << 20, [1.0, 2.0])
+    h, o = make_server(lib, 256 << 20, [1.0, 2.0])
     try:
-        big = W.uniform(8192, 1, 1000, 5, dtype=np.int16)   # 128 MiB > 64 MiB budget
+        # n = 8192 is charged about 14 n^2 bytes (matrix, K, reduced arrays): over 256 MiB
+        assert lib.sa_server_request_bytes(h, L.SA_I16, 8192) > 256 << 20
+        big = W.uniform(8192, 1, 1000, 5, dtype=np.int16)
         st, _ = submit(lib, h, big)
         assert st == L.SA_E_BUDGET
-        ok = W.uniform(2000, 1, 1000, 6, dtype=np.int16)    # 8 MiB each: admitted a few at a time
+        # n = 2000: about 61 MiB each, admitted a few at a time
+        charge = lib.sa_server_request_bytes(h, L.SA_I16, 2000)
+        assert 2000 * 2000 * 2 < charge < 256 << 20
+        ok = W.uniform(2000, 1, 1000, 6, dtype=np.int16)
         ts = [submit(lib, h, ok)[1] for _ in range(12)]
         for t in ts:
             st, perm, r = wait(lib, h, t)
             assert st == 0 and sorted(perm) == list(range(2000))
+    finally:
+        lib.sa_server_destroy(h)
+
+
+SERVER_CONSTANT = 64 << 20   # the workers' persistent state the budget does not cover
+
+
+def test_device_use_stays_within_budget(lib):
+    """A mixed stream under a budget that admits only a few large requests at a time: the
+    device memory in use (cudaMemGetInfo, sampled every millisecond from another thread)
+    never exceeds the idle server's by more than the budget plus SERVER_CONSTANT."""
+    import threading
+    ps = [2.0 ** k for k in range(5)]
+    budget = 512 << 20
+    sizes = [3000, 40, 2500, 100, 3000, 300, 2800, 64, 512, 2600, 900, 33, 3000, 2200]
+    mats = [W.uniform(n, 1, 1000, 3100 + n, dtype=np.int16) for n in sizes]
+    h, o = make_server(lib, budget, ps)
+    try:
+        # warm-up pass: modules loaded, workers' small workspaces at their size
+        ts = [submit(lib, h, m)[1] for m in mats]
+        for t in ts:
+            assert wait(lib, h, t)[0] == 0
+            lib.sa_result_release(h, t)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        low = [free0]
+        stop = threading.Event()
+
+        def sample():
+            while not stop.is_set():
+                low[0] = min(low[0], torch.cuda.mem_get_info()[0])
+                time.sleep(0.001)
+        th = threading.Thread(target=sample)
+        th.start()
+        try:
+            ts = [submit(lib, h, m)[1] for m in mats]
+            res = [wait(lib, h, t) for t in ts]
+        finally:
+            stop.set()
+            th.join()
+        for m, (st, perm, r) in zip(mats, res):
+            assert st == 0 and sorted(perm) == list(range(m.shape[0]))
+        used = free0 - low[0]
+        assert used <= budget + SERVER_CONSTANT, (used >> 20, budget >> 20)
+    finally:
+        lib.sa_server_destroy(h)
+
+
+def test_allocation_failure_fails_each_request(lib):
+    """A device allocation that fails (injected on the host: the server's allocation call
+    reports out-of-memory without allocating) finishes the request with SA_E_NOMEM, for a
+    small request (batched path) and a large one (sa_assign path); later requests run."""
+    h, o = make_server(lib, 1 << 30, [1.0, 2.0, 4.0])
+    try:
+        small = W.uniform(100, 1, 1000, 3201, dtype=np.int16)
+        large = W.uniform(1000, 1, 1000, 3202, dtype=np.int16)
+        for m in (small, large):
+            lib.sa_debug_fail_allocs(1)
+            try:
+                st, t = submit(lib, h, m)
+                assert st == 0
+                st, perm, r = wait(lib, h, t)
+            finally:
+                lib.sa_debug_fail_allocs(0)
+            assert st == L.SA_E_NOMEM and r.status == L.SA_E_NOMEM, (st, r.status)
+            st, t = submit(lib, h, m)
+            st, perm, r = wait(lib, h, t)
+            assert st == 0
+            b = oracle.log_weights(m.astype(np.int64))
+            assert oracle.perm_weight_exact(m, perm) == oracle.perm_weight_exact(m, oracle.hungarian(b)[0])
     finally:
         lib.sa_server_destroy(h)
