@@ -2,16 +2,23 @@
 """Benchmark of the Sinkhorn preprocessing hot path on GB300.
 
 One step = one pass of the whole path over one instance: log-domain Sinkhorn over the
-p schedule (fused single-read kernel), prune + CSR compaction, exact solve of the
-reduced instance and the LP-duality certificate on A (sa_assign).  The default workload
-is the planted n = 8192 instance (int16 weights, 128 MiB, p = 1, 2, ..., 512, tol 1e-6).
+p schedule (the step kernel: one evaluation of the per-step FP32 matrix K per p, then one
+read of K per sweep), prune + CSR compaction, exact solve of the reduced instance and the
+LP-duality certificate on A (sa_assign).  The default workload is the planted n = 8192
+instance (int16 weights, 128 MiB, p = 1, 2, ..., 512, tol 1e-6).
 
 Prints one JSON line.  value = Sinkhorn sweeps per second over the whole step (all
-ranks), roofline = the fused sweep kernel against the measured HBM copy bandwidth,
-e2e = the same metric through sa_assign_host with the matrix in pinned host memory.
+ranks), roofline = the step kernel against the measured HBM copy bandwidth, e2e = the
+same metric through sa_assign_host with the matrix in pinned host memory.  At one GPU the
+line also carries the metric's two other parts, each timed in the same run with its own
+clock record: "batched" (the 4096-instance batched form, instances/s of one persistent
+launch against the plain one-instance-per-launch path, and a sample of exact optimal
+weights against the oracle) and "serve" (the first requests of the Poisson stream through
+the continuous-batching server against a plain FIFO path: p50/p99 latency, instances/s).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload planted8192|tied8192|uniform256|uniform20000|small]
+                  [--workload planted8192|tied8192|uniform256|uniform20000|batch4096|serve|
+                              precision20000|reduced|euclidean1000|small]
 
 Under torchrun every rank runs its own replica on its own GPU (the instances are
 independent: no collective on the data path); value sums the ranks' sweeps over the
@@ -283,19 +290,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
-    """Batched form: 4096 independent instances, n log-uniform in [16, 512], int32 weights
-    in [1, 1000], p = 1, 2, ..., 128, scaled in one persistent launch (sa_batch_scale);
-    compared with the plain one-instance-per-launch path on a sample."""
+def certified_weight(ctx, d, p, u, v, max_repairs=64):
+    """The exact optimum of one scaled instance from its potentials, as sa_assign finds it:
+    prune (t = 1/n, row and column maxima kept), solve B toward v/p, certify on all of A
+    and re-solve with the violating entries added.  Returns (perm, certified)."""
+    from paper_1104_3830_gb300 import api
+    n = d.size(0)
+    rp, col, wv, _ = api.sa_prune(ctx, d, p, u, v)
+    vv = v.cpu().numpy() / p
+    perm, _, al, be = api.sa_solve_reduced(rp, col, wv, near=vv)
+    for _ in range(max_repairs):
+        nv, (arp, acol, aw) = api.sa_certify(ctx, d, al, be)
+        if nv == 0:
+            return perm, True
+        rows = np.concatenate([np.repeat(np.arange(n), np.diff(rp)), np.repeat(np.arange(n), np.diff(arp))])
+        cols = np.concatenate([col, acol])
+        ws = np.concatenate([wv, aw])
+        key = rows.astype(np.int64) * n + cols
+        key, first = np.unique(key, return_index=True)
+        rows, cols, ws = key // n, (key % n).astype(np.int32), ws[first]
+        rp = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=n))]).astype(np.int64)
+        col, wv = cols, ws.astype(np.int32)
+        perm, _, al, be = api.sa_solve_reduced(rp, col, wv, beta0=be)
+    return perm, False
+
+
+def batched_part(args):
+    """Batched form: 4096 independent dense instances, n log-uniform in [16, 512], int32
+    weights in [1, 1000], p = 1, 2, ..., 128, scaled by sa_batch_scale under the
+    autotuner's launch plan (one persistent launch per size bucket).  Beside it: the plain one-instance-per-launch path (plain and fused
+    kernels) on a sample, and, for another sample, the certified optimum reached from the
+    batch's potentials against the oracle's Hungarian optimum (exact integer products)."""
     import ctypes
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
+    import oracle
     from paper_1104_3830_gb300 import _lib as L
     from paper_1104_3830_gb300 import api
     from paper_1104_3830_gb300 import workloads as W
-    count = args.batch_count
-    mats, ps = W.c4(count=count)
+    mats, ps = W.c4(count=args.batch_count)
     k = len(mats)
     ns = np.array([m.shape[0] for m in mats], dtype=np.int32)
     lds = ((ns + 3) // 4 * 4).astype(np.int64)   # 16-byte pitch for int32
@@ -309,7 +341,8 @@ def run_batch(args):
     ptrs = torch.tensor([base + 4 * int(o_) for o_ in offs_w], dtype=torch.int64, device="cuda")
     dn = torch.from_numpy(ns).cuda()
     dld = torch.from_numpy(lds).cuda()
-    offs = torch.from_numpy(np.concatenate([[0], np.cumsum(ns)[:-1]]).astype(np.int64)).cuda()
+    offs_np = np.concatenate([[0], np.cumsum(ns)[:-1]]).astype(np.int64)
+    offs = torch.from_numpy(offs_np).cuda()
     tot = int(ns.sum())
     u = torch.zeros(tot, dtype=torch.float64, device="cuda")
     v = torch.zeros(tot, dtype=torch.float64, device="cuda")
@@ -318,18 +351,23 @@ def run_batch(args):
     o = L.make_opts(ps, 1e-6, args.max_sweeps)
     stream = torch.cuda.current_stream()
     ctx = api.sa_create(0, stream.cuda_stream)
+    # the launch plan of the size buckets: the autotuner's cached choice for this GPU and
+    # weight type, or a fresh tuning run (outside the timed region)
+    from paper_1104_3830_gb300 import autotune
+    plan, choice, plan_src = autotune.load_or_tune(ctx, np.int32)
+    api.sa_set_batch_plan(ctx, plan)
 
     def once():
         return L.lib().sa_batch_scale(ctx.handle, k, ctypes.c_void_p(ptrs.data_ptr()), ctypes.c_void_p(dn.data_ptr()),
                                       ctypes.c_void_p(dld.data_ptr()), ctypes.c_void_p(offs.data_ptr()), L.SA_I32,
                                       ctypes.byref(o), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()),
                                       sw.ctypes.data_as(L._I32P), st.ctypes.data_as(L._I32P))
-    for _ in range(args.warmup):
+    for _ in range(max(1, args.batch_warmup)):
         once()
     times = []
     launches0 = L.lib().sa_kernel_launches()
     with ClockSampler(0) as clk:
-        for _ in range(args.steps):
+        for _ in range(args.batch_steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -337,12 +375,12 @@ def run_batch(args):
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
-    launches = (L.lib().sa_kernel_launches() - launches0) // args.steps
+    launches = (L.lib().sa_kernel_launches() - launches0) // args.batch_steps
     ms = statistics.mean(times)
     value = k / (ms / 1e3)
     sweeps = int(sw.sum())
-    elems = float(sum(int(n) * int(n) * int(s) for n, s in zip(ns, sw)))
-    # plain path: one instance per launch sequence (fused or plain kernels), on a sample
+    elems = float(sum(int(n) * int(n) * int(s_) for n, s_ in zip(ns, sw)))
+    # plain path: one instance per launch sequence (plain or fused kernels), on a sample
     rng = np.random.default_rng(0)
     sample = rng.choice(k, size=min(args.plain_sample, k), replace=False)
     plain = {}
@@ -354,27 +392,60 @@ def run_batch(args):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         plain[kern] = len(sample) / dt
+    # exact optimal weights of a sample, from the batch's potentials, against the oracle
+    chk = rng.choice(k, size=min(args.check_sample, k), replace=False)
+    equal = certified = 0
+    for q in chk:
+        n = int(ns[q])
+        d = api.to_device(mats[q])
+        uq = u[int(offs_np[q]):int(offs_np[q]) + n].clone()
+        vq = v[int(offs_np[q]):int(offs_np[q]) + n].clone()
+        perm, cert = certified_weight(ctx, d, ps[-1], uq, vq)
+        b = oracle.log_weights(mats[q].astype(np.int64))
+        ref = oracle.hungarian(b)[0]
+        certified += int(cert)
+        equal += int(oracle.perm_weight_exact(mats[q], perm) == oracle.perm_weight_exact(mats[q], ref))
     # SFU roofline: one ex2 per element per sweep (log2 tables in shared memory)
     ex2_peak = 30.0 * 152 * 2.07e9 / 1e12   # measured ex2/clk/SM x SMs x max clock (Tex2/s)
     achieved = elems / (ms / 1e3) / 1e12
-    line = {"metric": METRIC, "value": value, "unit": "instances/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (exp/sum), f64 potentials", "data": "synthetic",
-            "config": {"workload": f"{k} instances, n log-uniform [16,512], int32 w in [1,1000], p=1..128 (x2), tol 1e-6",
-                       "status_counts": {str(s_): int((st == s_).sum()) for s_ in np.unique(st)},
-                       "sweeps_total": sweeps, "impl": "sa_batch_scale (one persistent launch)",
-                       "l2": "instances re-read from L2/smem (working set < L2)"},
+    ctx.close()
+    return {"value": value, "unit": "instances/s", "ms_per_launch": ms, "launches_timed": len(times),
+            "workload": f"{k} instances, n log-uniform [16,512], int32 w in [1,1000], p=1..128 (x2), tol 1e-6",
+            "impl": "sa_batch_scale (one persistent launch per size bucket, buckets side by side)",
+            "plan": {"buckets": [list(x) for x in plan], "source": plan_src},
+            "status_counts": {str(s_): int((st == s_).sum()) for s_ in np.unique(st)},
+            "sweeps_total": sweeps, "l2": "instances re-read from L2/smem (working set < L2)",
             "plain_one_instance_per_launch": {"instances_per_s_plain_kernels": plain["plain"],
                                               "instances_per_s_fused_kernel": plain["fused"],
                                               "sample": len(sample)},
+            "exact_check": {"sample": len(chk), "optimum_equal_to_oracle": equal, "certified": certified,
+                            "how": "prune + exact solve + LP certificate from the batch's potentials, "
+                                   "exact integer product against the oracle's Hungarian optimum"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": ex2_peak, "unit": "Tex2/s",
                          "frac": achieved / ex2_peak, "traffic": None,
                          "peak_source": "own micro-benchmark: 30 ex2/clk/SM x 152 SMs x 2.07 GHz"},
             "gpu_launches": int(launches), "clocks": clk.summary()}
+
+
+def run_batch(args):
+    """The batched form on its own line (value = instances/s of the persistent launch)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    part = batched_part(args)
+    line = {"metric": METRIC, "value": part["value"], "unit": "instances/s", "n_gpus": 1,
+            "steps": args.batch_steps, "warmup": args.batch_warmup, "ms_per_step": part["ms_per_launch"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (exp/sum), f64 potentials", "data": "synthetic",
+            "config": {"workload": part["workload"], "status_counts": part["status_counts"],
+                       "sweeps_total": part["sweeps_total"], "impl": part["impl"], "l2": part["l2"]},
+            "plain_one_instance_per_launch": part["plain_one_instance_per_launch"],
+            "exact_check": part["exact_check"], "roofline": part["roofline"],
+            "gpu_launches": part["gpu_launches"], "clocks": part["clocks"]}
     if not args.no_cpu_baseline:
+        from paper_1104_3830_gb300 import workloads as W
+        mats, ps = W.c4(count=args.batch_count)
         line["cpu_baseline"] = oracle_instances_baseline(mats, ps)
     print(json.dumps(line), flush=True)
-    ctx.close()
 
 
 def run_precision(args):
@@ -452,21 +523,18 @@ def run_precision(args):
     ctx.close()
 
 
-def run_serve(args):
-    """Serving form: Poisson request stream of dense instances, n log-uniform in
-    [32, 4096], through the continuous-batching server (sa_submit/sa_poll) and through a
-    plain FIFO one-at-a-time path; p50/p99 latency and instances/s."""
+def serve_part(args):
+    """Serving form: the first requests of a Poisson stream of dense instances (n log-uniform
+    in [32, 4096]) through the continuous-batching server (sa_submit/sa_poll), and the same
+    requests at the same arrival times through a plain FIFO one-at-a-time path (sa_assign_host
+    on the plain kernels); p50/p99 latency and instances/s of both."""
     import ctypes
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1104_3830_gb300 import _lib as L
     from paper_1104_3830_gb300 import api
     from paper_1104_3830_gb300 import workloads as W
     seed = W.BASE_SEED + 4
     pool_n = W.loguniform_sizes(args.serve_pool, 32, 4096, seed)
     pool = [W.c5_request(seed, q, int(n), args.serve_dist) for q, n in enumerate(pool_n)]
-    # the first serve_requests arrivals of the Poisson stream, served by both systems
     arrivals = W.poisson_arrivals(args.serve_rate, args.serve_seconds, seed)[: args.serve_requests]
     ps = [2.0 ** q for q in range(9)]
     o = L.make_opts(ps, 1e-6, args.max_sweeps)
@@ -484,7 +552,7 @@ def run_serve(args):
             t = ctypes.c_uint64()
             L.check(lib.sa_submit(h, ctypes.c_void_p(m.ctypes.data), L.SA_I16, m.shape[0], ctypes.byref(t)))
             tickets.append(t.value)
-        lat, done_t, first = [], [], None
+        lat, done_t, first, bad = [], [], None, 0
         r = L.sa_result()
         for t in tickets:
             while True:
@@ -492,6 +560,7 @@ def run_serve(args):
                 if stt != L.SA_PENDING:
                     break
                 time.sleep(0.0005)
+            bad += int(stt != 0)
             lat.append(r.t_done - r.t_submit)
             done_t.append(r.t_done)
             first = r.t_submit if first is None else min(first, r.t_submit)
@@ -500,37 +569,45 @@ def run_serve(args):
         lat = np.array(lat)
         span = max(done_t) - first
         return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "instances_per_s": len(lat) / span, "requests": len(lat)}
+                "instances_per_s": len(lat) / span, "requests": len(lat), "failed": bad}
 
-    ours = serve_run(arrivals)
-    # plain FIFO: one request at a time on the plain kernels, the same arrivals
-    ctx = api.sa_create(0)
-    arr_f = arrivals
-    lat = []
-    t0 = time.perf_counter()
-    free_at = 0.0
-    for q, ta in enumerate(arr_f):
-        now = time.perf_counter() - t0
-        if now < ta:
-            time.sleep(ta - now)
-        m = pool[q % len(pool)]
-        api.sa_assign_host(ctx, m, ps, 1e-6, args.max_sweeps, kernel="plain")
-        lat.append(time.perf_counter() - t0 - ta)
-    span = time.perf_counter() - t0 - arr_f[0]
+    with ClockSampler(0) as clk:
+        ours = serve_run(arrivals)
+        # plain FIFO: one request at a time on the plain kernels, the same arrivals
+        ctx = api.sa_create(0)
+        lat = []
+        t0 = time.perf_counter()
+        for q, ta in enumerate(arrivals):
+            now = time.perf_counter() - t0
+            if now < ta:
+                time.sleep(ta - now)
+            m = pool[q % len(pool)]
+            api.sa_assign_host(ctx, m, ps, 1e-6, args.max_sweeps, kernel="plain")
+            lat.append(time.perf_counter() - t0 - ta)
+        span = time.perf_counter() - t0 - arrivals[0]
+        ctx.close()
     lat = np.array(lat)
     fifo = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "instances_per_s": len(lat) / span, "requests": len(lat)}
-    ctx.close()
-    line = {"metric": METRIC, "value": ours["instances_per_s"], "unit": "instances/s", "n_gpus": 1,
+    return {"value": ours["instances_per_s"], "unit": "instances/s",
+            "workload": f"first {len(arrivals)} requests of a Poisson {args.serve_rate:g}/s stream, "
+                        f"n log-uniform [32,4096], {args.serve_dist} weights, 40 GB budget, p=1..256 (x2); "
+                        "the same requests and arrival times for both systems",
+            "offered_per_s": args.serve_rate, "pool": len(pool), "serve": ours, "plain_fifo": fifo,
+            "clocks": clk.summary()}
+
+
+def run_serve(args):
+    """The serving form on its own line (value = the server's instances/s)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    part = serve_part(args)
+    line = {"metric": METRIC, "value": part["value"], "unit": "instances/s", "n_gpus": 1,
             "steps": 1, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (exp/sum), f64 potentials", "data": "synthetic",
-            "config": {"workload": f"first {len(arrivals)} requests of a Poisson {args.serve_rate}/s stream, "
-                                   f"n log-uniform [32,4096], {args.serve_dist} weights, 40 GB budget, p=1..256 (x2); "
-                                   "the same requests and arrival times for both systems",
-                       "offered_per_s": args.serve_rate, "pool": len(pool)},
-            "serve": ours, "plain_fifo": fifo}
+            "config": {"workload": part["workload"], "offered_per_s": part["offered_per_s"], "pool": part["pool"]},
+            "serve": part["serve"], "plain_fifo": part["plain_fifo"], "clocks": part["clocks"]}
     print(json.dumps(line), flush=True)
-
 
 
 def run_reduced(args):
@@ -648,12 +725,18 @@ def main():
                     help="sweep implementation of sa_scale (auto: the library's choice)")
     ap.add_argument("--max-sweeps", type=int, default=20000)
     ap.add_argument("--batch-count", type=int, default=4096)
-    ap.add_argument("--plain-sample", type=int, default=128)
+    ap.add_argument("--plain-sample", type=int, default=64)
+    ap.add_argument("--check-sample", type=int, default=32,
+                    help="batched form: instances whose certified optimum is compared with the oracle's")
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--batch-warmup", type=int, default=1)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the batched and serving parts of the line")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-pool", type=int, default=96)
     ap.add_argument("--serve-dist", default="uniform", choices=["uniform", "zipf"])
-    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-requests", type=int, default=150)
     ap.add_argument("--no-newton", action="store_true",
                     help="skip the Newton-path time-to-solution measurement beside the main line")
     args = ap.parse_args()
@@ -794,8 +877,17 @@ def main():
             line["newton_variant"] = newton
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, ps)
-        print(json.dumps(line), flush=True)
     ctx.close()
+    if rank == 0:
+        # the metric's other two parts, at one GPU (the replicas of a multi-GPU run time
+        # only the headline workload)
+        if world == 1 and args.workload == "planted8192" and not args.no_extras:
+            del d, flush
+            torch.cuda.empty_cache()
+            line["batched"] = batched_part(args)
+            torch.cuda.empty_cache()
+            line["serve"] = serve_part(args)
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
