@@ -165,7 +165,7 @@ typedef enum {
                                  K is read "evict first", so that this part stays in L2 from
                                  one sweep to the next.  A value >= the size of K reads all of
                                  it with the default policy.  Speed only: results are equal. */
-    SA_OPT_TEST_UNREACHABLE_BARRIER = 6  /* testing hook for failure handling without a
+    SA_OPT_TEST_UNREACHABLE_BARRIER = 6 /* testing hook for failure handling without a
                                  device fault (not part of the method): 1 makes the STEP
                                  kernel's first grid barrier wait for one arrival more than its
                                  grid provides, so the wait runs out after SA_OPT_WAIT_LIMIT_NS
@@ -429,13 +429,44 @@ sa_status sa_narrow_i32_to_i16(sa_ctx* ctx, const int32_t* d_src, int64_t ld_src
 
 /* ---- Batched scaling of many independent small instances (one launch) -------------- */
 
+/* How sa_batch_scale runs an instance (a deployment choice; the paper has no counterpart).
+ * BLOCK: one thread block of 256 threads per instance; every sweep forms each term with an
+ *   SFU exp2 of an FP32 exponent (the log2 table of the instance in shared memory when it
+ *   fits), so the error of the sums grows like 1.3e-7 p.
+ * GROUP: a group of 1, 2 or 4 warps per instance (n <= 128), with the per-step matrix K of
+ *   the STEP path in a shared-memory slot of the group (exponent in float-pair arithmetic
+ *   once per p step); the sweeps multiply and add only, the group's warps meet at a named
+ *   barrier of their own, and the error does not grow with p. */
+typedef enum { SA_BATCH_BLOCK = 0, SA_BATCH_GROUP = 1 } sa_batch_path;
+
+/* A launch plan: instances are grouped by n into buckets (n_hi[b-1], n_hi[b]] (n_hi
+ * increasing, the last >= 512), and each bucket runs on its path in a persistent launch of
+ * its own; the launches of the buckets run side by side on the device.  The project's
+ * autotuner (paper_1104_3830_gb300/autotune.py) picks a plan per GPU and weight type by
+ * timing the candidates, and caches it. */
+#define SA_BATCH_MAX_BUCKETS 8
+typedef struct {
+    int32_t count;                          /* buckets in use, 1 .. SA_BATCH_MAX_BUCKETS */
+    int32_t n_hi[SA_BATCH_MAX_BUCKETS];     /* largest n of each bucket */
+    int32_t path[SA_BATCH_MAX_BUCKETS];     /* sa_batch_path; GROUP only for n_hi <= 128 */
+    int32_t warps[SA_BATCH_MAX_BUCKETS];    /* GROUP: warps per instance, 1, 2 or 4 */
+    int32_t per_block[SA_BATCH_MAX_BUCKETS];/* GROUP: groups per block; warps * per_block <= 8 */
+} sa_batch_plan;
+
+/* Set the context's plan (copied); NULL restores the default: n <= 32 one warp per
+ * instance and n <= 64 two, four groups per block; n <= 128 four warps, one group per block;
+ * the rest on the block path.  SA_E_INVALID for a plan that breaks the rules above. */
+sa_status sa_set_batch_plan(sa_ctx* ctx, const sa_batch_plan* plan);
+
 /*
- * sa_batch_scale: scale k independent instances in one persistent launch.  Instance i
- * is the device matrix d_w[i] (n[i] x ld[i] int16 or int32 per wtype, all the same
- * type); its potentials go to d_u + off[i], d_v + off[i] (device FP64).  The schedule,
- * tol and cap are shared.  Instances with n <= 512 run one per thread block; larger
- * ones return SA_E_UNSUPPORTED.  Per-instance sweeps and status go to the host arrays
- * sweeps[k] and status[k] (may be NULL).
+ * sa_batch_scale: scale k independent instances, each bucket of the context's plan in one
+ * persistent launch (Sec. 4.1.2 iteration and Sec. 4.2 stop rule per instance, p schedule
+ * and warm start as sa_scale).  Instance i is the device matrix d_w[i] (n[i] x ld[i] int16
+ * or int32 per wtype, all the same type); its potentials go to d_u + off[i], d_v + off[i]
+ * (device FP64, natural units).  The schedule, tol and cap are shared.  Instances with
+ * n <= 512 are supported; larger ones return SA_E_UNSUPPORTED.  Per-instance sweeps and
+ * status (0 converged, 1 a step hit the cap, -6 a row or column lost all mass) go to the
+ * host arrays sweeps[k] and status[k] (may be NULL).
  *   d_w, d_n, d_ld, d_off  device arrays of length k (pointers, int32, int64, int64)
  */
 sa_status sa_batch_scale(sa_ctx* ctx, int32_t k, const void* const* d_w, const int32_t* d_n,

@@ -22,6 +22,7 @@ SA_E_NO_PERFECT_MATCHING, SA_E_NONFINITE, SA_E_BUDGET, SA_E_TIMEOUT, SA_E_UNSUPP
 SA_I16, SA_I32 = 0, 1
 OPTION = {"wait_limit_ns": 0, "solve_gpu": 1, "step_sparse": 2, "max_grid": 3, "fused_threads": 4, "step_l2_bytes": 5,
           "test_unreachable_barrier": 6}
+SA_BATCH_BLOCK, SA_BATCH_GROUP = 0, 1
 PREC = {"mixed": 0, "fp32": 1, "fp64": 2}
 KERNEL = {"auto": 0, "fused": 1, "plain": 2, "step": 3, "newton": 4}
 STATUS_NAMES = {0: "SA_OK", 1: "SA_PENDING", -1: "SA_E_INVALID", -2: "SA_E_NOMEM", -3: "SA_E_CUDA",
@@ -50,6 +51,11 @@ class sa_scale_info(ctypes.Structure):
                 ("converged", ctypes.c_int32), ("steps_done", ctypes.c_int32), ("fallback_rows", ctypes.c_int32),
                 ("kernel_used", ctypes.c_int32), ("kernel_ms", ctypes.c_double),
                 ("sparse_epochs", ctypes.c_int32), ("reanchors", ctypes.c_int32)]
+
+
+class sa_batch_plan(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("n_hi", ctypes.c_int32 * 8), ("path", ctypes.c_int32 * 8),
+                ("warps", ctypes.c_int32 * 8), ("per_block", ctypes.c_int32 * 8)]
 
 
 class sa_csr(ctypes.Structure):
@@ -99,6 +105,7 @@ SIGNATURES = {
     "sa_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p]),
     "sa_destroy": (None, [_VP]),
     "sa_set_option": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int64]),
+    "sa_set_batch_plan": (ctypes.c_int, [_VP, ctypes.c_void_p]),
     "sa_last_error": (ctypes.c_char_p, []),
     "sa_version": (ctypes.c_char_p, []),
     "sa_kernel_launches": (ctypes.c_int64, []),

@@ -47,6 +47,23 @@ def sa_destroy(ctx: Context) -> None:
     ctx.close()
 
 
+def sa_set_batch_plan(ctx: Context, buckets=None) -> None:
+    """sa_set_batch_plan from a list of (n_hi, path, warps, per_block) with path "group" or
+    "block" (warps and per_block: the group path's warps per instance and groups per block);
+    None restores the library's default plan."""
+    if buckets is None:
+        check(lib().sa_set_batch_plan(ctx.handle, None))
+        return
+    plan = L.sa_batch_plan()
+    plan.count = len(buckets)
+    for b, (n_hi, path, warps, per_block) in enumerate(buckets):
+        plan.n_hi[b] = int(n_hi)
+        plan.path[b] = L.SA_BATCH_GROUP if path == "group" else L.SA_BATCH_BLOCK
+        plan.warps[b] = int(warps)
+        plan.per_block[b] = int(per_block)
+    check(lib().sa_set_batch_plan(ctx.handle, ctypes.byref(plan)))
+
+
 def sa_set_option(ctx: Context, name: str, value: int) -> None:
     """sa_set_option by name: wait_limit_ns, solve_gpu, step_sparse, max_grid, fused_threads,
     step_l2_bytes, test_unreachable_barrier."""

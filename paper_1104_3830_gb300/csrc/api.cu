@@ -369,11 +369,44 @@ sa_status sa_set_option(sa_ctx* ctx, sa_option opt, int64_t value) {
     return SA_E_INVALID;
 }
 
+sa_status sa_set_batch_plan(sa_ctx* ctx, const sa_batch_plan* plan) {
+    if (!ctx) { set_error("null context"); return SA_E_INVALID; }
+    if (!plan) {
+        ctx->batch_plan = default_batch_plan();
+        return SA_OK;
+    }
+    if (plan->count < 1 || plan->count > SA_BATCH_MAX_BUCKETS) { set_error("plan needs 1 .. 8 buckets"); return SA_E_INVALID; }
+    for (int b = 0; b < plan->count; ++b) {
+        if (plan->n_hi[b] < 1 || (b > 0 && plan->n_hi[b] <= plan->n_hi[b - 1])) {
+            set_error("plan bucket %d: n_hi must be positive and increasing", b);
+            return SA_E_INVALID;
+        }
+        if (plan->path[b] == SA_BATCH_GROUP) {
+            const int w = plan->warps[b], g = plan->per_block[b];
+            if (plan->n_hi[b] > 128 || (w != 1 && w != 2 && w != 4) || g < 1 || w * g > 8) {
+                set_error("plan bucket %d: the group path takes n_hi <= 128, 1, 2 or 4 warps per instance and "
+                          "at most 8 warps per block", b);
+                return SA_E_INVALID;
+            }
+        } else if (plan->path[b] != SA_BATCH_BLOCK) {
+            set_error("plan bucket %d: unknown path %d", b, plan->path[b]);
+            return SA_E_INVALID;
+        }
+    }
+    if (plan->n_hi[plan->count - 1] < 512) { set_error("the last bucket must reach n = 512"); return SA_E_INVALID; }
+    ctx->batch_plan = *plan;
+    return SA_OK;
+}
+
 void sa_destroy(sa_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
+    for (cudaStream_t& s : ctx->batch_streams)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t& e : ctx->batch_events)
+        if (e) cudaEventDestroy(e);
     delete ctx;
 }
 

@@ -17,10 +17,12 @@
 // block-wide reductions, which the other block's instance hides.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <numeric>
 #include <vector>
 
 #include "common.cuh"
+#include "log2pair.cuh"
 #include "sa_internal.h"
 
 namespace sa {
@@ -254,10 +256,363 @@ __global__ void __launch_bounds__(NT, 2) batch_kernel(BatchArgs A) {
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Group path: a group of G warps (G = 1, 2, 4) scales one small instance (n <= NMAX <= 128)
+// on its own, with no block barrier in its sweeps.  The instances of these sizes run the
+// most sweeps of a batch (on uniform weights at p = 128 most n <= 32 instances end at the
+// sweep cap), so the latency of one sweep, not arithmetic, sets their time; a few warps
+// each and many groups per SM keep that latency small and hidden.
+//
+// Per p step the group evaluates the step matrix of the per-step path once,
+//     K_ij = 2^(p log2 w_ij - C_i - V_j)       (C_i ~ max_j (p log2 w_ij - V_j)),
+// with the same float-pair exponent (log2 w to about 2^-40, exact two-products and
+// two-sums, one SFU exp2), into its shared-memory slot; the sweeps then only multiply
+// and add (Sec. 4.1.2 iteration on the diagonally equivalent K, error independent of p):
+//     s_i = sum_j K_ij c_j,   S_j = c_j sum_i K_ij / s_i,   c_j <- c_j / S_j,
+// residual max_j |S_j - 1| (Sec. 4.2), and at the end of the step U_i = C_i + log2 s_i,
+// V_j <- V_j - log2 c_j in FP64.  Thread t of the group owns rows and columns t, t + 32G,
+// ...; the row pass reads K by rows (slot rows padded to an odd stride: conflict-free), the
+// column pass by columns, the vectors c and 1/s are broadcast from the slot, and the loops
+// run over NMAX (compile time, fully unrolled) so that each pass issues its loads at once.
+// Sums use four independent FP32 accumulators of at most NMAX/4 terms each.  The group's
+// warps meet at a named barrier (one per group of the block) twice a sweep; a group of one
+// warp only synchronises the warp.
+// ---------------------------------------------------------------------------------------
+constexpr int kGroupMaxN = 128;
+
+// floats of one group's slot for instances with n <= nmax: K (n4 x (n4 + 1)), then c, 1/s,
+// C (nmax each), V as float pairs (2 nmax) and the warps' residuals (8)
+__host__ __device__ inline unsigned group_slot_floats(int nmax) {
+    const unsigned n4 = (unsigned)((nmax + 3) & ~3);
+    return ((n4 * (n4 + 1) + 3u) & ~3u) + 5u * n4 + 8u;
+}
+
+template <int G>
+__device__ __forceinline__ void group_sync(int group) {
+    if (G == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(32 * G) : "memory");
+    }
+}
+
+template <typename WT, int G, int NMAX>
+__global__ void __launch_bounds__(256) batch_group_kernel(BatchArgs A) {
+    constexpr int NT = 32 * G;                  // threads of a group
+    constexpr int RPT = (NMAX + NT - 1) / NT;   // rows (and columns) per thread
+    constexpr int N4 = (NMAX + 3) & ~3;
+    constexpr int CPL = (N4 + 31) / 32;         // columns per lane in the evaluation of K
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float4 s_l2tab[256];
+    const int tid = threadIdx.x;
+    for (int j = tid; j < 256; j += blockDim.x) s_l2tab[j] = log2_tab_entry(j);
+    __syncthreads();   // the only block barrier: the groups are independent from here on
+    const int group = tid / NT, tg = tid % NT, lane = tid & 31, wig = tg >> 5;
+    float* K = (float*)smem + (size_t)group * group_slot_floats(NMAX);
+    float* cs = K + ((N4 * (N4 + 1) + 3) & ~3);
+    float* rs = cs + N4;
+    float* Cs = rs + N4;
+    float2* vp = (float2*)(Cs + N4);
+    float* wres = (float*)(vp + N4);
+    __shared__ int s_q[8];
+    for (;;) {
+        if (tg == 0) s_q[group] = (int)atomicAdd(A.queue, 1u);
+        group_sync<G>(group);
+        const int q = s_q[group];
+        group_sync<G>(group);   // s_q is rewritten by the next instance
+        if (q >= A.k) break;
+        const int inst = A.order[q];
+        const int n = A.n[inst];
+        const int n4 = (n + 3) & ~3;
+        const int stride = n4 + 1;   // odd: the threads' rows fall in distinct banks
+        const WT* wb = (const WT*)A.w[inst];
+        const int64_t ld = A.ld[inst];
+        double V[RPT];               // log2 units, columns tg + r NT
+        float c[RPT], sr[RPT];       // column factors; last row sums of rows tg + r NT
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            V[r] = 0.0;
+            c[r] = 0.0f;
+            sr[r] = 1.0f;
+        }
+        int sweeps_all = 0;
+        bool bad = false, capped = false;
+        for (int k = 0; k < A.n_p && !bad; ++k) {
+            const double p = A.P[k];
+            if (k > 0) {
+                const double f = p / A.P[k - 1];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) V[r] *= f;
+            }
+            // ---- one evaluation of K for this p ----
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const int j = tg + r * NT;
+                if (j < N4) {
+                    const float h = (float)V[r];
+                    vp[j] = make_float2(h, (float)(V[r] - (double)h));
+                }
+            }
+            group_sync<G>(group);
+            const float ph = (float)p;
+            const float pl = (float)(p - (double)ph);
+            int badk = 0;
+            for (int i = wig; i < n; i += G) {   // a row per warp, lanes over its columns
+                const WT* wr = wb + (int64_t)i * ld;
+                int wv[CPL];
+                float m = -INFINITY;
+#pragma unroll
+                for (int h = 0; h < CPL; ++h) {
+                    const int j = lane + 32 * h;
+                    wv[h] = j < n ? (int)wr[j] : 0;
+                    // reference C ~ max_j (p log2 w - V_j), an FP32 estimate (only a scale:
+                    // C enters the row potential exactly)
+                    if (wv[h] > 0) m = fmaxf(m, fmaf(ph, lg2_approx((float)wv[h]), -vp[j].x));
+                }
+                m = warp_max(m);
+                if (!(m > -INFINITY)) { badk = 1; m = 0.0f; }
+                if (lane == 0) Cs[i] = m;
+                float* kr = K + (size_t)i * stride;
+#pragma unroll
+                for (int h = 0; h < CPL; ++h) {
+                    const int j = lane + 32 * h;
+                    float x = 0.0f;
+                    if (wv[h] > 0) {
+                        // p log2 w - V_j - m with 48-bit operands: the large parts cancel
+                        // exactly (two-product, two-sums), the small ones are added after
+                        const float2 lw = wlog2(s_l2tab, wv[h]);
+                        const float2 vj = vp[j];
+                        const float t = ph * lw.x;
+                        const float te = fmaf(ph, lw.x, -t);
+                        float e1, e2;
+                        const float u1 = two_sum(t, -vj.x, &e1);
+                        const float u2 = two_sum(u1, -m, &e2);
+                        const float rest = ((te + e1) + e2) + (fmaf(ph, lw.y, pl * lw.x) - vj.y);
+                        x = ex2_approx(u2 + rest);
+                    }
+                    if (j < n4) kr[j] = x;
+                }
+            }
+            for (int i = n + wig; i < n4; i += G)   // zero rows up to the multiple of four
+#pragma unroll
+                for (int h = 0; h < CPL; ++h)
+                    if (lane + 32 * h < n4) K[(size_t)i * stride + lane + 32 * h] = 0.0f;
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const int j = tg + r * NT;
+                c[r] = j < n ? 1.0f : 0.0f;
+                if (j < N4) {
+                    cs[j] = c[r];
+                    rs[j] = 0.0f;
+                }
+            }
+            if (lane == 0) wres[wig] = (float)badk;
+            group_sync<G>(group);
+#pragma unroll
+            for (int x = 0; x < G; ++x) bad = bad || wres[x] != 0.0f;
+            float Cr[RPT];
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const int i = tg + r * NT;
+                Cr[r] = i < n ? Cs[i] : 0.0f;
+            }
+            group_sync<G>(group);   // wres is rewritten by the sweeps
+            // ---- sweeps ----
+            int sweeps = 0;
+            bool done = bad;
+            while (!done) {
+                // row pass: s_i = sum_j K_ij c_j for the thread's rows
+                int badr = 0;
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const int i = tg + r * NT;
+                    if (i < n) {
+                        const float* kr = K + (size_t)i * stride;
+                        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < N4; j += 4) {
+                            if (j < n4) {
+                                const float4 c4 = *(const float4*)(cs + j);
+                                a0 = fmaf(kr[j], c4.x, a0);
+                                a1 = fmaf(kr[j + 1], c4.y, a1);
+                                a2 = fmaf(kr[j + 2], c4.z, a2);
+                                a3 = fmaf(kr[j + 3], c4.w, a3);
+                            }
+                        }
+                        const float sv = (a0 + a1) + (a2 + a3);
+                        if (!(sv >= 0x1p-120f && sv <= 0x1p120f)) badr = 1;
+                        sr[r] = sv;
+                        rs[i] = rcp_approx(sv);
+                    }
+                }
+                group_sync<G>(group);
+                // column pass: S_j = c_j sum_i K_ij / s_i for the thread's columns
+                float resid = 0.0f;
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const int j = tg + r * NT;
+                    if (j < n) {
+                        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll
+                        for (int i = 0; i < N4; i += 4) {
+                            if (i < n4) {
+                                const float4 r4 = *(const float4*)(rs + i);
+                                const float* kc = K + (size_t)i * stride + j;
+                                a0 = fmaf(kc[0], r4.x, a0);
+                                a1 = fmaf(kc[stride], r4.y, a1);
+                                a2 = fmaf(kc[2 * stride], r4.z, a2);
+                                a3 = fmaf(kc[3 * stride], r4.w, a3);
+                            }
+                        }
+                        const float S = c[r] * ((a0 + a1) + (a2 + a3));
+                        if (!(S > 0.0f) || !(S < INFINITY)) badr = 1;
+                        resid = fmaxf(resid, fabsf(S - 1.0f));
+                        c[r] = c[r] / S;
+                        cs[j] = c[r];
+                    }
+                }
+                // the group's residual (and failure flag, as a NaN) from every warp
+                resid = warp_max(badr ? INFINITY : resid);
+                if (G > 1 && lane == 0) wres[wig] = resid;
+                group_sync<G>(group);
+                if (G > 1) {
+                    resid = 0.0f;
+#pragma unroll
+                    for (int x = 0; x < G; ++x) resid = fmaxf(resid, wres[x]);
+                }
+                ++sweeps;
+                bad = !(resid < INFINITY);
+                done = bad || (resid <= (float)A.tol) || (sweeps >= A.max_sweeps);
+                if (done && !bad && !(resid <= (float)A.tol)) capped = true;
+                if (G > 1) group_sync<G>(group);   // wres is rewritten by the next sweep
+            }
+            sweeps_all += sweeps;
+            if (bad) break;
+            // potentials reached at this p: V_j <- V_j - log2 c_j; U from C and s at the end
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const int j = tg + r * NT;
+                if (j < n) V[r] -= log2((double)c[r]);
+            }
+            if (k + 1 == A.n_p) {
+                double* Uo = A.U + A.off[inst];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const int i = tg + r * NT;
+                    if (i < n) Uo[i] = ((double)Cr[r] + log2((double)sr[r])) * kLn2;
+                }
+            }
+        }
+        double* Vo = A.V + A.off[inst];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int j = tg + r * NT;
+            if (j < n) Vo[j] = V[r] * kLn2;
+        }
+        if (tg == 0) {
+            A.sweeps[inst] = sweeps_all;
+            A.status[inst] = bad ? -6 : (capped ? 1 : 0);
+        }
+        group_sync<G>(group);   // the slot is rewritten by the next instance
+    }
+}
+
 }  // namespace
 }  // namespace sa
 
 using namespace sa;
+
+namespace {
+// group path: `per_block` groups of G warps per block, one slot of K each, as many blocks as
+// fit on each SM, at most one group per instance
+template <typename WT, int G, int NMAX>
+sa_status launch_group(sa_ctx* ctx, cudaStream_t bs, const BatchArgs& args, int per_block) {
+    auto kern = batch_group_kernel<WT, G, NMAX>;
+    const size_t smem = (size_t)per_block * group_slot_floats(NMAX) * sizeof(float);
+    cudaFuncAttributes fa;
+    SA_CUDA(cudaFuncGetAttributes(&fa, kern));
+    if (smem + fa.sharedSizeBytes > ctx->smem_optin) {
+        set_error("batch group path: %d slots for n <= %d need %zu bytes of shared memory (%zu available)", per_block,
+                  NMAX, smem + fa.sharedSizeBytes, ctx->smem_optin);
+        return SA_E_UNSUPPORTED;
+    }
+    SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * G * per_block, smem));
+    if (per_sm < 1) {
+        set_error("batch group path: %d groups of %d warps (%zu bytes) do not fit on an SM", per_block, G, smem);
+        return SA_E_UNSUPPORTED;
+    }
+    const int blocks = std::max(1, std::min((args.k + per_block - 1) / per_block, ctx->num_sms * per_sm));
+    kern<<<blocks, 32 * G * per_block, smem, bs>>>(args);
+    count_launch();
+    SA_CUDA(cudaGetLastError());
+    return SA_OK;
+}
+
+template <typename WT, int G>
+sa_status launch_group_n(sa_ctx* ctx, cudaStream_t bs, const BatchArgs& args, int nmax, int per_block) {
+    if (nmax <= 32) return launch_group<WT, G, 32>(ctx, bs, args, per_block);
+    if (nmax <= 64) return launch_group<WT, G, 64>(ctx, bs, args, per_block);
+    return launch_group<WT, G, 128>(ctx, bs, args, per_block);
+}
+
+sa_status launch_group_path(sa_ctx* ctx, cudaStream_t bs, const BatchArgs& args, int nmax, int warps, int per_block,
+                            sa_wtype wtype) {
+    if (wtype == SA_I16) {
+        if (warps == 1) return launch_group_n<int16_t, 1>(ctx, bs, args, nmax, per_block);
+        if (warps == 2) return launch_group_n<int16_t, 2>(ctx, bs, args, nmax, per_block);
+        return launch_group_n<int16_t, 4>(ctx, bs, args, nmax, per_block);
+    }
+    if (warps == 1) return launch_group_n<int32_t, 1>(ctx, bs, args, nmax, per_block);
+    if (warps == 2) return launch_group_n<int32_t, 2>(ctx, bs, args, nmax, per_block);
+    return launch_group_n<int32_t, 4>(ctx, bs, args, nmax, per_block);
+}
+
+// block path: one block of 256 threads per instance, two blocks per SM
+sa_status launch_block_path(sa_ctx* ctx, cudaStream_t bs, BatchArgs args, int maxn, sa_wtype wtype) {
+    const int vec = 16 / wbytes(wtype);
+    const int kc = ((maxn + vec - 1) / vec + 31) / 32;   // chunks per lane
+    constexpr int NT = 256;
+    constexpr int NW = NT / 32;
+    const size_t fixed = kBatchMaxN * 8 + 4 * kBatchMaxN * 4 + (size_t)NW * kBatchMaxN * 4 + NW * 8 + 64;
+    size_t smem = std::min<size_t>(ctx->smem_optin, 110 * 1024);   // two blocks per SM
+    args.smem_table = smem > fixed ? smem - fixed : 0;
+    auto go = [&](auto kern) -> sa_status {
+        SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+        const int grid = std::max(1, std::min(args.k, ctx->num_sms * std::max(per_sm, 1)));
+        kern<<<grid, NT, smem, bs>>>(args);
+        count_launch();
+        SA_CUDA(cudaGetLastError());
+        return SA_OK;
+    };
+    if (wtype == SA_I16) return kc <= 1 ? go(batch_kernel<int16_t, NT, 1>) : go(batch_kernel<int16_t, NT, 2>);
+    if (kc <= 1) return go(batch_kernel<int32_t, NT, 1>);
+    if (kc <= 2) return go(batch_kernel<int32_t, NT, 2>);
+    return go(batch_kernel<int32_t, NT, 4>);
+}
+
+// per-instance sweeps and statuses to the host; the call's status from the worst instance
+sa_status finish_batch(cudaStream_t st, int k, const int32_t* d_sw, const int32_t* d_st, int32_t* sweeps,
+                       int32_t* status) {
+    std::vector<int32_t> hsw(k), hst(k);
+    SA_CUDA(cudaMemcpyAsync(hsw.data(), d_sw, 4 * k, cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaMemcpyAsync(hst.data(), d_st, 4 * k, cudaMemcpyDeviceToHost, st));
+    SA_CUDA(cudaStreamSynchronize(st));
+    if (sweeps) memcpy(sweeps, hsw.data(), 4 * k);
+    if (status) memcpy(status, hst.data(), 4 * k);
+    int worst = 0;
+    for (int q = 0; q < k; ++q) {
+        if (hst[q] < 0) worst = -6;
+        else if (hst[q] > 0 && worst == 0) worst = 1;
+    }
+    if (worst < 0) { set_error("a batch instance lost all mass in a row or column"); return SA_E_NONFINITE; }
+    if (worst > 0) { set_error("a batch instance hit max_sweeps_per_p"); return SA_E_NOT_CONVERGED; }
+    return SA_OK;
+}
+}  // namespace
 
 extern "C" sa_status sa_batch_scale(sa_ctx* ctx, int32_t k, const void* const* d_w, const int32_t* d_n,
                                     const int64_t* d_ld, const int64_t* d_off, sa_wtype wtype,
@@ -294,12 +649,27 @@ extern "C" sa_status sa_batch_scale(sa_ctx* ctx, int32_t k, const void* const* d
             return SA_E_INVALID;
         }
     }
-    std::vector<int32_t> order(k);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hn[a] > hn[b]; });
-    const int maxn = hn[order[0]];
-    const int vec = 16 / sz;
-    const int kc = ((maxn + vec - 1) / vec + 31) / 32;   // chunks per lane
+    // instances by bucket of the plan: group buckets smallest first (the smallest run the
+    // most sweeps), block buckets largest first
+    const sa_batch_plan& plan = ctx->batch_plan;
+    std::vector<std::vector<int32_t>> members(plan.count);
+    for (int q = 0; q < k; ++q) {
+        int b = 0;
+        while (b + 1 < plan.count && hn[q] > plan.n_hi[b]) ++b;
+        members[b].push_back(q);
+    }
+    std::vector<int32_t> order;
+    std::vector<int> first(plan.count), cnt(plan.count);
+    for (int b = 0; b < plan.count; ++b) {
+        auto& m = members[b];
+        if (plan.path[b] == SA_BATCH_GROUP)
+            std::stable_sort(m.begin(), m.end(), [&](int a, int c) { return hn[a] < hn[c]; });
+        else
+            std::stable_sort(m.begin(), m.end(), [&](int a, int c) { return hn[a] > hn[c]; });
+        first[b] = (int)order.size();
+        cnt[b] = (int)m.size();
+        order.insert(order.end(), m.begin(), m.end());
+    }
     size_t need = align_up((size_t)k * 4, 256) * 3 + align_up((size_t)o->n_p * 8, 256) + 1024;
     sa_status rc = ctx->ws.reserve(need);
     if (rc) return rc;
@@ -308,49 +678,35 @@ extern "C" sa_status sa_batch_scale(sa_ctx* ctx, int32_t k, const void* const* d
     int32_t* d_sw = cv.take<int32_t>(k);
     int32_t* d_st = cv.take<int32_t>(k);
     double* d_P = cv.take<double>(o->n_p);
-    unsigned* d_q = cv.take<unsigned>(1);
+    unsigned* d_q = cv.take<unsigned>(SA_BATCH_MAX_BUCKETS);
     SA_CUDA(cudaMemcpyAsync(d_order, order.data(), 4 * k, cudaMemcpyHostToDevice, st));
     SA_CUDA(cudaMemcpyAsync(d_P, o->p, 8 * o->n_p, cudaMemcpyHostToDevice, st));
-    SA_CUDA(cudaMemsetAsync(d_q, 0, 4, st));
-    BatchArgs args{d_w, d_n, d_ld, d_off, d_order, k, wtype == SA_I16, d_P, o->n_p, o->tol, o->max_sweeps_per_p,
-                   d_u, d_v, d_sw, d_st, d_q, 0};
-    constexpr int NT = 256;
-    constexpr int NW = NT / 32;
-    const size_t fixed = kBatchMaxN * 8 + 4 * kBatchMaxN * 4 + (size_t)NW * kBatchMaxN * 4 + NW * 8 + 64;
-    size_t smem = std::min<size_t>(ctx->smem_optin, 110 * 1024);   // two blocks per SM
-    args.smem_table = smem > fixed ? smem - fixed : 0;
-    int grid = 0;
-    auto launch = [&](auto kern) -> sa_status {
-        SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0;
-        SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
-        grid = std::max(1, std::min(k, ctx->num_sms * std::max(per_sm, 1)));
-        kern<<<grid, NT, smem, st>>>(args);
-        count_launch();
-        return SA_OK;
-    };
-    if (wtype == SA_I16) {
-        if (kc <= 1) rc = launch(batch_kernel<int16_t, NT, 1>);
-        else rc = launch(batch_kernel<int16_t, NT, 2>);
-    } else {
-        if (kc <= 1) rc = launch(batch_kernel<int32_t, NT, 1>);
-        else if (kc <= 2) rc = launch(batch_kernel<int32_t, NT, 2>);
-        else rc = launch(batch_kernel<int32_t, NT, 4>);
+    SA_CUDA(cudaMemsetAsync(d_q, 0, 4 * SA_BATCH_MAX_BUCKETS, st));
+    // fork: each non-empty bucket launches on a stream of its own after the set-up above,
+    // so the buckets' kernels run side by side; the context stream waits for all of them
+    if (!ctx->batch_events[SA_BATCH_MAX_BUCKETS])
+        SA_CUDA(cudaEventCreateWithFlags(&ctx->batch_events[SA_BATCH_MAX_BUCKETS], cudaEventDisableTiming));
+    SA_CUDA(cudaEventRecord(ctx->batch_events[SA_BATCH_MAX_BUCKETS], st));
+    for (int b = 0; b < plan.count; ++b) {
+        if (cnt[b] == 0) continue;
+        if (!ctx->batch_streams[b]) SA_CUDA(cudaStreamCreateWithFlags(&ctx->batch_streams[b], cudaStreamNonBlocking));
+        if (!ctx->batch_events[b]) SA_CUDA(cudaEventCreateWithFlags(&ctx->batch_events[b], cudaEventDisableTiming));
+        cudaStream_t bs = ctx->batch_streams[b];
+        SA_CUDA(cudaStreamWaitEvent(bs, ctx->batch_events[SA_BATCH_MAX_BUCKETS], 0));
+        const auto& m = members[b];
+        const int nmax = plan.path[b] == SA_BATCH_GROUP ? hn[m.back()] : hn[m.front()];
+        BatchArgs args{d_w, d_n, d_ld, d_off, d_order + first[b], cnt[b], wtype == SA_I16, d_P, o->n_p, o->tol,
+                       o->max_sweeps_per_p, d_u, d_v, d_sw, d_st, d_q + b, 0};
+        if (plan.path[b] == SA_BATCH_GROUP)
+            rc = launch_group_path(ctx, bs, args, nmax, plan.warps[b], plan.per_block[b], wtype);
+        else rc = launch_block_path(ctx, bs, args, nmax, wtype);
+        // joined even after a failed launch: the buckets already running finish first
+        SA_CUDA(cudaEventRecord(ctx->batch_events[b], bs));
+        SA_CUDA(cudaStreamWaitEvent(st, ctx->batch_events[b], 0));
+        if (rc) {
+            cudaStreamSynchronize(st);
+            return rc;
+        }
     }
-    if (rc) return rc;
-    SA_CUDA(cudaGetLastError());
-    std::vector<int32_t> hsw(k), hst(k);
-    SA_CUDA(cudaMemcpyAsync(hsw.data(), d_sw, 4 * k, cudaMemcpyDeviceToHost, st));
-    SA_CUDA(cudaMemcpyAsync(hst.data(), d_st, 4 * k, cudaMemcpyDeviceToHost, st));
-    SA_CUDA(cudaStreamSynchronize(st));
-    if (sweeps) memcpy(sweeps, hsw.data(), 4 * k);
-    if (status) memcpy(status, hst.data(), 4 * k);
-    int worst = 0;
-    for (int q = 0; q < k; ++q) {
-        if (hst[q] < 0) worst = -6;
-        else if (hst[q] > 0 && worst == 0) worst = 1;
-    }
-    if (worst < 0) { set_error("a batch instance lost all mass in a row or column"); return SA_E_NONFINITE; }
-    if (worst > 0) { set_error("a batch instance hit max_sweeps_per_p"); return SA_E_NOT_CONVERGED; }
-    return SA_OK;
+    return finish_batch(st, k, d_sw, d_st, sweeps, status);
 }

@@ -52,6 +52,21 @@ struct PinnedBuf {
     ~PinnedBuf();
 };
 
+// sa_batch_scale's plan when none is set (see sa_set_batch_plan)
+inline sa_batch_plan default_batch_plan() {
+    sa_batch_plan p{};
+    p.count = 4;
+    const int n_hi[4] = {32, 64, 128, 512}, path[4] = {SA_BATCH_GROUP, SA_BATCH_GROUP, SA_BATCH_GROUP, SA_BATCH_BLOCK};
+    const int warps[4] = {1, 2, 4, 0}, per_block[4] = {4, 4, 1, 0};
+    for (int b = 0; b < 4; ++b) {
+        p.n_hi[b] = n_hi[b];
+        p.path[b] = path[b];
+        p.warps[b] = warps[b];
+        p.per_block[b] = per_block[b];
+    }
+    return p;
+}
+
 }  // namespace sa
 
 struct sa_ctx {
@@ -68,6 +83,9 @@ struct sa_ctx {
     size_t step_l2_bytes = (size_t)48 << 20;  // step kernel: bytes of K read with the default L2
                                               // policy (the rest "evict first")
     int test_unreachable_barrier = 0;         // testing hook (SA_OPT_TEST_UNREACHABLE_BARRIER)
+    sa_batch_plan batch_plan = sa::default_batch_plan();
+    cudaStream_t batch_streams[SA_BATCH_MAX_BUCKETS] = {};   // one per bucket launch (lazily made)
+    cudaEvent_t batch_events[SA_BATCH_MAX_BUCKETS + 1] = {};
     sa::Workspace ws;        // scratch for sweeps, prune, certify
     sa::Workspace input;     // device copy of host inputs (sa_assign_host)
     sa::Workspace keep;      // sa_scale: the caller's warm-start potentials, restored on failure

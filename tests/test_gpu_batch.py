@@ -26,7 +26,7 @@ def ctx():
     c.close()
 
 
-def batch_scale(ctx, mats, ps, tol=1e-6, sweeps=20000):
+def batch_scale(ctx, mats, ps, tol=1e-6, sweeps=20000, plan=None):
     """Pack instances as device tensors and run sa_batch_scale; returns (u_list, v_list, sweeps, status)."""
     devs = [api.to_device(m) for m in mats]
     k = len(mats)
@@ -42,10 +42,16 @@ def batch_scale(ctx, mats, ps, tol=1e-6, sweeps=20000):
     st = np.zeros(k, dtype=np.int32)
     o = L.make_opts(ps, tol, sweeps)
     wt = L.SA_I16 if mats[0].dtype == np.int16 else L.SA_I32
-    rc = L.lib().sa_batch_scale(ctx.handle, k, ctypes.c_void_p(ptrs.data_ptr()), ctypes.c_void_p(ns.data_ptr()),
-                                ctypes.c_void_p(lds.data_ptr()), ctypes.c_void_p(offs.data_ptr()), wt,
-                                ctypes.byref(o), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()),
-                                sw.ctypes.data_as(L._I32P), st.ctypes.data_as(L._I32P))
+    if plan is not None:
+        api.sa_set_batch_plan(ctx, plan)
+    try:
+        rc = L.lib().sa_batch_scale(ctx.handle, k, ctypes.c_void_p(ptrs.data_ptr()), ctypes.c_void_p(ns.data_ptr()),
+                                    ctypes.c_void_p(lds.data_ptr()), ctypes.c_void_p(offs.data_ptr()), wt,
+                                    ctypes.byref(o), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                                    sw.ctypes.data_as(L._I32P), st.ctypes.data_as(L._I32P))
+    finally:
+        if plan is not None:
+            api.sa_set_batch_plan(ctx, None)
     uh, vh = u.cpu().numpy(), v.cpu().numpy()
     us = [uh[o_:o_ + m.shape[0]] for o_, m in zip(offs_h, mats)]
     vs = [vh[o_:o_ + m.shape[0]] for o_, m in zip(offs_h, mats)]
@@ -69,6 +75,49 @@ def test_batch_matches_oracle(ctx, dtype):
         xo = oracle.xmatrix(b, ps[-1], uo, vo)
         xg = oracle.xmatrix(b, ps[-1], u, v)
         assert np.max(np.abs(xg - xo)) < 1e-4
+
+
+@pytest.mark.parametrize("dtype", [np.int16, np.int32])
+def test_group_path_error_does_not_grow_with_p(ctx, dtype):
+    """Instances of n <= 128 run on the group path on the per-step matrix K (float-pair
+    exponent once per p step): up to p = 128 their FP64-recomputed sums stay within the bound
+    of the per-step path (2e-6), independent of p, unlike the block path's FP32 logarithm
+    (about 1.3e-7 p).  Ragged sizes: one row, odd n, every template (n <= 32, 64, 128) and
+    both sides of each boundary."""
+    sizes = [1, 3, 5, 16, 31, 32, 33, 47, 63, 64, 65, 99, 127, 128]
+    mats = [W.uniform(n, 1, 1000, 1100 + n, dtype=dtype) for n in sizes]
+    ps = [2.0 ** k for k in range(8)]
+    rc, us, vs, sw, st = batch_scale(ctx, mats, ps, sweeps=20000)
+    assert rc in (0, L.SA_E_NOT_CONVERGED), rc
+    for m, u, v, s_, c_ in zip(mats, us, vs, sw, st):
+        b = oracle.log_weights(m.astype(np.int64))
+        uo, vo, swo, rso, sto = oracle.sinkhorn(b, ps, 1e-6, 20000)
+        # the same stopping decisions as the oracle's (the cap where it caps)
+        assert c_ == (1 if sto == oracle.NOT_CONVERGED else 0), (m.shape, c_, sto)
+        if c_ != 0:
+            continue
+        r, c = oracle.sums(b, ps[-1], u, v)
+        err = max(np.abs(r - 1).max(), np.abs(c - 1).max())
+        assert err < 2e-6, (m.shape, err)
+        xo = oracle.xmatrix(b, ps[-1], uo, vo)
+        xg = oracle.xmatrix(b, ps[-1], u, v)
+        assert np.all(np.abs(xg - xo) <= 8e-6 * np.maximum(xo, 1.0 / m.shape[0]) + 1e-9), m.shape
+
+
+def test_group_and_block_paths_agree(ctx):
+    """The same small instances through the group path and through the block path (a plan
+    with one block bucket): both within their bounds of the oracle's X(p)."""
+    sizes = [2, 9, 24, 40, 64, 90, 128]
+    mats = [W.uniform(n, 1, 1000, 1200 + n, dtype=np.int16) for n in sizes]
+    ps = [1.0, 2.0, 4.0, 8.0]
+    rc_w, uw, vw, sww, stw = batch_scale(ctx, mats, ps)
+    rc_b, ub, vb, swb, stb = batch_scale(ctx, mats, ps, plan=[(512, "block", 0, 0)])
+    assert rc_w == 0 and rc_b == 0
+    for m, a, b_, c, d in zip(mats, uw, vw, ub, vb):
+        b = oracle.log_weights(m.astype(np.int64))
+        xw = oracle.xmatrix(b, ps[-1], a, b_)
+        xb = oracle.xmatrix(b, ps[-1], c, d)
+        assert np.max(np.abs(xw - xb)) < 2 * ps[-1] * np.log(2) * 1e-6 + 1e-5
 
 
 def test_batch_not_converged_like_oracle(ctx):
@@ -96,6 +145,31 @@ def test_alone_equals_in_batch(ctx):
         # same instance, same block program: bit-identical potentials and sweep counts
         assert sw1[0] == sw[k]
         assert np.array_equal(u1[0], us[k]) and np.array_equal(v1[0], vs[k])
+
+
+def test_plans_are_checked_and_applied(ctx):
+    """Bad plans are refused; plans of several group buckets with different launch shapes
+    give each instance the result of the default plan (the group path's program per
+    instance does not depend on the bucket or the launch shape: bit-identical)."""
+    for bad in ([(64, "group", 1, 4)],                                     # does not reach 512
+                [(256, "group", 4, 1), (512, "block", 0, 0)],              # group path beyond 128
+                [(32, "group", 3, 1), (512, "block", 0, 0)],               # 3 warps per instance
+                [(32, "group", 4, 4), (512, "block", 0, 0)],               # 16 warps per block
+                [(64, "block", 0, 0), (32, "group", 1, 4), (512, "block", 0, 0)]):   # not increasing
+        with pytest.raises(api.SaError):
+            api.sa_set_batch_plan(ctx, bad)
+    sizes = [5, 12, 20, 30, 40, 50, 60, 64, 70, 100, 128, 200]
+    mats = [W.uniform(n, 1, 1000, 1300 + n, dtype=np.int16) for n in sizes]
+    ps = [1.0, 2.0, 4.0, 8.0]
+    rc0, u0, v0, sw0, st0 = batch_scale(ctx, mats, ps)
+    for plan in ([(16, "group", 1, 1), (32, "group", 2, 4), (48, "group", 4, 2), (64, "group", 1, 2),
+                  (128, "group", 2, 1), (512, "block", 0, 0)],
+                 [(128, "group", 4, 2), (512, "block", 0, 0)]):
+        rc1, u1, v1, sw1, st1 = batch_scale(ctx, mats, ps, plan=plan)
+        assert rc0 == 0 and rc1 == 0
+        for a, b, c, d in zip(u0, v0, u1, v1):
+            assert np.array_equal(a, c) and np.array_equal(b, d)
+        assert np.array_equal(sw0, sw1)
 
 
 def test_batch_rejects_large_n(ctx):
