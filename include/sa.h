@@ -436,8 +436,11 @@ sa_status sa_narrow_i32_to_i16(sa_ctx* ctx, const int32_t* d_src, int64_t ld_src
  * GROUP: a group of 1, 2 or 4 warps per instance (n <= 128), with the per-step matrix K of
  *   the STEP path in a shared-memory slot of the group (exponent in float-pair arithmetic
  *   once per p step); the sweeps multiply and add only, the group's warps meet at a named
- *   barrier of their own, and the error does not grow with p. */
-typedef enum { SA_BATCH_BLOCK = 0, SA_BATCH_GROUP = 1 } sa_batch_path;
+ *   barrier of their own, and the error does not grow with p.
+ * REGS: as GROUP, with K in registers during the sweeps (each row and column of K split
+ *   over 32 G / NMAX adjacent lanes): 1, 2 or 4 warps for n <= 32, 4 or 8 for n <= 64, 16
+ *   for n <= 128. */
+typedef enum { SA_BATCH_BLOCK = 0, SA_BATCH_GROUP = 1, SA_BATCH_REGS = 2 } sa_batch_path;
 
 /* A launch plan: instances are grouped by n into buckets (n_hi[b-1], n_hi[b]] (n_hi
  * increasing, the last >= 512), and each bucket runs on its path in a persistent launch of
@@ -448,9 +451,11 @@ typedef enum { SA_BATCH_BLOCK = 0, SA_BATCH_GROUP = 1 } sa_batch_path;
 typedef struct {
     int32_t count;                          /* buckets in use, 1 .. SA_BATCH_MAX_BUCKETS */
     int32_t n_hi[SA_BATCH_MAX_BUCKETS];     /* largest n of each bucket */
-    int32_t path[SA_BATCH_MAX_BUCKETS];     /* sa_batch_path; GROUP only for n_hi <= 128 */
-    int32_t warps[SA_BATCH_MAX_BUCKETS];    /* GROUP: warps per instance, 1, 2 or 4 */
-    int32_t per_block[SA_BATCH_MAX_BUCKETS];/* GROUP: groups per block; warps * per_block <= 8 */
+    int32_t path[SA_BATCH_MAX_BUCKETS];     /* sa_batch_path; GROUP and REGS for n_hi <= 128 */
+    int32_t warps[SA_BATCH_MAX_BUCKETS];    /* GROUP: warps per instance, 1, 2 or 4;
+                                               REGS: 1, 2, 4, 8 or 16 (as above) */
+    int32_t per_block[SA_BATCH_MAX_BUCKETS];/* groups per block: GROUP warps * per_block <= 8,
+                                               REGS <= 16 warps per block */
 } sa_batch_plan;
 
 /* Set the context's plan (copied); NULL restores the default: n <= 32 one warp per

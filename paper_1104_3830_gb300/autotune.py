@@ -7,8 +7,10 @@ the sweep cap), so the latency of one sweep decides their time, while the larges
 by the SFU work of their elements.  No single launch shape suits both, so instances are
 grouped into size buckets and each bucket gets the shape that measured fastest for it:
 
-* the group path (n <= 128): a group of 1, 2 or 4 warps per instance, 1, 2 or 4 groups per
-  block (at most 8 warps per block);
+* the group path (n <= 128): a group of 1, 2 or 4 warps per instance with K in shared
+  memory, 1, 2 or 4 groups per block (at most 8 warps per block);
+* the register path (n <= 128): K in registers during the sweeps, 1, 2 or 4 warps per
+  instance up to n = 32, 4 or 8 up to 64, 16 up to 128 (at most 16 warps per block);
 * the block path: one block of 256 threads per instance.
 
 :func:`tune` times every candidate of every bucket on a seeded synthetic pack of that
@@ -40,6 +42,8 @@ def candidates(lo: int, hi: int):
     out = []
     if hi <= GROUP_MAX_N:
         out += [("group", w, g) for w in (1, 2, 4) for g in (1, 2, 4) if w * g <= 8]
+        regs = (1, 2, 4) if hi <= 32 else (4, 8) if hi <= 64 else (16,)
+        out += [("regs", w, g) for w in regs for g in (1, 2, 4, 8) if w * g <= 16]
     out.append(("block", 0, 0))
     return out
 
@@ -55,10 +59,10 @@ def plan_from_choice(choice: dict):
     plan = []
     for lo, hi in BUCKETS:
         path, warps, per_block = choice.get(bucket_name(lo, hi), ("block", 0, 0))
-        if path == "group":
+        if path in ("group", "regs"):
             if hi > GROUP_MAX_N:
-                raise ValueError(f"bucket {lo}-{hi}: the group path takes n <= {GROUP_MAX_N}")
-            plan.append((hi, "group", int(warps), int(per_block)))
+                raise ValueError(f"bucket {lo}-{hi}: the {path} path takes n <= {GROUP_MAX_N}")
+            plan.append((hi, path, int(warps), int(per_block)))
         else:
             plan.append((hi, "block", 0, 0))
     return plan

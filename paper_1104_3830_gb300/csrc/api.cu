@@ -388,6 +388,15 @@ sa_status sa_set_batch_plan(sa_ctx* ctx, const sa_batch_plan* plan) {
                           "at most 8 warps per block", b);
                 return SA_E_INVALID;
             }
+        } else if (plan->path[b] == SA_BATCH_REGS) {
+            const int w = plan->warps[b], g = plan->per_block[b], nh = plan->n_hi[b];
+            const bool shape = (nh <= 32 && (w == 1 || w == 2 || w == 4)) || (nh <= 64 && (w == 4 || w == 8)) ||
+                               (nh <= 128 && w == 16);
+            if (!shape || g < 1 || w * g > 16) {
+                set_error("plan bucket %d: the register path takes 1, 2 or 4 warps per instance up to n = 32, 4 or 8 "
+                          "up to 64, 16 up to 128, and at most 16 warps per block", b);
+                return SA_E_INVALID;
+            }
         } else if (plan->path[b] != SA_BATCH_BLOCK) {
             set_error("plan bucket %d: unknown path %d", b, plan->path[b]);
             return SA_E_INVALID;

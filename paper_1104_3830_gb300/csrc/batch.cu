@@ -517,6 +517,208 @@ __global__ void __launch_bounds__(256) batch_group_kernel(BatchArgs A) {
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Register path: the group path with K held in registers during the sweeps.  A group of G
+// warps (T = 32 G threads) takes n <= NMAX; each row q (and column q) of the padded NMAX x
+// NMAX matrix belongs to P = T / NMAX adjacent lanes, lane part p holding the L = NMAX / P
+// entries K_q,[pL, pL+L) of the row and K_[pL, pL+L),q of the column in registers (2 L <= 64
+// floats).  A sweep then reads no K: the row pass multiplies the row part by the c of its
+// columns (broadcast from shared memory) and adds the P parts with lane shuffles; the
+// column pass does the same with 1/s; one group barrier after each pass publishes 1/s and
+// c.  K is evaluated once per p step exactly as in the group path (same float-pair
+// exponent), staged in shared memory and loaded into the registers.
+// ---------------------------------------------------------------------------------------
+template <int NMAX, int P>
+__host__ __device__ inline unsigned regs_slot_floats() {
+    constexpr unsigned L = NMAX / P;
+    // staging K (NMAX x (NMAX + 1)), c and 1/s (P segments of L + 4), V pairs, C, residuals
+    return ((NMAX * (NMAX + 1) + 3u) & ~3u) + 2u * P * (L + 4) + 2u * NMAX + NMAX + 64u;
+}
+
+template <typename WT, int G, int NMAX>
+__global__ void __launch_bounds__(512) batch_regs_kernel(BatchArgs A) {
+    constexpr int NT = 32 * G;
+    constexpr int P = NT / NMAX;   // lanes per row (and per column)
+    constexpr int L = NMAX / P;    // entries of a row part
+    constexpr int SEG = L + 4;     // padded segment of c and 1/s (parts in distinct banks)
+    constexpr int CPL = NMAX / 32; // columns per lane in the evaluation of K
+    static_assert(P >= 1 && P * NMAX == NT && L <= 32 && (P & (P - 1)) == 0 && P <= 32, "shape");
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float4 s_l2tab[256];
+    const int tid = threadIdx.x;
+    for (int j = tid; j < 256; j += blockDim.x) s_l2tab[j] = log2_tab_entry(j);
+    __syncthreads();   // the only block barrier: the groups are independent from here on
+    const int group = tid / NT, tg = tid % NT, lane = tid & 31, wig = tg >> 5;
+    const int q = tg / P, part = tg % P;   // row and column q, part `part`
+    float* Kst = (float*)smem + (size_t)group * regs_slot_floats<NMAX, P>();
+    float* cs = Kst + ((NMAX * (NMAX + 1) + 3) & ~3);
+    float* rs = cs + P * SEG;
+    float2* vp = (float2*)(rs + P * SEG);
+    float* Cs = (float*)(vp + NMAX);
+    float* wres = Cs + NMAX;                  // [2][G] residuals, by sweep parity
+    int* s_q = (int*)(wres + 2 * G);
+    constexpr int STR = NMAX + 1;
+    const unsigned FULL = 0xffffffffu;
+    for (;;) {
+        if (tg == 0) *s_q = (int)atomicAdd(A.queue, 1u);
+        group_sync<G>(group);
+        const int qi = *s_q;
+        group_sync<G>(group);   // s_q is rewritten by the next instance
+        if (qi >= A.k) break;
+        const int inst = A.order[qi];
+        const int n = A.n[inst];
+        const WT* wb = (const WT*)A.w[inst];
+        const int64_t ld = A.ld[inst];
+        double Vq = 0.0;           // column q's potential, log2 units (the same in every part)
+        float cq = 0.0f, sq = 1.0f, Cq = 0.0f;
+        float kr[L], kc[L];
+        int sweeps_all = 0;
+        bool bad = false, capped = false;
+        for (int k = 0; k < A.n_p && !bad; ++k) {
+            const double p = A.P[k];
+            if (k > 0) Vq *= p / A.P[k - 1];
+            // ---- one evaluation of K for this p, staged in shared memory ----
+            if (part == 0) {
+                const float h = (float)Vq;
+                vp[q] = make_float2(h, (float)(Vq - (double)h));
+            }
+            group_sync<G>(group);
+            const float ph = (float)p;
+            const float pl = (float)(p - (double)ph);
+            int badk = 0;
+            for (int i = wig; i < NMAX; i += G) {   // a row per warp, lanes over its columns
+                float* kr_s = Kst + (size_t)i * STR;
+                if (i >= n) {
+#pragma unroll
+                    for (int h = 0; h < CPL; ++h) kr_s[lane + 32 * h] = 0.0f;
+                    continue;
+                }
+                const WT* wr = wb + (int64_t)i * ld;
+                int wv[CPL];
+                float m = -INFINITY;
+#pragma unroll
+                for (int h = 0; h < CPL; ++h) {
+                    const int j = lane + 32 * h;
+                    wv[h] = j < n ? (int)wr[j] : 0;
+                    if (wv[h] > 0) m = fmaxf(m, fmaf(ph, lg2_approx((float)wv[h]), -vp[j].x));
+                }
+                m = warp_max(m);
+                if (!(m > -INFINITY)) { badk = 1; m = 0.0f; }
+                if (lane == 0) Cs[i] = m;
+#pragma unroll
+                for (int h = 0; h < CPL; ++h) {
+                    const int j = lane + 32 * h;
+                    float x = 0.0f;
+                    if (wv[h] > 0) {
+                        const float2 lw = wlog2(s_l2tab, wv[h]);
+                        const float2 vj = vp[j];
+                        const float t = ph * lw.x;
+                        const float te = fmaf(ph, lw.x, -t);
+                        float e1, e2;
+                        const float u1 = two_sum(t, -vj.x, &e1);
+                        const float u2 = two_sum(u1, -m, &e2);
+                        const float rest = ((te + e1) + e2) + (fmaf(ph, lw.y, pl * lw.x) - vj.y);
+                        x = ex2_approx(u2 + rest);
+                    }
+                    kr_s[j] = x;
+                }
+            }
+            if (lane == 0) wres[wig] = (float)badk;
+            group_sync<G>(group);
+#pragma unroll
+            for (int x = 0; x < G; ++x) bad = bad || wres[x] != 0.0f;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                kr[l] = Kst[(size_t)q * STR + part * L + l];
+                kc[l] = Kst[(size_t)(part * L + l) * STR + q];
+            }
+            Cq = q < n ? Cs[q] : 0.0f;
+            cq = q < n ? 1.0f : 0.0f;
+            if (part == 0) {
+                cs[(q / L) * SEG + q % L] = cq;
+                rs[(q / L) * SEG + q % L] = 0.0f;   // rows beyond n keep 1/s = 0
+            }
+            group_sync<G>(group);   // c published; wres and the staging area are reused
+            // ---- sweeps ----
+            int sweeps = 0;
+            bool done = bad;
+            while (!done) {
+                const int par = sweeps & 1;
+                // row pass: s_q = sum over the parts of K_q,part . c_part
+                const float* cseg = cs + part * SEG;
+                float a[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int l = 0; l < L; l += 4) {
+                    const float4 c4 = *(const float4*)(cseg + l);
+                    a[(l / 4) & 7] = fmaf(kr[l], c4.x, a[(l / 4) & 7]);
+                    a[(l / 4 + 2) & 7] = fmaf(kr[l + 1], c4.y, a[(l / 4 + 2) & 7]);
+                    a[(l / 4 + 4) & 7] = fmaf(kr[l + 2], c4.z, a[(l / 4 + 4) & 7]);
+                    a[(l / 4 + 6) & 7] = fmaf(kr[l + 3], c4.w, a[(l / 4 + 6) & 7]);
+                }
+                float sv = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+#pragma unroll
+                for (int o = 1; o < P; o <<= 1) sv += __shfl_xor_sync(FULL, sv, o);
+                int badr = 0;
+                if (q < n) {
+                    if (!(sv >= 0x1p-120f && sv <= 0x1p120f)) badr = 1;
+                    sq = sv;
+                    if (part == 0) rs[(q / L) * SEG + q % L] = rcp_approx(sv);
+                }
+                group_sync<G>(group);
+                // column pass: S_q = c_q sum over the parts of K_part,q . (1/s)_part
+                const float* rseg = rs + part * SEG;
+#pragma unroll
+                for (int x = 0; x < 8; ++x) a[x] = 0.0f;
+#pragma unroll
+                for (int l = 0; l < L; l += 4) {
+                    const float4 r4 = *(const float4*)(rseg + l);
+                    a[(l / 4) & 7] = fmaf(kc[l], r4.x, a[(l / 4) & 7]);
+                    a[(l / 4 + 2) & 7] = fmaf(kc[l + 1], r4.y, a[(l / 4 + 2) & 7]);
+                    a[(l / 4 + 4) & 7] = fmaf(kc[l + 2], r4.z, a[(l / 4 + 4) & 7]);
+                    a[(l / 4 + 6) & 7] = fmaf(kc[l + 3], r4.w, a[(l / 4 + 6) & 7]);
+                }
+                float cv = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+#pragma unroll
+                for (int o = 1; o < P; o <<= 1) cv += __shfl_xor_sync(FULL, cv, o);
+                float resid = 0.0f;
+                if (q < n) {
+                    const float S = cq * cv;
+                    if (!(S > 0.0f) || !(S < INFINITY)) badr = 1;
+                    resid = fabsf(S - 1.0f);
+                    cq = __fdividef(cq, S);
+                    if (part == 0) cs[(q / L) * SEG + q % L] = cq;
+                }
+                // the group's residual (a failure as +inf): non-negative floats order like
+                // their bit patterns, so one warp reduction of the bits gives the maximum
+                const unsigned rb = __reduce_max_sync(FULL, __float_as_uint(badr ? INFINITY : resid));
+                if (G > 1 && lane == 0) wres[par * G + wig] = __uint_as_float(rb);
+                group_sync<G>(group);
+                float rmax = __uint_as_float(rb);
+                if (G > 1) {
+                    rmax = 0.0f;
+#pragma unroll
+                    for (int x = 0; x < G; ++x) rmax = fmaxf(rmax, wres[par * G + x]);
+                }
+                ++sweeps;
+                bad = !(rmax < INFINITY);
+                done = bad || (rmax <= (float)A.tol) || (sweeps >= A.max_sweeps);
+                if (done && !bad && !(rmax <= (float)A.tol)) capped = true;
+            }
+            sweeps_all += sweeps;
+            if (bad) break;
+            if (q < n) Vq -= log2((double)cq);
+            if (k + 1 == A.n_p && part == 0 && q < n)
+                A.U[A.off[inst] + q] = ((double)Cq + log2((double)sq)) * kLn2;
+        }
+        if (part == 0 && q < n) A.V[A.off[inst] + q] = Vq * kLn2;
+        if (tg == 0) {
+            A.sweeps[inst] = sweeps_all;
+            A.status[inst] = bad ? -6 : (capped ? 1 : 0);
+        }
+        group_sync<G>(group);   // the slot is rewritten by the next instance
+    }
+}
+
 }  // namespace
 }  // namespace sa
 
@@ -555,6 +757,54 @@ sa_status launch_group_n(sa_ctx* ctx, cudaStream_t bs, const BatchArgs& args, in
     if (nmax <= 32) return launch_group<WT, G, 32>(ctx, bs, args, per_block);
     if (nmax <= 64) return launch_group<WT, G, 64>(ctx, bs, args, per_block);
     return launch_group<WT, G, 128>(ctx, bs, args, per_block);
+}
+
+// register path: `per_block` groups of G warps per block
+template <typename WT, int G, int NMAX>
+sa_status launch_regs(sa_ctx* ctx, cudaStream_t bs, const BatchArgs& args, int per_block) {
+    constexpr int P = 32 * G / NMAX;
+    auto kern = batch_regs_kernel<WT, G, NMAX>;
+    const size_t smem = (size_t)per_block * regs_slot_floats<NMAX, P>() * sizeof(float);
+    const int threads = 32 * G * per_block;
+    cudaFuncAttributes fa;
+    SA_CUDA(cudaFuncGetAttributes(&fa, kern));
+    if (threads > fa.maxThreadsPerBlock || smem + fa.sharedSizeBytes > ctx->smem_optin) {
+        set_error("batch register path: %d groups of %d warps for n <= %d do not fit a block (%d threads, %zu bytes)",
+                  per_block, G, NMAX, threads, smem + fa.sharedSizeBytes);
+        return SA_E_UNSUPPORTED;
+    }
+    SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) {
+        set_error("batch register path: %d groups of %d warps do not fit on an SM", per_block, G);
+        return SA_E_UNSUPPORTED;
+    }
+    const int blocks = std::max(1, std::min((args.k + per_block - 1) / per_block, ctx->num_sms * per_sm));
+    kern<<<blocks, threads, smem, bs>>>(args);
+    count_launch();
+    SA_CUDA(cudaGetLastError());
+    return SA_OK;
+}
+
+// the register path's shapes: (warps per instance, largest n) with 2 L <= 64 registers of K
+template <typename WT>
+sa_status launch_regs_t(sa_ctx* ctx, cudaStream_t bs, const BatchArgs& args, int nmax, int warps, int per_block) {
+    if (nmax <= 32 && warps == 1) return launch_regs<WT, 1, 32>(ctx, bs, args, per_block);
+    if (nmax <= 32 && warps == 2) return launch_regs<WT, 2, 32>(ctx, bs, args, per_block);
+    if (nmax <= 32 && warps == 4) return launch_regs<WT, 4, 32>(ctx, bs, args, per_block);
+    if (nmax <= 64 && warps == 4) return launch_regs<WT, 4, 64>(ctx, bs, args, per_block);
+    if (nmax <= 64 && warps == 8) return launch_regs<WT, 8, 64>(ctx, bs, args, per_block);
+    if (nmax <= 128 && warps == 16) return launch_regs<WT, 16, 128>(ctx, bs, args, per_block);
+    set_error("batch register path: no shape of %d warps for n = %d (1, 2 or 4 warps up to 32, 4 or 8 up to 64, "
+              "16 up to 128)", warps, nmax);
+    return SA_E_UNSUPPORTED;
+}
+
+sa_status launch_regs_path(sa_ctx* ctx, cudaStream_t bs, const BatchArgs& args, int nmax, int warps, int per_block,
+                           sa_wtype wtype) {
+    return wtype == SA_I16 ? launch_regs_t<int16_t>(ctx, bs, args, nmax, warps, per_block)
+                           : launch_regs_t<int32_t>(ctx, bs, args, nmax, warps, per_block);
 }
 
 sa_status launch_group_path(sa_ctx* ctx, cudaStream_t bs, const BatchArgs& args, int nmax, int warps, int per_block,
@@ -662,7 +912,7 @@ extern "C" sa_status sa_batch_scale(sa_ctx* ctx, int32_t k, const void* const* d
     std::vector<int> first(plan.count), cnt(plan.count);
     for (int b = 0; b < plan.count; ++b) {
         auto& m = members[b];
-        if (plan.path[b] == SA_BATCH_GROUP)
+        if (plan.path[b] != SA_BATCH_BLOCK)
             std::stable_sort(m.begin(), m.end(), [&](int a, int c) { return hn[a] < hn[c]; });
         else
             std::stable_sort(m.begin(), m.end(), [&](int a, int c) { return hn[a] > hn[c]; });
@@ -694,11 +944,13 @@ extern "C" sa_status sa_batch_scale(sa_ctx* ctx, int32_t k, const void* const* d
         cudaStream_t bs = ctx->batch_streams[b];
         SA_CUDA(cudaStreamWaitEvent(bs, ctx->batch_events[SA_BATCH_MAX_BUCKETS], 0));
         const auto& m = members[b];
-        const int nmax = plan.path[b] == SA_BATCH_GROUP ? hn[m.back()] : hn[m.front()];
+        const int nmax = plan.path[b] == SA_BATCH_BLOCK ? hn[m.front()] : hn[m.back()];
         BatchArgs args{d_w, d_n, d_ld, d_off, d_order + first[b], cnt[b], wtype == SA_I16, d_P, o->n_p, o->tol,
                        o->max_sweeps_per_p, d_u, d_v, d_sw, d_st, d_q + b, 0};
         if (plan.path[b] == SA_BATCH_GROUP)
             rc = launch_group_path(ctx, bs, args, nmax, plan.warps[b], plan.per_block[b], wtype);
+        else if (plan.path[b] == SA_BATCH_REGS)
+            rc = launch_regs_path(ctx, bs, args, nmax, plan.warps[b], plan.per_block[b], wtype);
         else rc = launch_block_path(ctx, bs, args, nmax, wtype);
         // joined even after a failed launch: the buckets already running finish first
         SA_CUDA(cudaEventRecord(ctx->batch_events[b], bs));

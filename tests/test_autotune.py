@@ -15,6 +15,11 @@ def test_candidates_respect_the_group_path_limits():
         grp = [x for x in c if x[0] == "group"]
         assert (len(grp) == 8) == (hi <= A.GROUP_MAX_N)
         assert all(w in (1, 2, 4) and g >= 1 and w * g <= 8 for _, w, g in grp)
+        regs = [x for x in c if x[0] == "regs"]
+        assert bool(regs) == (hi <= A.GROUP_MAX_N)
+        # K of a thread's row and column parts fits 64 registers: 2 * n_max / (32 w / n_max) <= 64
+        nmax = 32 if hi <= 32 else 64 if hi <= 64 else 128
+        assert all(2 * nmax * nmax // (32 * w) <= 64 and w * g <= 16 for _, w, g in regs)
     with pytest.raises(ValueError):
         A.candidates(10, 5)
 

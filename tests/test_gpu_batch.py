@@ -120,6 +120,54 @@ def test_group_and_block_paths_agree(ctx):
         assert np.max(np.abs(xw - xb)) < 2 * ps[-1] * np.log(2) * 1e-6 + 1e-5
 
 
+REGS_PLAN = [(32, "regs", 1, 4), (64, "regs", 4, 2), (128, "regs", 16, 1), (512, "block", 0, 0)]
+
+
+@pytest.mark.parametrize("dtype", [np.int16, np.int32])
+def test_register_path_matches_oracle(ctx, dtype):
+    """The register path (K in registers during the sweeps; rows and columns split over 1,
+    2 or 4 lanes) on every shape: the oracle's stopping decisions, X(p) within 8e-6 of the
+    oracle's entries and FP64 sums within 2e-6 up to p = 128."""
+    sizes = [1, 2, 7, 31, 32, 33, 50, 64, 65, 100, 128]
+    mats = [W.uniform(n, 1, 1000, 1500 + n, dtype=dtype) for n in sizes]
+    ps = [2.0 ** k for k in range(8)]
+    rc, us, vs, sw, st = batch_scale(ctx, mats, ps, plan=REGS_PLAN)
+    assert rc in (0, L.SA_E_NOT_CONVERGED), rc
+    for m, u, v, c_ in zip(mats, us, vs, st):
+        b = oracle.log_weights(m.astype(np.int64))
+        uo, vo, swo, rso, sto = oracle.sinkhorn(b, ps, 1e-6, 20000)
+        assert c_ == (1 if sto == oracle.NOT_CONVERGED else 0), (m.shape, c_, sto)
+        if c_ != 0:
+            continue
+        r, c = oracle.sums(b, ps[-1], u, v)
+        assert max(np.abs(r - 1).max(), np.abs(c - 1).max()) < 2e-6, m.shape
+        xo = oracle.xmatrix(b, ps[-1], uo, vo)
+        xg = oracle.xmatrix(b, ps[-1], u, v)
+        assert np.all(np.abs(xg - xo) <= 8e-6 * np.maximum(xo, 1.0 / m.shape[0]) + 1e-9), m.shape
+
+
+def test_register_path_shapes(ctx):
+    """Shapes the register path does not have are refused; the groups per block do not change
+    an instance's result (bit-identical), and a zero column is reported as non-finite."""
+    for bad in ([(64, "regs", 1, 4), (512, "block", 0, 0)],      # one warp cannot hold n <= 64
+                [(128, "regs", 8, 1), (512, "block", 0, 0)],     # eight warps cannot hold n <= 128
+                [(32, "regs", 4, 8), (512, "block", 0, 0)]):     # 32 warps per block
+        with pytest.raises(api.SaError):
+            api.sa_set_batch_plan(ctx, bad)
+    mats = [W.uniform(n, 1, 1000, 1600 + n, dtype=np.int16) for n in (5, 20, 32, 40, 64, 90)]
+    ps = [1.0, 2.0, 4.0]
+    rc0, u0, v0, sw0, _ = batch_scale(ctx, mats, ps, plan=REGS_PLAN)
+    rc1, u1, v1, sw1, _ = batch_scale(ctx, mats, ps, plan=[(32, "regs", 1, 1), (64, "regs", 4, 4),
+                                                           (128, "regs", 16, 1), (512, "block", 0, 0)])
+    assert rc0 == 0 and rc1 == 0 and np.array_equal(sw0, sw1)
+    for a, b, c, d in zip(u0, v0, u1, v1):
+        assert np.array_equal(a, c) and np.array_equal(b, d)
+    z = W.uniform(30, 1, 1000, 1700, dtype=np.int16)
+    z[:, 7] = 0
+    rc, *_, st = batch_scale(ctx, [z, mats[0]], ps, plan=REGS_PLAN)
+    assert rc == L.SA_E_NONFINITE and st[0] == -6 and st[1] == 0
+
+
 def test_batch_not_converged_like_oracle(ctx):
     # small uniform instances at p = 128 are nearly decomposable: the oracle hits the
     # cap on exactly these, and so must the batch (status 1, SA_E_NOT_CONVERGED overall)
