@@ -458,9 +458,10 @@ typedef struct {
                                                REGS <= 16 warps per block */
 } sa_batch_plan;
 
-/* Set the context's plan (copied); NULL restores the default: n <= 32 one warp per
- * instance and n <= 64 two, four groups per block; n <= 128 four warps, one group per block;
- * the rest on the block path.  SA_E_INVALID for a plan that breaks the rules above. */
+/* Set the context's plan (copied); NULL restores the default (the autotuner's choice on a
+ * GB300): the register path with one warp per instance (two per block) up to n = 32, four
+ * warps up to 64 and sixteen up to 128, the rest on the block path.  SA_E_INVALID for a plan
+ * that breaks the rules above. */
 sa_status sa_set_batch_plan(sa_ctx* ctx, const sa_batch_plan* plan);
 
 /*

@@ -56,8 +56,8 @@ struct PinnedBuf {
 inline sa_batch_plan default_batch_plan() {
     sa_batch_plan p{};
     p.count = 4;
-    const int n_hi[4] = {32, 64, 128, 512}, path[4] = {SA_BATCH_GROUP, SA_BATCH_GROUP, SA_BATCH_GROUP, SA_BATCH_BLOCK};
-    const int warps[4] = {1, 2, 4, 0}, per_block[4] = {4, 4, 1, 0};
+    const int n_hi[4] = {32, 64, 128, 512}, path[4] = {SA_BATCH_REGS, SA_BATCH_REGS, SA_BATCH_REGS, SA_BATCH_BLOCK};
+    const int warps[4] = {1, 4, 16, 0}, per_block[4] = {2, 1, 1, 0};
     for (int b = 0; b < 4; ++b) {
         p.n_hi[b] = n_hi[b];
         p.path[b] = path[b];

@@ -77,6 +77,9 @@ def test_batch_matches_oracle(ctx, dtype):
         assert np.max(np.abs(xg - xo)) < 1e-4
 
 
+GROUP_PLAN = [(32, "group", 1, 4), (64, "group", 2, 4), (128, "group", 4, 1), (512, "block", 0, 0)]
+
+
 @pytest.mark.parametrize("dtype", [np.int16, np.int32])
 def test_group_path_error_does_not_grow_with_p(ctx, dtype):
     """Instances of n <= 128 run on the group path on the per-step matrix K (float-pair
@@ -87,7 +90,7 @@ def test_group_path_error_does_not_grow_with_p(ctx, dtype):
     sizes = [1, 3, 5, 16, 31, 32, 33, 47, 63, 64, 65, 99, 127, 128]
     mats = [W.uniform(n, 1, 1000, 1100 + n, dtype=dtype) for n in sizes]
     ps = [2.0 ** k for k in range(8)]
-    rc, us, vs, sw, st = batch_scale(ctx, mats, ps, sweeps=20000)
+    rc, us, vs, sw, st = batch_scale(ctx, mats, ps, sweeps=20000, plan=GROUP_PLAN)
     assert rc in (0, L.SA_E_NOT_CONVERGED), rc
     for m, u, v, s_, c_ in zip(mats, us, vs, sw, st):
         b = oracle.log_weights(m.astype(np.int64))
@@ -110,7 +113,7 @@ def test_group_and_block_paths_agree(ctx):
     sizes = [2, 9, 24, 40, 64, 90, 128]
     mats = [W.uniform(n, 1, 1000, 1200 + n, dtype=np.int16) for n in sizes]
     ps = [1.0, 2.0, 4.0, 8.0]
-    rc_w, uw, vw, sww, stw = batch_scale(ctx, mats, ps)
+    rc_w, uw, vw, sww, stw = batch_scale(ctx, mats, ps, plan=GROUP_PLAN)
     rc_b, ub, vb, swb, stb = batch_scale(ctx, mats, ps, plan=[(512, "block", 0, 0)])
     assert rc_w == 0 and rc_b == 0
     for m, a, b_, c, d in zip(mats, uw, vw, ub, vb):
@@ -197,8 +200,8 @@ def test_alone_equals_in_batch(ctx):
 
 def test_plans_are_checked_and_applied(ctx):
     """Bad plans are refused; plans of several group buckets with different launch shapes
-    give each instance the result of the default plan (the group path's program per
-    instance does not depend on the bucket or the launch shape: bit-identical)."""
+    give each instance the result of the same warps per instance (the group path's program
+    per instance does not depend on the bucket or the groups per block: bit-identical)."""
     for bad in ([(64, "group", 1, 4)],                                     # does not reach 512
                 [(256, "group", 4, 1), (512, "block", 0, 0)],              # group path beyond 128
                 [(32, "group", 3, 1), (512, "block", 0, 0)],               # 3 warps per instance
@@ -209,10 +212,10 @@ def test_plans_are_checked_and_applied(ctx):
     sizes = [5, 12, 20, 30, 40, 50, 60, 64, 70, 100, 128, 200]
     mats = [W.uniform(n, 1, 1000, 1300 + n, dtype=np.int16) for n in sizes]
     ps = [1.0, 2.0, 4.0, 8.0]
-    rc0, u0, v0, sw0, st0 = batch_scale(ctx, mats, ps)
-    for plan in ([(16, "group", 1, 1), (32, "group", 2, 4), (48, "group", 4, 2), (64, "group", 1, 2),
-                  (128, "group", 2, 1), (512, "block", 0, 0)],
-                 [(128, "group", 4, 2), (512, "block", 0, 0)]):
+    rc0, u0, v0, sw0, st0 = batch_scale(ctx, mats, ps, plan=GROUP_PLAN)
+    for plan in ([(16, "group", 1, 1), (32, "group", 1, 2), (48, "group", 2, 1), (64, "group", 2, 2),
+                  (128, "group", 4, 2), (512, "block", 0, 0)],
+                 [(32, "group", 1, 8), (64, "group", 2, 4), (128, "group", 4, 1), (512, "block", 0, 0)]):
         rc1, u1, v1, sw1, st1 = batch_scale(ctx, mats, ps, plan=plan)
         assert rc0 == 0 and rc1 == 0
         for a, b, c, d in zip(u0, v0, u1, v1):
