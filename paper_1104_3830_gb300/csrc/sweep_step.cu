@@ -308,14 +308,23 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     // ---- one evaluation of this stripe's rows of K for p (V: the epoch's starting column
     //      potentials), dense rows in global memory plus, when enabled, the entries
     //      >= theta as (column, value) records ----
-    auto prep = [&](double p) {
+    // cscale > 0: the row references come from the previous step's row potentials,
+    // C_i = cscale U_i (cscale = p_k / p_{k-1}): with (u, v) scaled by that ratio, C_i lies
+    // within cscale log2 n above max_j (p log2 w_ij - V_j), so every entry of K stays in
+    // [2^-(cscale log2 n + the range of the row), 1] and no per-row maximum pass is needed.
+    // cscale = 0: the references are the FP32 row maxima (a cold start, a kept v, a
+    // re-evaluation within a step).
+    auto prep = [&](double p, double cscale) {
         const float pf = (float)p;
-        // the region is idle: stage V there as float pairs (hi, lo)
-        float2* vsm = (float2*)region;
-        for (int j = tid; j < n; j += NT) {
-            const double vj = A.V[j];
+        // the region is idle: stage V there as the FP32 head and tail of each entry, in two
+        // arrays, so that a thread reads its four columns with one 16-byte load from each
+        float* vhi = (float*)region;
+        float* vlo = vhi + NC * 4;
+        for (int j = tid; j < NC * 4; j += NT) {
+            const double vj = j < n ? A.V[j] : 0.0;
             const float hi = (float)vj;
-            vsm[j] = make_float2(hi, (float)(vj - (double)hi));
+            vhi[j] = hi;
+            vlo[j] = (float)(vj - (double)hi);
         }
         // p = ph + pl (pl = 0 for any p with at most 24 significant bits)
         const float ph = (float)p;
@@ -325,8 +334,10 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
         unsigned* wcnt = (unsigned*)red;   // [NW] per-warp kept counts (scratch)
         size_t roff = 0;                   // records written so far (block-relative)
         bool overflow = false;
-        // the weights of row q + 1 are loaded while row q is evaluated
-        int wv[M], wn[M];
+        // the weights of row q + 1 are loaded while row q is evaluated (up to eight chunks a
+        // thread: wider rows would spill the second set of registers)
+        constexpr bool PREF = CH <= 8;
+        int wv[M], wn[PREF ? M : 1];
         auto load_row = [&](int q, int* dst) {
 #pragma unroll
             for (int k = 0; k < CH; ++k) {
@@ -336,38 +347,61 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 for (int e = 0; e < 4; ++e) dst[4 * k + e] = w4[e];
             }
         };
-        load_row(0, wn);
+        if (PREF) load_row(0, wn);
         for (int q = 0; q < nrows; ++q) {
             const int64_t row = r0 + q;
+            if (PREF) {
 #pragma unroll
-            for (int x = 0; x < M; ++x) wv[x] = wn[x];
-            load_row(q + 1, wn);
-            // reference C ~ max_j (p log2 w - V_j), an FP32 estimate (only a scale; C itself
-            // enters the row potential exactly)
-            float mloc = -INFINITY;
-#pragma unroll
-            for (int x = 0; x < M; ++x)
-                if ((x % 4) < nval[x / 4] && wv[x] > 0)
-                    mloc = fmaxf(mloc, fmaf(pf, lg2_approx((float)wv[x]), -vsm[cidx[x / 4] * 4 + (x % 4)].x));
-            mloc = warp_max(mloc);
-            float* smx = (float*)redd;
-            if (lane == 0) smx[wid] = mloc;
-            __syncthreads();
-            float mf = -INFINITY;
-#pragma unroll
-            for (int x = 0; x < NW; ++x) mf = fmaxf(mf, smx[x]);
-            if (!(mf > -INFINITY)) {
-                if (tid == 0) atomicCAS(A.err, 0, kErrNonfinite);
-                mf = 0.0f;
+                for (int x = 0; x < M; ++x) wv[x] = wn[PREF ? x : 0];
+                load_row(q + 1, wn);
+            } else {
+                load_row(q, wv);
             }
-            if (tid == 0) crow[q] = (double)mf;
-            __syncthreads();   // smx is rewritten by the next row
-            const float mh = mf, ml = 0.0f;
+            double cref;
+            if (cscale > 0.0) {
+                cref = A.U[row] * cscale;
+            } else {
+                // reference C ~ max_j (p log2 w - V_j), an FP32 estimate (only a scale; C itself
+                // enters the row potential exactly)
+                float mloc = -INFINITY;
+#pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    if (nval[k] == 0) continue;
+                    const float4 vh4 = *(const float4*)(vhi + cidx[k] * 4);
+                    const float vh[4] = {vh4.x, vh4.y, vh4.z, vh4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (e < nval[k] && wv[4 * k + e] > 0)
+                            mloc = fmaxf(mloc, fmaf(pf, lg2_approx((float)wv[4 * k + e]), -vh[e]));
+                }
+                mloc = warp_max(mloc);
+                float* smx = (float*)redd;
+                if (lane == 0) smx[wid] = mloc;
+                __syncthreads();
+                float mf = -INFINITY;
+#pragma unroll
+                for (int x = 0; x < NW; ++x) mf = fmaxf(mf, smx[x]);
+                if (!(mf > -INFINITY)) {
+                    if (tid == 0) atomicCAS(A.err, 0, kErrNonfinite);
+                    mf = 0.0f;
+                }
+                cref = (double)mf;
+                __syncthreads();   // smx is rewritten by the next row
+            }
+            if (tid == 0) crow[q] = cref;
+            const float mh = (float)cref, ml = (float)(cref - (double)mh);
             float* krow = A.K + row * A.ldk;
             float kvs[M];
 #pragma unroll
             for (int k = 0; k < CH; ++k) {
                 float kv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                float vh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, vl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                if (nval[k] > 0) {
+                    const float4 h4 = *(const float4*)(vhi + cidx[k] * 4);
+                    const float4 l4 = *(const float4*)(vlo + cidx[k] * 4);
+                    vh[0] = h4.x; vh[1] = h4.y; vh[2] = h4.z; vh[3] = h4.w;
+                    vl[0] = l4.x; vl[1] = l4.y; vl[2] = l4.z; vl[3] = l4.w;
+                }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int x = 4 * k + e;
@@ -376,7 +410,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                         // parts cancel exactly (two-product, two-sums), the small ones are
                         // added after; x is then exact to about 2^-24 |x|
                         const float2 lw = wlog2(s_l2tab, wv[x]);
-                        const float2 vj = vsm[cidx[k] * 4 + e];
+                        const float2 vj = make_float2(vh[e], vl[e]);
                         const float t = ph * lw.x;
                         const float te = fmaf(ph, lw.x, -t);
                         float e1, e2;
@@ -465,7 +499,9 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 A.Vs[j] = A.V[j];
                 A.Cf[j] = 1.0f;
             }
-            prep(p);
+            // the first evaluation of a step after a step (or a resumed one) scaled (u, v):
+            // row references from U; otherwise the row maxima
+            prep(p, (k > 0 && !A.keep_v && step_reanchors == 0) ? p / A.P[k - 1] : 0.0);
             if (!gsync()) { drain(); return; }
             // mode of this epoch, identical in every block
             if (tid == 0) {
@@ -811,14 +847,14 @@ StepCfg pick_step(const sa_ctx* ctx, int n) {
     const unsigned row_bytes = (unsigned)align_up((size_t)n * 4, 16);
     const int max_rows = step_max_rows(ctx, n);
     if (c.direct) {
-        // no ring: the region only stages V (8 n bytes) while K is evaluated
-        if (step_smem_bytes(c.nt, align_up((size_t)n * 8, 16), max_rows) <= ctx->smem_optin) return c;
+        // no ring: the region only stages V (8 ceil(n/4)*4 bytes) while K is evaluated
+        if (step_smem_bytes(c.nt, align_up((size_t)nc * 32, 16), max_rows) <= ctx->smem_optin) return c;
         c.nt = 0;
         return c;
     }
-    // the ring doubles as scratch for V (8 n bytes) during the per-step evaluation
+    // the ring doubles as scratch for V (8 ceil(n/4)*4 bytes) during the per-step evaluation
     for (int ring = 8; ring >= 4; --ring) {
-        if ((size_t)ring * row_bytes < (size_t)n * 8) break;
+        if ((size_t)ring * row_bytes < (size_t)nc * 32) break;
         if (step_smem_bytes(c.nt, (size_t)ring * row_bytes, max_rows) <= ctx->smem_optin) {
             c.ring = ring;
             return c;
@@ -930,7 +966,7 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     } else if (!o->warm_keep_v) {
         launch_scale_vec(V, n, o->p[k0] / o->p[k0 - 1], st);
     }
-    const size_t region = cfg.direct ? align_up((size_t)n * 8, 16) : (size_t)cfg.ring * align_up((size_t)n * 4, 16);
+    const size_t region = cfg.direct ? align_up((size_t)((n + 3) / 4) * 32, 16) : (size_t)cfg.ring * align_up((size_t)n * 4, 16);
     const size_t cs_bytes = align_up((size_t)n * 8, 16);
     StepArgs args{};
     args.w = a->w;
