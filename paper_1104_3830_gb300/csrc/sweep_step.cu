@@ -45,6 +45,11 @@ constexpr int kStepMaxRing = 16;  // ring slots at most; a slot holds one stage 
 // 487 us per sweep at n = 20000 for four stages ahead): it evicts rows that are still to
 // be re-read for the column accumulation.
 constexpr int kStepPrefetch = 0;
+// rows per ring stage of the dense ring mode.  A stage costs a fixed ~0.5 us (the
+// publication of the warps' partial row sums and the slot's release) plus ~0.4 us per row
+// at n = 8192, so two-row stages beat one-row stages (34.7 against 47.7 us per row pass)
+// although a one-row ring keeps twice the rows in flight.
+constexpr int kDenseRowsPerStage = 2;
 
 struct StepArgs {
     const void* w;
@@ -167,7 +172,7 @@ struct KahanS {
 // SP: sparse epochs possible.  DIR: rows too wide for a shared-memory ring (n > 12288) are
 // read straight from global memory (with a bulk L2 prefetch of the stage being read) and
 // re-read from L2 for the column accumulation.
-template <int NT, int CH, bool SP, bool DIR>
+template <int NT, int CH, bool SP, bool DIR, int RPS>
 __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     constexpr int NW = NT / 32;
     constexpr int M = CH * 4;   // columns owned per thread (dense mode)
@@ -175,6 +180,8 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     constexpr int MAXR = kStepMaxRing;
     constexpr int FG = NT / 64;
     static_assert(NT % 64 == 0, "layout");
+    static_assert(RPS == 1 || RPS == 2, "rows per stage");
+    static_assert(!SP || RPS == 2, "sparse records come in stages of two rows");
     extern __shared__ __align__(128) unsigned char smem[];
     // [region: dense ring | or sparse c, S and ring] [barriers] [scratch]
     unsigned char* region = smem;
@@ -235,7 +242,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     // the records of the two rows) in fixed slots: ring index v is stage v % nst of its sweep,
     // in slot v % ring_n.  The warp whose release completes a slot's count refills it with
     // ring index v + ring_n: no thread waits to issue a copy.
-    const int nst = (nrows + 1) / 2;
+    const int nst = (nrows + RPS - 1) / RPS;
     // Stage read at ring index v: the sweeps of an epoch alternate direction over the stripe,
     // so the rows a sweep reads last -- the ones most likely still in L2 (K is about twice
     // the L2 at n = 8192) -- are the rows the next sweep reads first.  The first sweep of an
@@ -247,8 +254,8 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     auto issue_index = [&](uint32_t v) {   // one thread
         const uint32_t slot = v % (uint32_t)ring_n;
         const int stg = stage_of(v);
-        const int q0 = 2 * stg;
-        const int nr = min(2, nrows - q0);
+        const int q0 = RPS * stg;
+        const int nr = min(RPS, nrows - q0);
         const void* src;
         unsigned bytes;
         if (SP && sparse) {
@@ -268,8 +275,8 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
             bulk_g2s_hint(sbase + (size_t)slot * slot_bytes, src, bytes, &mbar[slot], l2_policy_evict_first());
     };
     auto prefetch_stage = [&](int g) {   // one thread: the K rows of stage g into L2
-        const int q0 = 2 * g;
-        const int nr = min(2, nrows - q0);
+        const int q0 = RPS * g;
+        const int nr = min(RPS, nrows - q0);
         if (nr > 0) bulk_prefetch_l2(kbase + (size_t)(r0 + q0) * kpitch, (unsigned)nr * A.row_bytes);
     };
     auto release_index = [&](uint32_t v) {   // lane 0 after __syncwarp
@@ -531,9 +538,9 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 sbase = region + cs_bytes;
                 ring_n = (int)min((size_t)MAXR, ((size_t)A.region_bytes - cs_bytes) / slot_bytes);
             } else {
-                slot_bytes = 2u * A.row_bytes;
+                slot_bytes = (unsigned)RPS * A.row_bytes;
                 sbase = region;
-                ring_n = A.ring / 2;
+                ring_n = A.ring / RPS;
 #pragma unroll
                 for (int m = 0; m < M; ++m) cf[m] = (m % 4) < nval[m / 4] ? 1.0f : 0.0f;
             }
@@ -582,8 +589,8 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 };
                 auto produce = [&](int g) {
                     const uint32_t v = its + g;
-                    const int q0 = 2 * stage_of(v);
-                    const bool two = q0 + 1 < nrows;
+                    const int q0 = RPS * stage_of(v);
+                    const bool two = RPS == 2 && q0 + 1 < nrows;
                     const uint32_t rn = (uint32_t)ring_n;
                     if (DIR) {
                         // rows of stage g + P into L2 (the stage after the last wraps to the
@@ -595,26 +602,26 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                     const float sp0 = row_partial(row_of(v, q0, 0), q0);
                     const float sp1 = two ? row_partial(row_of(v, q0, 1), q0 + 1) : 0.0f;
                     const float w0 = warp_sum(sp0);
-                    const float w1 = warp_sum(sp1);
+                    const float w1 = RPS == 2 ? warp_sum(sp1) : 0.0f;
                     if (lane == 0) {
                         const uint32_t gs = gbase + g;
                         red[((gs % NRED) * 2) * NW + wid] = w0;
-                        red[((gs % NRED) * 2 + 1) * NW + wid] = w1;
+                        if (RPS == 2) red[((gs % NRED) * 2 + 1) * NW + wid] = w1;
                         mbar_arrive(&mrow[gs % NRED]);
                     }
                 };
                 auto consume = [&](int g) -> bool {
                     const uint32_t v = its + g;
-                    const int q0 = 2 * stage_of(v);
-                    const bool two = q0 + 1 < nrows;
+                    const int q0 = RPS * stage_of(v);
+                    const bool two = RPS == 2 && q0 + 1 < nrows;
                     const uint32_t gs = gbase + g;
                     if (!mbar_wait(&mrow[gs % NRED], (gs / NRED) & 1u, A.err, A.wait_ns)) s_flag = 1;
                     // warp-uniform: a warp either releases the stage (every lane got its copy
                     // and every partial) or leaves the pass as a whole
                     if (__any_sync(0xffffffffu, *(volatile int*)&s_flag != 0)) return false;
-                    float ss[2];
+                    float ss[2] = {1.0f, 1.0f};
 #pragma unroll
-                    for (int r = 0; r < 2; ++r) {
+                    for (int r = 0; r < RPS; ++r) {
                         const float4* rv = (const float4*)(red + ((gs % NRED) * 2 + r) * NW);
                         float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
 #pragma unroll
@@ -637,7 +644,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                         if (two) srow[q0 + 1] = ss[1];
                     }
 #pragma unroll
-                    for (int r = 0; r < 2; ++r) {
+                    for (int r = 0; r < RPS; ++r) {
                         if (r == 1 && !two) break;
                         const float inv = rcp_approx(ss[r]);
                         const unsigned char* rowp = row_of(v, q0, r);
@@ -867,7 +874,8 @@ StepCfg pick_step(const sa_ctx* ctx, int n) {
 template <int NT, int CH, bool DIR>
 sa_status launch_step(sa_ctx* ctx, const StepArgs& args, size_t smem, int* grid_out) {
     // the dense-only instantiation carries none of the sparse code
-    auto kern = (!DIR && args.sparse_ok) ? step_kernel<NT, CH, !DIR, DIR> : step_kernel<NT, CH, false, DIR>;
+    auto kern = (!DIR && args.sparse_ok) ? step_kernel<NT, CH, !DIR, DIR, 2>
+                                         : step_kernel<NT, CH, false, DIR, DIR ? 2 : kDenseRowsPerStage>;
     SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
@@ -886,7 +894,7 @@ sa_status launch_step(sa_ctx* ctx, const StepArgs& args, size_t smem, int* grid_
     *grid_out = G;
     StepArgs a = args;
     // stages of each stripe that stay L2-resident: the context's byte budget over the grid
-    const size_t stage_bytes = 2 * (size_t)args.row_bytes;
+    const size_t stage_bytes = (size_t)(DIR || args.sparse_ok ? 2 : kDenseRowsPerStage) * args.row_bytes;
     const size_t keep = ctx->step_l2_bytes / ((size_t)G * stage_bytes);
     a.l2_keep_stages = (int)std::min<size_t>(keep, (size_t)args.n);
     void* params[] = {&a};
