@@ -439,8 +439,12 @@ sa_status sa_narrow_i32_to_i16(sa_ctx* ctx, const int32_t* d_src, int64_t ld_src
  *   barrier of their own, and the error does not grow with p.
  * REGS: as GROUP, with K in registers during the sweeps (each row and column of K split
  *   over 32 G / NMAX adjacent lanes): 1, 2 or 4 warps for n <= 32, 4 or 8 for n <= 64, 16
- *   for n <= 128. */
-typedef enum { SA_BATCH_BLOCK = 0, SA_BATCH_GROUP = 1, SA_BATCH_REGS = 2 } sa_batch_path;
+ *   for n <= 128.
+ * KROWS: one block of 256 threads per instance (n <= 512) on the same K, kept in a global
+ *   slot of n x ceil(n/4)*4 FP32 per block (taken from the context workspace: up to two
+ *   blocks per SM); each warp evaluates and reads whole rows, so a row sum needs no block
+ *   barrier, and a sweep has one; the error does not grow with p. */
+typedef enum { SA_BATCH_BLOCK = 0, SA_BATCH_GROUP = 1, SA_BATCH_REGS = 2, SA_BATCH_KROWS = 3 } sa_batch_path;
 
 /* A launch plan: instances are grouped by n into buckets (n_hi[b-1], n_hi[b]] (n_hi
  * increasing, the last >= 512), and each bucket runs on its path in a persistent launch of
@@ -460,8 +464,8 @@ typedef struct {
 
 /* Set the context's plan (copied); NULL restores the default (the autotuner's choice on a
  * GB300): the register path with one warp per instance (two per block) up to n = 32, four
- * warps up to 64 and sixteen up to 128, the rest on the block path.  SA_E_INVALID for a plan
- * that breaks the rules above. */
+ * warps up to 64 and sixteen up to 128, the K rows path in two buckets up to 256 and 512.
+ * SA_E_INVALID for a plan that breaks the rules above. */
 sa_status sa_set_batch_plan(sa_ctx* ctx, const sa_batch_plan* plan);
 
 /*
@@ -498,8 +502,8 @@ typedef struct {
  * admitted request is charged an upper bound of the device memory it can hold while it
  * runs (sa_server_request_bytes), and is admitted only while the charges of the requests
  * on the device stay within hbm_budget.  Outside the budget the server holds only its
- * workers' small persistent state: per small-request worker (two) a context workspace of a
- * few MiB, and a CUDA stream per worker. */
+ * workers' small persistent state: per small-request worker (two) a context workspace of at
+ * most 32 MiB, and a CUDA stream per worker. */
 sa_status sa_server_create(sa_server** s, int device, size_t hbm_budget, const sa_scale_opts* opts,
                            int32_t solver_threads);
 void sa_server_destroy(sa_server* s);
@@ -520,7 +524,8 @@ double sa_server_now(const sa_server* s);
 
 /* Bytes of the budget an n x n request of this weight type is charged: its matrix (16-byte
  * row pitch) plus, for n <= 512, its potentials, the reduced instance's device arrays (8
- * bytes per kept entry, at most n^2) and 1 MiB; for larger n, everything sa_assign can
+ * bytes per kept entry, at most n^2), 1 MiB and above n = 128 a batched slot of K
+ * (4 * 512^2 bytes); for larger n, everything sa_assign can
  * allocate (the per-step matrix K of 4 n ceil(n/4)*4 bytes, the reduced instance's device
  * arrays up to 8 n^2 bytes, column partials, vectors).  0 for bad arguments. */
 size_t sa_server_request_bytes(const sa_server* s, sa_wtype wtype, int32_t n);

@@ -22,7 +22,7 @@ SA_E_NO_PERFECT_MATCHING, SA_E_NONFINITE, SA_E_BUDGET, SA_E_TIMEOUT, SA_E_UNSUPP
 SA_I16, SA_I32 = 0, 1
 OPTION = {"wait_limit_ns": 0, "solve_gpu": 1, "step_sparse": 2, "max_grid": 3, "fused_threads": 4, "step_l2_bytes": 5,
           "test_unreachable_barrier": 6}
-SA_BATCH_BLOCK, SA_BATCH_GROUP, SA_BATCH_REGS = 0, 1, 2
+SA_BATCH_BLOCK, SA_BATCH_GROUP, SA_BATCH_REGS, SA_BATCH_KROWS = 0, 1, 2, 3
 PREC = {"mixed": 0, "fp32": 1, "fp64": 2}
 KERNEL = {"auto": 0, "fused": 1, "plain": 2, "step": 3, "newton": 4}
 STATUS_NAMES = {0: "SA_OK", 1: "SA_PENDING", -1: "SA_E_INVALID", -2: "SA_E_NOMEM", -3: "SA_E_CUDA",

@@ -48,8 +48,8 @@ def sa_destroy(ctx: Context) -> None:
 
 
 def sa_set_batch_plan(ctx: Context, buckets=None) -> None:
-    """sa_set_batch_plan from a list of (n_hi, path, warps, per_block) with path "group", "regs"
-    or "block" (warps and per_block: warps per instance and groups per block);
+    """sa_set_batch_plan from a list of (n_hi, path, warps, per_block) with path "group", "regs",
+    "krows" or "block" (warps and per_block: warps per instance and groups per block);
     None restores the library's default plan."""
     if buckets is None:
         check(lib().sa_set_batch_plan(ctx.handle, None))
@@ -58,7 +58,8 @@ def sa_set_batch_plan(ctx: Context, buckets=None) -> None:
     plan.count = len(buckets)
     for b, (n_hi, path, warps, per_block) in enumerate(buckets):
         plan.n_hi[b] = int(n_hi)
-        plan.path[b] = {"group": L.SA_BATCH_GROUP, "regs": L.SA_BATCH_REGS}.get(path, L.SA_BATCH_BLOCK)
+        plan.path[b] = {"group": L.SA_BATCH_GROUP, "regs": L.SA_BATCH_REGS, "krows": L.SA_BATCH_KROWS}.get(
+            path, L.SA_BATCH_BLOCK)
         plan.warps[b] = int(warps)
         plan.per_block[b] = int(per_block)
     check(lib().sa_set_batch_plan(ctx.handle, ctypes.byref(plan)))

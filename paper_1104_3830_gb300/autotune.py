@@ -11,7 +11,9 @@ grouped into size buckets and each bucket gets the shape that measured fastest f
   memory, 1, 2 or 4 groups per block (at most 8 warps per block);
 * the register path (n <= 128): K in registers during the sweeps, 1, 2 or 4 warps per
   instance up to n = 32, 4 or 8 up to 64, 16 up to 128 (at most 16 warps per block);
-* the block path: one block of 256 threads per instance.
+* the K rows path: one block of 256 threads per instance on K kept in a global slot, each
+  warp on whole rows;
+* the block path: one block of 256 threads per instance, an SFU exp2 per term and sweep.
 
 :func:`tune` times every candidate of every bucket on a seeded synthetic pack of that
 bucket (instances/s of sa_batch_scale on that pack alone) and returns the fastest of each;
@@ -30,7 +32,7 @@ import numpy as np
 
 BUCKETS = [(1, 32), (33, 64), (65, 128), (129, 256), (257, 512)]
 GROUP_MAX_N = 128
-CACHE_VERSION = 2
+CACHE_VERSION = 3
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned", "batch_plan.json")
 
 
@@ -44,6 +46,7 @@ def candidates(lo: int, hi: int):
         out += [("group", w, g) for w in (1, 2, 4) for g in (1, 2, 4) if w * g <= 8]
         regs = (1, 2, 4) if hi <= 32 else (4, 8) if hi <= 64 else (16,)
         out += [("regs", w, g) for w in regs for g in (1, 2, 4, 8) if w * g <= 16]
+    out.append(("krows", 0, 0))
     out.append(("block", 0, 0))
     return out
 
@@ -64,7 +67,7 @@ def plan_from_choice(choice: dict):
                 raise ValueError(f"bucket {lo}-{hi}: the {path} path takes n <= {GROUP_MAX_N}")
             plan.append((hi, path, int(warps), int(per_block)))
         else:
-            plan.append((hi, "block", 0, 0))
+            plan.append((hi, "krows" if path == "krows" else "block", 0, 0))
     return plan
 
 

@@ -397,7 +397,7 @@ sa_status sa_set_batch_plan(sa_ctx* ctx, const sa_batch_plan* plan) {
                           "up to 64, 16 up to 128, and at most 16 warps per block", b);
                 return SA_E_INVALID;
             }
-        } else if (plan->path[b] != SA_BATCH_BLOCK) {
+        } else if (plan->path[b] != SA_BATCH_BLOCK && plan->path[b] != SA_BATCH_KROWS) {
             set_error("plan bucket %d: unknown path %d", b, plan->path[b]);
             return SA_E_INVALID;
         }

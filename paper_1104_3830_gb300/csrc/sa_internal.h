@@ -55,10 +55,11 @@ struct PinnedBuf {
 // sa_batch_scale's plan when none is set (see sa_set_batch_plan)
 inline sa_batch_plan default_batch_plan() {
     sa_batch_plan p{};
-    p.count = 4;
-    const int n_hi[4] = {32, 64, 128, 512}, path[4] = {SA_BATCH_REGS, SA_BATCH_REGS, SA_BATCH_REGS, SA_BATCH_BLOCK};
-    const int warps[4] = {1, 4, 16, 0}, per_block[4] = {2, 1, 1, 0};
-    for (int b = 0; b < 4; ++b) {
+    p.count = 5;
+    const int n_hi[5] = {32, 64, 128, 256, 512};
+    const int path[5] = {SA_BATCH_REGS, SA_BATCH_REGS, SA_BATCH_REGS, SA_BATCH_KROWS, SA_BATCH_KROWS};
+    const int warps[5] = {1, 4, 16, 0, 0}, per_block[5] = {2, 1, 1, 0, 0};
+    for (int b = 0; b < 5; ++b) {
         p.n_hi[b] = n_hi[b];
         p.path[b] = path[b];
         p.warps[b] = warps[b];

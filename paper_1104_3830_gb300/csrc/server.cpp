@@ -87,7 +87,7 @@ cudaError_t srv_alloc(void** p, size_t bytes, cudaStream_t st) {
 
 // Device bytes a request can hold while it runs (an upper bound).  Small requests: the
 // matrix, the potentials, the reduced instance's device arrays (8 bytes per kept entry,
-// at most n^2) and the batch launch's tables.  Large ones: the matrix and everything
+// at most n^2), the batch launch's tables and, above n = 128, a slot of K.  Large ones: the matrix and everything
 // sa_assign allocates (sa::assign_device_bound).  What is not counted is each worker
 // context's small persistent state: the small workers' workspaces (a few MiB for
 // n <= 512) and the CUDA streams.
@@ -95,7 +95,11 @@ size_t request_bytes(int n, sa_wtype wt, int num_sms) {
     const size_t sz = wt == SA_I16 ? 2 : 4;
     const size_t ld = sa::align_up((size_t)n * sz, 16) / sz;
     const size_t matrix = ld * n * sz;
-    if (n <= kSmallMax) return matrix + 2 * sizeof(double) * n + 8 * (size_t)n * n + 64 + (1 << 20);
+    // above n = 128 the batched form may keep K in a global slot sized for the group's
+    // largest instance (at most 4 * 512 * 512 bytes, one slot per instance at most)
+    if (n <= kSmallMax)
+        return matrix + 2 * sizeof(double) * n + 8 * (size_t)n * n + 64 + (1 << 20) +
+               (n > 128 ? (size_t)4 * kSmallMax * kSmallMax : 0);
     return matrix + sa::assign_device_bound(num_sms, n);
 }
 
@@ -285,6 +289,8 @@ void small_worker(sa_server* s) {
             cudaFreeAsync(d_tab, st);
             cudaFreeAsync(d_uv, st);
             cudaStreamSynchronize(st);
+            // the group's K slots were charged to its requests: keep only a small workspace
+            if (ctx->ws.size > ((size_t)32 << 20)) sa::release_buffers(ctx);
         } else {
             if (d_tab) cudaFreeAsync(d_tab, st);
             if (d_uv) cudaFreeAsync(d_uv, st);

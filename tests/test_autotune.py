@@ -11,7 +11,7 @@ from paper_1104_3830_gb300 import autotune as A
 def test_candidates_respect_the_group_path_limits():
     for lo, hi in A.BUCKETS:
         c = A.candidates(lo, hi)
-        assert ("block", 0, 0) in c and len(set(c)) == len(c)
+        assert ("block", 0, 0) in c and ("krows", 0, 0) in c and len(set(c)) == len(c)
         grp = [x for x in c if x[0] == "group"]
         assert (len(grp) == 8) == (hi <= A.GROUP_MAX_N)
         assert all(w in (1, 2, 4) and g >= 1 and w * g <= 8 for _, w, g in grp)

@@ -171,6 +171,39 @@ def test_register_path_shapes(ctx):
     assert rc == L.SA_E_NONFINITE and st[0] == -6 and st[1] == 0
 
 
+KROWS_PLAN = [(128, "regs", 16, 1), (512, "krows", 0, 0)]
+
+
+@pytest.mark.parametrize("dtype", [np.int16, np.int32])
+def test_krows_path_matches_oracle(ctx, dtype):
+    """The K rows path (n up to 512, K in a global slot per block, warps on whole rows) on
+    its three widths (n <= 128, 256, 512) and ragged sizes: X(p) within 8e-6 of the oracle's
+    entries and FP64 sums within 2e-6 up to p = 64, independent of p."""
+    sizes = [129, 130, 200, 255, 256, 257, 300, 511, 512]
+    mats = [W.uniform(n, 1, 1000, 1800 + n, dtype=dtype) for n in sizes]
+    ps = [2.0 ** k for k in range(7)]
+    rc, us, vs, sw, st = batch_scale(ctx, mats, ps, plan=KROWS_PLAN)
+    assert rc in (0, L.SA_E_NOT_CONVERGED), rc
+    for m, u, v, c_ in zip(mats, us, vs, st):
+        b = oracle.log_weights(m.astype(np.int64))
+        uo, vo, swo, rso, sto = oracle.sinkhorn(b, ps, 1e-6, 20000)
+        assert c_ == (1 if sto == oracle.NOT_CONVERGED else 0), (m.shape, c_, sto)
+        if c_ != 0:
+            continue
+        r, c = oracle.sums(b, ps[-1], u, v)
+        assert max(np.abs(r - 1).max(), np.abs(c - 1).max()) < 2e-6, m.shape
+        xo = oracle.xmatrix(b, ps[-1], uo, vo)
+        xg = oracle.xmatrix(b, ps[-1], u, v)
+        assert np.all(np.abs(xg - xo) <= 8e-6 * np.maximum(xo, 1.0 / m.shape[0]) + 1e-9), m.shape
+    # alone equals in the batch (one program per instance), and a lost column is reported
+    rc1, u1, v1, sw1, st1 = batch_scale(ctx, [mats[4]], ps, plan=KROWS_PLAN)
+    assert sw1[0] == sw[4] and np.array_equal(u1[0], us[4]) and np.array_equal(v1[0], vs[4])
+    z = mats[0].copy()
+    z[:, 5] = 0
+    rc2, *_, st2 = batch_scale(ctx, [z, mats[1]], ps, plan=KROWS_PLAN)
+    assert rc2 == L.SA_E_NONFINITE and st2[0] == -6 and st2[1] == 0
+
+
 def test_batch_not_converged_like_oracle(ctx):
     # small uniform instances at p = 128 are nearly decomposable: the oracle hits the
     # cap on exactly these, and so must the batch (status 1, SA_E_NOT_CONVERGED overall)
