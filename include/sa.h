@@ -215,7 +215,7 @@ sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* opts, d
  *   fused kernel reads (16-byte aligned base and row pitch).  Anything else returns
  *   SA_E_UNSUPPORTED or SA_E_INVALID with a message and runs nothing.
  *   The first call on a device looks the array's device address up (once per device,
- *   with that device current); make that first call before any stream capture.
+ *   with that device current).
  *   All calls share the array and find the previous call's contents in it; each call
  *   clears what must start at zero, but calls whose work overlaps on the GPU race on
  *   the array, so serialise them (one stream, or events).
