@@ -571,30 +571,55 @@ def serve_part(args):
             t = ctypes.c_uint64()
             L.check(lib.sa_submit(h, ctypes.c_void_p(m.ctypes.data), L.SA_I16, m.shape[0], ctypes.byref(t)))
             tickets.append(t.value)
-        lat, done_t, first, bad = [], [], None, 0
+        lat, done_t, first, bad, small, wait_adm, to_scaled = [], [], None, 0, [], [], []
         r = L.sa_result()
+        deadline = time.perf_counter() + 600.0
         for t in tickets:
             while True:
                 stt = lib.sa_poll(h, t, ctypes.byref(r))
                 if stt != L.SA_PENDING:
                     break
+                if time.perf_counter() > deadline:
+                    raise RuntimeError(f"serve: request {t} still pending after 600 s")
                 time.sleep(0.0005)
             bad += int(stt != 0)
             lat.append(r.t_done - r.t_submit)
+            wait_adm.append(r.t_start - r.t_submit)
+            to_scaled.append(r.t_scaled - r.t_submit if r.t_scaled > 0 else np.nan)
+            small.append(r.n <= 512)
             done_t.append(r.t_done)
             first = r.t_submit if first is None else min(first, r.t_submit)
             lib.sa_result_release(h, t)
+        stats = L.sa_server_stats()
+        L.check(lib.sa_server_get_stats(h, ctypes.byref(stats)))
         lib.sa_server_destroy(h)
         lat = np.array(lat)
+        small = np.array(small)
+        wait_adm = np.array(wait_adm)
+        to_scaled = np.array(to_scaled)
         span = max(done_t) - first
+
+        def pct(x, w, sc=None):
+            if not len(x):
+                return None
+            d = {"p50_ms": float(np.percentile(x, 50) * 1e3), "p99_ms": float(np.percentile(x, 99) * 1e3),
+                 "admission_wait_p50_ms": float(np.percentile(w, 50) * 1e3), "requests": int(len(x))}
+            if sc is not None and np.isfinite(sc).any():
+                d["scaled_after_p50_ms"] = float(np.nanpercentile(sc, 50) * 1e3)
+            return d
         return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "instances_per_s": len(lat) / span, "requests": len(lat), "failed": bad}
+                "instances_per_s": len(lat) / span, "requests": len(lat), "failed": bad,
+                "small_n_le_512": pct(lat[small], wait_adm[small], to_scaled[small]),
+                "large": pct(lat[~small], wait_adm[~small]),
+                "request_queue": {"launches": int(stats.live_launches), "requests": int(stats.live_requests),
+                                  "blocks_per_launch": int(stats.live_blocks), "launch_slots": int(stats.live_slots),
+                                  "large_grid": int(stats.large_grid)}}
 
     with ClockSampler(0) as clk:
         ours = serve_run(arrivals)
         # plain FIFO: one request at a time on the plain kernels, the same arrivals
         ctx = api.sa_create(0)
-        lat = []
+        lat, small = [], []
         t0 = time.perf_counter()
         for q, ta in enumerate(arrivals):
             now = time.perf_counter() - t0
@@ -603,11 +628,16 @@ def serve_part(args):
             m = pool[q % len(pool)]
             api.sa_assign_host(ctx, m, ps, 1e-6, args.max_sweeps, kernel="plain")
             lat.append(time.perf_counter() - t0 - ta)
+            small.append(m.shape[0] <= 512)
         span = time.perf_counter() - t0 - arrivals[0]
         ctx.close()
     lat = np.array(lat)
+    small = np.array(small)
     fifo = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "instances_per_s": len(lat) / span, "requests": len(lat)}
+            "instances_per_s": len(lat) / span, "requests": len(lat),
+            "small_n_le_512": {"p50_ms": float(np.percentile(lat[small], 50) * 1e3),
+                               "p99_ms": float(np.percentile(lat[small], 99) * 1e3), "requests": int(small.sum())}
+            if small.any() else None}
     return {"value": ours["instances_per_s"], "unit": "instances/s",
             "workload": f"first {len(arrivals)} requests of a Poisson {args.serve_rate:g}/s stream, "
                         f"n log-uniform [32,4096], {args.serve_dist} weights, 40 GB budget, p=1..256 (x2); "

@@ -71,8 +71,9 @@ typedef enum { SA_PREC_MIXED = 0, SA_PREC_FP32 = 1, SA_PREC_FP64 = 2 } sa_prec;
  *   K = 2^(p log2 w - C_i - V_j) once (exponent in float-pair arithmetic, log2 w to about
  *   2^-40, one SFU exp2) into a workspace of n * ceil(n/4)*4 floats, and each sweep reads K once
  *   (4 bytes per element): no per-element SFU work in the sweeps and an error that does
- *   not grow with p.  Needs n <= 24576 (above 12288 the rows are read from global
- *   memory, prefetched into L2, instead of through the shared-memory ring).
+ *   not grow with p.  The first evaluation of a call also keeps log2 w as a float pair
+ *   (8 bytes per element), which the later ones read instead of the weights.  Needs
+ *   n <= 24576 (above 12288 the shared-memory ring holds one row per stage).
  * NEWTON: the Newton variant of Sec. 5.3 (Knight-Ruiz iteration on the symmetric
  *   embedding S = [[0, A], [A^T, 0]], conjugate gradients for each Newton system).  At
  *   every p step it evaluates the same K as STEP, then iterates on K; each CG iteration
@@ -485,6 +486,13 @@ sa_status sa_batch_scale(sa_ctx* ctx, int32_t k, const void* const* d_w, const i
                          int32_t* status);
 
 /* ---- Continuous-batching server ---------------------------------------------------- */
+/* Not part of the paper: a serving layer around the same path.  Small requests (n <= 512)
+ * are scaled on a device-resident queue: the blocks of a persistent kernel take published
+ * requests one per block as they free up (the K rows form of the batched path), so a
+ * request joins the scaling already under way; a block leaves after 2 ms without a
+ * request while none is busy, and the next request starts the kernel again.  Each scaled
+ * request is then pruned, solved exactly and certified on the host side of the path.
+ * Larger requests run sa_assign on workers of their own. */
 
 typedef struct sa_server sa_server;
 
@@ -496,14 +504,21 @@ typedef struct {
     int64_t sweeps;
     int32_t status;           /* sa_status of the request */
     double t_submit, t_start, t_done;  /* seconds on the server's monotonic clock */
+    double t_scaled;          /* small requests: when the request queue had scaled it; else 0 */
 } sa_result;
 
 /* Start a server on `device` with a device-memory budget for resident requests.  Each
  * admitted request is charged an upper bound of the device memory it can hold while it
  * runs (sa_server_request_bytes), and is admitted only while the charges of the requests
- * on the device stay within hbm_budget.  Outside the budget the server holds only its
- * workers' small persistent state: per small-request worker (two) a context workspace of at
- * most 32 MiB, and a CUDA stream per worker. */
+ * on the device stay within hbm_budget.  SMs are shared the same way: a large request's
+ * scaling kernel (a cooperative grid of at most num_sms / solver_threads blocks) takes only
+ * SMs that the request queue's running blocks and the other large requests leave, and
+ * while small requests wait for the queue, the SMs of one launch of it are kept free.  The
+ * request queue's device memory (its slots of K, one 1 MiB slot per block of each of its
+ * two launch slots, at most an eighth of hbm_budget) is charged once, here; SA_E_BUDGET if
+ * hbm_budget does not exceed it.  Outside the budget the server holds only its workers'
+ * small persistent state: per small-request worker (two) a context workspace of at most
+ * 16 MiB, and a CUDA stream per worker. */
 sa_status sa_server_create(sa_server** s, int device, size_t hbm_budget, const sa_scale_opts* opts,
                            int32_t solver_threads);
 void sa_server_destroy(sa_server* s);
@@ -514,8 +529,8 @@ sa_status sa_submit(sa_server* s, const void* host_w, sa_wtype wtype, int32_t n,
 
 /* SA_PENDING until the request is done; then SA_OK (or its error) with *out filled.  Every
  * finished request's permutation is the certified optimum of its matrix, as from sa_assign
- * (small requests: batched scaling, then sa_solve_reduced_near toward v/p, the certificate
- * and its repairs; SA_E_NOT_CONVERGED if the repairs do not settle). */
+ * (small requests: scaling on the request queue, then sa_solve_reduced_near toward v/p, the
+ * certificate and its repairs; SA_E_NOT_CONVERGED if the repairs do not settle). */
 sa_status sa_poll(sa_server* s, uint64_t ticket, sa_result* out);
 void sa_result_release(sa_server* s, uint64_t ticket);
 
@@ -524,9 +539,8 @@ double sa_server_now(const sa_server* s);
 
 /* Bytes of the budget an n x n request of this weight type is charged: its matrix (16-byte
  * row pitch) plus, for n <= 512, its potentials, the reduced instance's device arrays (8
- * bytes per kept entry, at most n^2), 1 MiB and above n = 128 a batched slot of K
- * (4 * 512^2 bytes); for larger n, everything sa_assign can
- * allocate (the per-step matrix K of 4 n ceil(n/4)*4 bytes, the reduced instance's device
+ * bytes per kept entry, at most n^2) and 1 MiB; for larger n, everything sa_assign can
+ * allocate (the per-step matrix K and the log2 w pairs, 12 n ceil(n/4)*4 bytes, the reduced instance's device
  * arrays up to 8 n^2 bytes, column partials, vectors).  0 for bad arguments. */
 size_t sa_server_request_bytes(const sa_server* s, sa_wtype wtype, int32_t n);
 
@@ -535,6 +549,18 @@ size_t sa_server_request_bytes(const sa_server* s, sa_wtype wtype, int32_t n);
  * were out of memory, without allocating; the requests concerned finish with SA_E_NOMEM.
  * Process-wide; 0 clears it. */
 void sa_debug_fail_allocs(int32_t count);
+
+/* Counters of a server's request queue and its launch geometry. */
+typedef struct {
+    int64_t live_launches;      /* launches of the queue's kernel so far */
+    int64_t live_requests;      /* small requests it has scaled */
+    int64_t live_device_bytes;  /* device memory of the queue (charged at creation) */
+    int32_t live_blocks;        /* blocks per launch */
+    int32_t live_slots;         /* launches that may run at once */
+    int32_t live_capacity;      /* requests published and not yet scaled, at most */
+    int32_t large_grid;         /* grid of a large request's scaling kernel on a free GPU */
+} sa_server_stats;
+sa_status sa_server_get_stats(sa_server* s, sa_server_stats* out);
 
 #ifdef __cplusplus
 }

@@ -93,7 +93,14 @@ class sa_alg1_result(ctypes.Structure):
 class sa_result(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("perm", ctypes.POINTER(ctypes.c_int32)), ("sum_log_w", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("sweeps", ctypes.c_int64), ("status", ctypes.c_int32),
-                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("t_scaled", ctypes.c_double)]
+
+
+class sa_server_stats(ctypes.Structure):
+    _fields_ = [("live_launches", ctypes.c_int64), ("live_requests", ctypes.c_int64),
+                ("live_device_bytes", ctypes.c_int64), ("live_blocks", ctypes.c_int32),
+                ("live_slots", ctypes.c_int32), ("live_capacity", ctypes.c_int32), ("large_grid", ctypes.c_int32)]
 
 
 _lib = None
@@ -143,6 +150,7 @@ SIGNATURES = {
     "sa_server_now": (ctypes.c_double, [_VP]),
     "sa_server_request_bytes": (ctypes.c_size_t, [_VP, ctypes.c_int, ctypes.c_int32]),
     "sa_debug_fail_allocs": (None, [ctypes.c_int32]),
+    "sa_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(sa_server_stats)]),
 }
 
 

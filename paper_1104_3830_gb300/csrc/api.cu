@@ -60,7 +60,7 @@ size_t assign_device_bound(int num_sms, int n) {
     const size_t nn = (size_t)n;
     const size_t ldk = align_up(nn, 4);
     const size_t npad = align_up(nn, 32);
-    return 4 * nn * ldk                        // K (STEP, NEWTON)
+    return 12 * nn * ldk                       // K and the log2 pairs of w (STEP; NEWTON: K)
            + 8 * nn * nn                       // prune: device column and weight arrays
            + 2 * (size_t)num_sms * npad * 4    // column partials, two blocks per SM
            + 512 * nn                          // per-row and per-column vectors of every stage

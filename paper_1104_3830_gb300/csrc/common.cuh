@@ -194,11 +194,6 @@ __device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, unsign
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
-// Bulk prefetch of [src, src + bytes) from global memory into L2 (16-byte aligned, bytes a
-// multiple of 16); no completion to wait for.
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }

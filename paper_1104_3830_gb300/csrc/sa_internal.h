@@ -194,13 +194,46 @@ sa_status auction_device(sa_ctx* ctx, int n, const int64_t* d_rp, const int32_t*
                          double eps0, double eps_final, int64_t max_rounds, double* d_price, int* d_assigned,
                          int* phases, int64_t* rounds, int* complete);
 
+// serve_live.cu: the server's device-resident queue of small requests (n <= 512).
+// Ring entry of one request, in host-mapped memory.
+struct LiveDesc {
+    const void* w;     // device matrix, n x ld elements
+    double* u;         // device FP64[n] outputs (natural units)
+    double* v;
+    int64_t ld;
+    int32_t n;
+    int32_t i16;       // weights are int16 (else int32)
+};
+struct LiveArgs {
+    const LiveDesc* desc;   // host-mapped [cap]
+    const unsigned* tail;   // host-mapped: requests published
+    const unsigned* stop;   // host-mapped: nonzero ends the kernel
+    unsigned* claimed;      // host-mapped [cap]: q + 1 once request q is claimed
+    unsigned* done;         // host-mapped [cap]: q + 1 once request q is scaled
+    int32_t* sweeps;        // host-mapped [cap]
+    int32_t* status;        // host-mapped [cap]: 0 ok, 1 a step hit its cap, -6 non-finite
+    unsigned* head;         // device: requests claimed
+    unsigned* busy;         // device: blocks scaling a request
+    unsigned cap;
+    const double* P;        // device schedule
+    int n_p;
+    double tol;
+    int max_sweeps;
+    float* kscr;            // device: a slot of K per block
+    size_t kscr_floats;     // floats per slot (live_slot_floats())
+    uint64_t idle_ns;       // a block leaves after this long without a request
+};
+size_t live_slot_floats();
+sa_status live_launch(const LiveArgs& args, int grid, cudaStream_t st);
+
 // csr helpers (api.cu)
 sa_status csr_alloc(sa_csr* c, int n, int64_t nnz);
 
 // Upper bound of the device memory sa_assign allocates for an n x n matrix besides the
 // matrix itself, on a device of num_sms SMs: the largest scaling workspace (the per-step
-// matrix K, 4 n ceil(n/4)*4 bytes, of the STEP and NEWTON kernels; column partials of up
-// to two blocks per SM), the prune's device CSR arrays (8 bytes per kept entry, at most
+// matrix K of the STEP and NEWTON kernels and the STEP kernel's log2 w pairs, 12 n
+// ceil(n/4)*4 bytes; column partials of up to two blocks per SM), the prune's device CSR
+// arrays (8 bytes per kept entry, at most
 // n^2 when the re-prune reaches t = 0), the potentials and the certificate's buffers.
 size_t assign_device_bound(int num_sms, int n);
 // Give a context's device buffers (workspace, input copy, warm-start copy) back to the

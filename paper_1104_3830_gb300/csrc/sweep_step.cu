@@ -6,7 +6,10 @@
 // once, with the exponent formed in float-pair arithmetic (log2 w to about 2^-40 from a
 // 256-entry shared table and a series; exact two-product and two-sums), one SFU exp2, and
 // stores K as FP32 in a global workspace.  K is the iterate X(p) at the step start, so every entry is
-// in [0, ~1] and its relative error (about 2e-7) does not grow with p.  Within the step
+// in [0, ~1] and its relative error (about 2e-7) does not grow with p.  The launch's first
+// evaluation also stores log2 w as a float pair (two FP32 planes); the later ones read the
+// pairs (8 bytes per entry, no table lookups or series) and are bound by memory, not by
+// the arithmetic of the logarithm.  Within the step
 // the potentials move only through a column factor c_j = 2^(Vs_j - V_j) (Vs = V at the
 // step start) and the fresh row sums, so a sweep is
 //     s_i  = sum_j K_ij c_j,     S_j = c_j sum_i K_ij / s_i,     V_j += log2 S_j
@@ -25,6 +28,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "common.cuh"
 #include "log2pair.cuh"
@@ -40,11 +44,6 @@ namespace {
 
 constexpr int kStepNred = 4;      // row-sum publication buffers
 constexpr int kStepMaxRing = 16;  // ring slots at most; a slot holds one stage (two rows)
-// direct mode: a bulk L2 prefetch of the stage being read starts its rows' transfer while
-// the threads' own loads are issued.  Prefetching further ahead measured slower (690 against
-// 487 us per sweep at n = 20000 for four stages ahead): it evicts rows that are still to
-// be re-read for the column accumulation.
-constexpr int kStepPrefetch = 0;
 // rows per ring stage of the dense ring mode.  A stage costs a fixed ~0.5 us (the
 // publication of the warps' partial row sums and the slot's release) plus ~0.4 us per row
 // at n = 8192, so two-row stages beat one-row stages (34.7 against 47.7 us per row pass)
@@ -57,6 +56,8 @@ struct StepArgs {
     int64_t ld;            // elements
     int i16;               // weights are int16 (else int32)
     float* K;              // n x ldk, FP32
+    float* Lh;             // n x ldk: log2 w as a float pair (head, tail; -inf head: w = 0),
+    float* Ll;             //   written by the launch's first evaluation of K, read by the others
     int64_t ldk;           // floats, multiple of 4
     unsigned row_bytes;    // bytes copied per K row (multiple of 16)
     int ring;              // ring slots of a dense epoch (>= 4)
@@ -169,10 +170,9 @@ struct KahanS {
     }
 };
 
-// SP: sparse epochs possible.  DIR: rows too wide for a shared-memory ring (n > 12288) are
-// read straight from global memory (with a bulk L2 prefetch of the stage being read) and
-// re-read from L2 for the column accumulation.
-template <int NT, int CH, bool SP, bool DIR, int RPS>
+// SP: sparse epochs possible.  RPS: rows per ring stage (one for rows of more than 48 KB,
+// whose ring has two slots).
+template <int NT, int CH, bool SP, int RPS>
 __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     constexpr int NW = NT / 32;
     constexpr int M = CH * 4;   // columns owned per thread (dense mode)
@@ -274,11 +274,6 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
         else
             bulk_g2s_hint(sbase + (size_t)slot * slot_bytes, src, bytes, &mbar[slot], l2_policy_evict_first());
     };
-    auto prefetch_stage = [&](int g) {   // one thread: the K rows of stage g into L2
-        const int q0 = RPS * g;
-        const int nr = min(RPS, nrows - q0);
-        if (nr > 0) bulk_prefetch_l2(kbase + (size_t)(r0 + q0) * kpitch, (unsigned)nr * A.row_bytes);
-    };
     auto release_index = [&](uint32_t v) {   // lane 0 after __syncwarp
         const uint32_t slot = v % (uint32_t)ring_n;
         const unsigned old = atom_add_acq_rel(&rel_cnt[slot], 1u);
@@ -321,7 +316,10 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     // [2^-(cscale log2 n + the range of the row), 1] and no per-row maximum pass is needed.
     // cscale = 0: the references are the FP32 row maxima (a cold start, a kept v, a
     // re-evaluation within a step).
-    auto prep = [&](double p, double cscale) {
+    // FRESH (the launch's first evaluation): log2 w of every entry is formed from the
+    // weights and stored as a float pair in Lh, Ll; later evaluations read the pairs back.
+    auto prep = [&](double p, double cscale, auto fresh) {
+        constexpr bool FRESH = decltype(fresh)::value;
         const float pf = (float)p;
         // the region is idle: stage V there as the FP32 head and tail of each entry, in two
         // arrays, so that a thread reads its four columns with one 16-byte load from each
@@ -343,8 +341,8 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
         bool overflow = false;
         // the weights of row q + 1 are loaded while row q is evaluated (up to eight chunks a
         // thread: wider rows would spill the second set of registers)
-        constexpr bool PREF = CH <= 8;
-        int wv[M], wn[PREF ? M : 1];
+        constexpr bool PREF = FRESH && CH <= 8;
+        int wv[FRESH ? M : 1], wn[PREF ? M : 1];
         auto load_row = [&](int q, int* dst) {
 #pragma unroll
             for (int k = 0; k < CH; ++k) {
@@ -357,11 +355,28 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
         if (PREF) load_row(0, wn);
         for (int q = 0; q < nrows; ++q) {
             const int64_t row = r0 + q;
+            // the row's log2 pairs, every chunk's loads issued before the first is used (the
+            // stores of K below could alias them for the compiler, which then keeps the
+            // loads behind the stores)
+            float4 lh4[FRESH ? 1 : CH], ll4[FRESH ? 1 : CH];
+            if constexpr (!FRESH) {
+                const float* lhr = A.Lh + row * A.ldk;
+                const float* llr = A.Ll + row * A.ldk;
+#pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    lh4[k] = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+                    ll4[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if (nval[k] > 0) {
+                        lh4[k] = __ldcs((const float4*)(lhr + cidx[k] * 4));
+                        ll4[k] = __ldcs((const float4*)(llr + cidx[k] * 4));
+                    }
+                }
+            }
             if (PREF) {
 #pragma unroll
                 for (int x = 0; x < M; ++x) wv[x] = wn[PREF ? x : 0];
                 load_row(q + 1, wn);
-            } else {
+            } else if (FRESH) {
                 load_row(q, wv);
             }
             double cref;
@@ -376,10 +391,18 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                     if (nval[k] == 0) continue;
                     const float4 vh4 = *(const float4*)(vhi + cidx[k] * 4);
                     const float vh[4] = {vh4.x, vh4.y, vh4.z, vh4.w};
+                    if constexpr (FRESH) {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (e < nval[k] && wv[4 * k + e] > 0)
-                            mloc = fmaxf(mloc, fmaf(pf, lg2_approx((float)wv[4 * k + e]), -vh[e]));
+                        for (int e = 0; e < 4; ++e)
+                            if (e < nval[k] && wv[4 * k + e] > 0)
+                                mloc = fmaxf(mloc, fmaf(pf, lg2_approx((float)wv[4 * k + e]), -vh[e]));
+                    } else {
+                        const float4 l4 = lh4[FRESH ? 0 : k];
+                        const float lh[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (lh[e] > -INFINITY) mloc = fmaxf(mloc, fmaf(pf, lh[e], -vh[e]));
+                    }
                 }
                 mloc = warp_max(mloc);
                 float* smx = (float*)redd;
@@ -409,14 +432,35 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                     vh[0] = h4.x; vh[1] = h4.y; vh[2] = h4.z; vh[3] = h4.w;
                     vl[0] = l4.x; vl[1] = l4.y; vl[2] = l4.z; vl[3] = l4.w;
                 }
+                // log2 w of the chunk's entries as float pairs (-inf: no entry)
+                float lh[4], ll[4];
+                if constexpr (FRESH) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        lh[e] = -INFINITY;
+                        ll[e] = 0.0f;
+                        if (e < nval[k] && wv[4 * k + e] > 0) {
+                            const float2 lw = wlog2(s_l2tab, wv[4 * k + e]);
+                            lh[e] = lw.x;
+                            ll[e] = lw.y;
+                        }
+                    }
+                    if (cidx[k] < NC) {
+                        *(float4*)(A.Lh + row * A.ldk + cidx[k] * 4) = make_float4(lh[0], lh[1], lh[2], lh[3]);
+                        *(float4*)(A.Ll + row * A.ldk + cidx[k] * 4) = make_float4(ll[0], ll[1], ll[2], ll[3]);
+                    }
+                } else {
+                    const float4 h4 = lh4[FRESH ? 0 : k], l4 = ll4[FRESH ? 0 : k];
+                    lh[0] = h4.x; lh[1] = h4.y; lh[2] = h4.z; lh[3] = h4.w;
+                    ll[0] = l4.x; ll[1] = l4.y; ll[2] = l4.z; ll[3] = l4.w;
+                }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int x = 4 * k + e;
-                    if (e < nval[k] && wv[x] > 0) {
+                    if (lh[e] > -INFINITY) {
                         // x = p log2 w - V_j - m with 48-bit operands: the large leading
                         // parts cancel exactly (two-product, two-sums), the small ones are
                         // added after; x is then exact to about 2^-24 |x|
-                        const float2 lw = wlog2(s_l2tab, wv[x]);
+                        const float2 lw = make_float2(lh[e], ll[e]);
                         const float2 vj = make_float2(vh[e], vl[e]);
                         const float t = ph * lw.x;
                         const float te = fmaf(ph, lw.x, -t);
@@ -483,6 +527,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
         __syncthreads();
     };
 
+    bool l_ready = false;   // this launch has stored its stripe's log2 pairs
     for (int k = A.k0; k < A.n_p; ++k) {
         const double p = A.P[k];
         int sweeps = 0;
@@ -508,7 +553,15 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
             }
             // the first evaluation of a step after a step (or a resumed one) scaled (u, v):
             // row references from U; otherwise the row maxima
-            prep(p, (k > 0 && !A.keep_v && step_reanchors == 0) ? p / A.P[k - 1] : 0.0);
+            {
+                const double cs = (k > 0 && !A.keep_v && step_reanchors == 0) ? p / A.P[k - 1] : 0.0;
+                if (l_ready) {
+                    prep(p, cs, std::false_type{});
+                } else {
+                    prep(p, cs, std::true_type{});
+                    l_ready = true;
+                }
+            }
             if (!gsync()) { drain(); return; }
             // mode of this epoch, identical in every block
             if (tid == 0) {
@@ -545,10 +598,8 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 for (int m = 0; m < M; ++m) cf[m] = (m % 4) < nval[m / 4] ? 1.0f : 0.0f;
             }
             __syncthreads();
-            if (!DIR && tid == 0 && nrows > 0)
+            if (tid == 0 && nrows > 0)
                 for (uint32_t v = 0; v < (uint32_t)ring_n; ++v) issue_index(v);
-            if (DIR && tid == 0)
-                for (int g = 0; g < min(kStepPrefetch, nst); ++g) prefetch_stage(stage_of((uint32_t)g));   // none at 0
             bool done = false, reanchor = false;
             while (!done && !reanchor) {
                 SA_STEP_STAMP(0);
@@ -560,7 +611,6 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 // normalised rows into the column sums, release the slots.
                 // row r (0, 1) of the stage at ring index v
                 auto row_of = [&](uint32_t v, int q0, int r) -> const unsigned char* {
-                    if (DIR) return kbase + (size_t)(r0 + q0 + r) * kpitch;
                     const unsigned char* base = sbase + (size_t)(v % (uint32_t)ring_n) * slot_bytes;
                     if (r == 0) return base;
                     return base + ((SP && sparse) ? rowlen[q0] * 8u : A.row_bytes);
@@ -592,11 +642,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                     const int q0 = RPS * stage_of(v);
                     const bool two = RPS == 2 && q0 + 1 < nrows;
                     const uint32_t rn = (uint32_t)ring_n;
-                    if (DIR) {
-                        // rows of stage g + P into L2 (the stage after the last wraps to the
-                        // next sweep's first)
-                        if (tid == 0) prefetch_stage(stage_of(v + kStepPrefetch));
-                    } else if (!mbar_wait(&mbar[v % rn], (v / rn) & 1u, A.err, A.wait_ns)) {
+                    if (!mbar_wait(&mbar[v % rn], (v / rn) & 1u, A.err, A.wait_ns)) {
                         s_flag = 1;   // this thread's copy is not in: its warp never releases the slot
                     }
                     const float sp0 = row_partial(row_of(v, q0, 0), q0);
@@ -667,16 +713,26 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                             S[4 * kk + 3] = fmaf(kv.w, inv, S[4 * kk + 3]);
                         }
                     }
-                    if (!DIR) {
-                        __syncwarp();
-                        if (lane == 0) release_index(v);
-                    }
+                    __syncwarp();
+                    if (lane == 0) release_index(v);
                     return true;
                 };
-                if (nst > 0) produce(0);
-                for (int g = 0; g < nst; ++g) {
-                    if (g + 1 < nst) produce(g + 1);
-                    if (!consume(g)) break;
+                // With three or more ring stages the partial row sums of stage g + 1 are
+                // formed while the other warps' partials of stage g are still arriving.  A
+                // two-stage ring (rows too wide for more) cannot look ahead: the slot of g + 1
+                // is refilled only when g + 1 - 2 is released, so each stage is consumed first
+                // and its copy for g + 2 is in flight while the next stage is read.
+                if ((SP && sparse) || ring_n > 2) {
+                    if (nst > 0) produce(0);
+                    for (int g = 0; g < nst; ++g) {
+                        if (g + 1 < nst) produce(g + 1);
+                        if (!consume(g)) break;
+                    }
+                } else {
+                    for (int g = 0; g < nst; ++g) {
+                        produce(g);
+                        if (!consume(g)) break;
+                    }
                 }
                 __syncthreads();
                 SA_STEP_STAMP(1);
@@ -821,7 +877,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
 
 struct StepCfg {
     int nt, ch, ring;
-    bool direct;
+    int rps;   // rows per ring stage
 };
 
 size_t step_smem_bytes(int nt, size_t region_bytes, int max_rows) {
@@ -840,28 +896,25 @@ int step_max_rows(const sa_ctx* ctx, int n) {
 
 StepCfg pick_step(const sa_ctx* ctx, int n) {
     const int nc = (n + 3) / 4;
-    StepCfg c{0, 0, 0, false};
-    if (nc <= 128) c = {128, 1, 0, false};
-    else if (nc <= 256) c = {256, 1, 0, false};
-    else if (nc <= 512) c = {512, 1, 0, false};
-    else if (nc <= 1024) c = {512, 2, 0, false};
-    else if (nc <= 2048) c = {512, 4, 0, false};
-    else if (nc <= 3072) c = {512, 6, 0, false};
-    else if (nc <= 4096) c = {512, 8, 0, true};
-    else if (nc <= 5120) c = {512, 10, 0, true};
-    else if (nc <= 6144) c = {512, 12, 0, true};
+    const int R = kDenseRowsPerStage;
+    StepCfg c{0, 0, 0, R};
+    if (nc <= 128) c = {128, 1, 0, R};
+    else if (nc <= 256) c = {256, 1, 0, R};
+    else if (nc <= 512) c = {512, 1, 0, R};
+    else if (nc <= 1024) c = {512, 2, 0, R};
+    else if (nc <= 2048) c = {512, 4, 0, R};
+    else if (nc <= 3072) c = {512, 6, 0, R};
+    else if (nc <= 4096) c = {512, 8, 0, 1};
+    else if (nc <= 5120) c = {512, 10, 0, 1};
+    else if (nc <= 6144) c = {512, 12, 0, 1};
     else return c;
     const unsigned row_bytes = (unsigned)align_up((size_t)n * 4, 16);
     const int max_rows = step_max_rows(ctx, n);
-    if (c.direct) {
-        // no ring: the region only stages V (8 ceil(n/4)*4 bytes) while K is evaluated
-        if (step_smem_bytes(c.nt, align_up((size_t)nc * 32, 16), max_rows) <= ctx->smem_optin) return c;
-        c.nt = 0;
-        return c;
-    }
-    // the ring doubles as scratch for V (8 ceil(n/4)*4 bytes) during the per-step evaluation
-    for (int ring = 8; ring >= 4; --ring) {
-        if ((size_t)ring * row_bytes < (size_t)nc * 32) break;
+    // ring slots in rows: two-row stages up to 48 KB rows, else one-row stages (rows of 48
+    // to 96 KB: two or three of them fit).  The ring doubles as scratch for V (8 ceil(n/4)*4
+    // bytes = two rows) during the per-step evaluation of K.
+    const int rmax = c.rps == 1 ? 3 : 8, rmin = c.rps == 1 ? 2 : 4;
+    for (int ring = rmax; ring >= rmin; --ring) {
         if (step_smem_bytes(c.nt, (size_t)ring * row_bytes, max_rows) <= ctx->smem_optin) {
             c.ring = ring;
             return c;
@@ -871,11 +924,15 @@ StepCfg pick_step(const sa_ctx* ctx, int n) {
     return c;
 }
 
-template <int NT, int CH, bool DIR>
+template <int NT, int CH, int RPS = kDenseRowsPerStage>
 sa_status launch_step(sa_ctx* ctx, const StepArgs& args, size_t smem, int* grid_out) {
-    // the dense-only instantiation carries none of the sparse code
-    auto kern = (!DIR && args.sparse_ok) ? step_kernel<NT, CH, !DIR, DIR, 2>
-                                         : step_kernel<NT, CH, false, DIR, DIR ? 2 : kDenseRowsPerStage>;
+    // the dense-only instantiation carries none of the sparse code (sparse epochs need
+    // two-row stages)
+    void (*kern)(StepArgs);
+    if constexpr (RPS == 2)
+        kern = args.sparse_ok ? step_kernel<NT, CH, true, 2> : step_kernel<NT, CH, false, 2>;
+    else
+        kern = step_kernel<NT, CH, false, RPS>;
     SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
@@ -894,7 +951,7 @@ sa_status launch_step(sa_ctx* ctx, const StepArgs& args, size_t smem, int* grid_
     *grid_out = G;
     StepArgs a = args;
     // stages of each stripe that stay L2-resident: the context's byte budget over the grid
-    const size_t stage_bytes = (size_t)(DIR || args.sparse_ok ? 2 : kDenseRowsPerStage) * args.row_bytes;
+    const size_t stage_bytes = (size_t)RPS * args.row_bytes;
     const size_t keep = ctx->step_l2_bytes / ((size_t)G * stage_bytes);
     a.l2_keep_stages = (int)std::min<size_t>(keep, (size_t)args.n);
     void* params[] = {&a};
@@ -921,7 +978,7 @@ size_t step_workspace_bytes(const sa_ctx* ctx, const sa_matrix* a, int n_p) {
     const int G_max = ctx->num_sms * 2;
     const size_t npad = align_up((size_t)n, 32);
     const size_t recs = ctx->step_sparse ? (size_t)n * step_rec_cap_row(n) : 2;
-    return (size_t)n * ldk * 4 + recs * 8 + (size_t)G_max * npad * 4 +
+    return (size_t)n * ldk * 12 + recs * 8 + (size_t)G_max * npad * 4 +
            2 * align_up((size_t)n * 8, 256) + align_up((size_t)n * 4, 256) + (size_t)n_p * 16 + 32768;
 }
 
@@ -941,6 +998,8 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     if (rc) return rc;
     Carve cv(ctx->ws.ptr);
     float* K = cv.take<float>((size_t)n * ldk);
+    float* Lh = cv.take<float>((size_t)n * ldk);
+    float* Ll = cv.take<float>((size_t)n * ldk);
     const int64_t rec_cap_row = ctx->step_sparse ? step_rec_cap_row(n) : 0;
     uint2* rec = cv.take<uint2>(ctx->step_sparse ? (size_t)n * rec_cap_row : 2);
     float* part = cv.take<float>((size_t)G_max * npad);
@@ -974,7 +1033,7 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     } else if (!o->warm_keep_v) {
         launch_scale_vec(V, n, o->p[k0] / o->p[k0 - 1], st);
     }
-    const size_t region = cfg.direct ? align_up((size_t)((n + 3) / 4) * 32, 16) : (size_t)cfg.ring * align_up((size_t)n * 4, 16);
+    const size_t region = (size_t)cfg.ring * align_up((size_t)n * 4, 16);
     const size_t cs_bytes = align_up((size_t)n * 8, 16);
     StepArgs args{};
     args.w = a->w;
@@ -982,6 +1041,8 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     args.ld = a->ld;
     args.i16 = a->wtype == SA_I16;
     args.K = K;
+    args.Lh = Lh;
+    args.Ll = Ll;
     args.ldk = ldk;
     args.row_bytes = (unsigned)align_up((size_t)n * 4, 16);
     args.ring = cfg.ring;
@@ -994,7 +1055,7 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     // a sparse epoch's ring (next to c and S) needs >= 3 slots of its longest stage: two in
     // use and one in flight
     args.sparse_row_cap = region > cs_bytes ? (unsigned)(((region - cs_bytes) / (3 * 8)) & ~(size_t)1) : 0u;
-    args.sparse_ok = ctx->step_sparse && !cfg.direct && args.sparse_row_cap >= 2;
+    args.sparse_ok = ctx->step_sparse && cfg.rps == 2 && args.sparse_row_cap >= 2;
     args.sparse_max_total = (unsigned long long)n * (unsigned long long)n / 4ull;
     // dropped entries of a row sum to at most n * theta * (max c / min c) of its mass
     // (the largest entry of K in a row is about 1): n * 2^-70 * 2^20 <= 2^-36 for n <= 2^14
@@ -1026,15 +1087,15 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     SA_CUDA(cudaEventCreate(&ev0));
     SA_CUDA(cudaEventCreate(&ev1));
     SA_CUDA(cudaEventRecord(ev0, st));
-    if (cfg.nt == 128) rc = launch_step<128, 1, false>(ctx, args, smem, &G);
-    else if (cfg.nt == 256) rc = launch_step<256, 1, false>(ctx, args, smem, &G);
-    else if (cfg.ch == 1) rc = launch_step<512, 1, false>(ctx, args, smem, &G);
-    else if (cfg.ch == 2) rc = launch_step<512, 2, false>(ctx, args, smem, &G);
-    else if (cfg.ch == 4) rc = launch_step<512, 4, false>(ctx, args, smem, &G);
-    else if (cfg.ch == 6) rc = launch_step<512, 6, false>(ctx, args, smem, &G);
-    else if (cfg.ch == 8) rc = launch_step<512, 8, true>(ctx, args, smem, &G);
-    else if (cfg.ch == 10) rc = launch_step<512, 10, true>(ctx, args, smem, &G);
-    else rc = launch_step<512, 12, true>(ctx, args, smem, &G);
+    if (cfg.nt == 128) rc = launch_step<128, 1>(ctx, args, smem, &G);
+    else if (cfg.nt == 256) rc = launch_step<256, 1>(ctx, args, smem, &G);
+    else if (cfg.ch == 1) rc = launch_step<512, 1>(ctx, args, smem, &G);
+    else if (cfg.ch == 2) rc = launch_step<512, 2>(ctx, args, smem, &G);
+    else if (cfg.ch == 4) rc = launch_step<512, 4>(ctx, args, smem, &G);
+    else if (cfg.ch == 6) rc = launch_step<512, 6>(ctx, args, smem, &G);
+    else if (cfg.ch == 8) rc = launch_step<512, 8, 1>(ctx, args, smem, &G);
+    else if (cfg.ch == 10) rc = launch_step<512, 10, 1>(ctx, args, smem, &G);
+    else rc = launch_step<512, 12, 1>(ctx, args, smem, &G);
     if (rc) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); return rc; }
     SA_CUDA(cudaEventRecord(ev1, st));
     sa_status prc = ctx->pinned.reserve(4096 + (size_t)o->n_p * 16);

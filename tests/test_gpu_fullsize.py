@@ -12,8 +12,9 @@ not with the library's own FP64 check:
   of the result by ``oracle.sums`` (Sec. 4.2: the result is eps-bistochastic), the
   planted permutation carrying the mass (X(p) tends to the optimal permutation matrix,
   Sec. 3.1), and the exact optimum of ``sa_assign`` against the planted optimum.
-* n = 20000 (ten chunks per thread, rows read from global memory): X(p) entry by entry
-  against ``oracle.sinkhorn`` at p = 1, 2 and the FP64 sums by ``oracle.sums``.
+* n = 20000 (ten chunks per thread, rows of 80 KB through a ring of two one-row stages):
+  X(p) entry by entry against ``oracle.sinkhorn`` at p = 1, 2 and the FP64 sums by
+  ``oracle.sums``.
 
 Tolerances: as in the other step-kernel tests, entries within 8e-6 max(x, 1/n) of the
 oracle's (both sides stop within tol = 1e-6 of bistochastic, measured on different sums)
@@ -115,7 +116,7 @@ def test_c2_tied_variant(ctx):
     assert oracle.perm_weight_exact(w, res["perm"]) == oracle.perm_weight_exact(w, pi)
 
 
-def test_c3_direct_rows_match_oracle(ctx):
+def test_c3_wide_rows_match_oracle(ctx):
     """n = 20000, int16 weights uniform in [1, 32767] (the precision workload's matrix)."""
     w, _ = W.c3()
     b = oracle.log_weights(w.astype(np.int64))

@@ -1,6 +1,6 @@
 """The continuous-batching server (sa_submit / sa_poll): results of a mixed stream equal
-those of each request solved alone (exact optimum, same product), and the budget is
-enforced."""
+those of each request solved alone (exact optimum, same product), the budget is enforced,
+and small requests join the device-resident queue's running kernel."""
 import ctypes
 import time
 
@@ -83,12 +83,13 @@ def test_mixed_stream_is_exact_and_matches_alone(lib):
 def test_budget_is_enforced(lib):
     h, o = make_server(lib, 256 << 20, [1.0, 2.0])
     try:
-        # n = 8192 is charged about 14 n^2 bytes (matrix, K, reduced arrays): over 256 MiB
+        # n = 8192 is charged about 22 n^2 bytes (matrix, K, log2 pairs, reduced arrays):
+        # over 256 MiB
         assert lib.sa_server_request_bytes(h, L.SA_I16, 8192) > 256 << 20
         big = W.uniform(8192, 1, 1000, 5, dtype=np.int16)
         st, _ = submit(lib, h, big)
         assert st == L.SA_E_BUDGET
-        # n = 2000: about 61 MiB each, admitted a few at a time
+        # n = 2000: about 90 MiB each, admitted a few at a time
         charge = lib.sa_server_request_bytes(h, L.SA_I16, 2000)
         assert 2000 * 2000 * 2 < charge < 256 << 20
         ok = W.uniform(2000, 1, 1000, 6, dtype=np.int16)
@@ -166,5 +167,81 @@ def test_allocation_failure_fails_each_request(lib):
             assert st == 0
             b = oracle.log_weights(m.astype(np.int64))
             assert oracle.perm_weight_exact(m, perm) == oracle.perm_weight_exact(m, oracle.hungarian(b)[0])
+    finally:
+        lib.sa_server_destroy(h)
+
+
+def stats(lib, h):
+    st = L.sa_server_stats()
+    L.check(lib.sa_server_get_stats(h, ctypes.byref(st)))
+    return st
+
+
+def test_small_requests_join_the_running_queue(lib):
+    """Small requests published while the request queue's kernel is scaling a long one are
+    taken by its idle blocks at once: each finishes before the long one, all on the same
+    launch, with certified optima.  After the queue has been idle its kernel ends, and the
+    next request starts it again."""
+    ps = [2.0 ** k for k in range(15)]
+    h, o = make_server(lib, 1 << 30, ps, sweeps=20000)
+    try:
+        # uniform weights on a wide range at p up to 2^14: thousands of sweeps per step
+        slow = W.uniform(300, 1, 30000, 3300, dtype=np.int16)
+        # equal row and column sums at every p: one sweep per step
+        fast = []
+        for n in (40, 64, 100, 200, 333):
+            m = np.ones((n, n), dtype=np.int16)
+            np.fill_diagonal(m, 1000)
+            fast.append(m)
+        st, t_slow = submit(lib, h, slow)
+        assert st == 0
+        t0 = time.time()
+        while stats(lib, h).live_launches < 1:
+            assert time.time() - t0 < 10
+            time.sleep(0.001)
+        time.sleep(0.005)
+        tf = [submit(lib, h, m)[1] for m in fast]
+        res_fast = [wait(lib, h, t) for t in tf]
+        st_slow, perm_slow, r_slow = wait(lib, h, t_slow)
+        assert st_slow == 0
+        for m, (st, perm, r) in zip(fast, res_fast):
+            assert st == 0
+            assert np.array_equal(perm, np.arange(m.shape[0]))   # the heavy diagonal
+            assert r.t_done < r_slow.t_done, (r.t_done, r_slow.t_done)
+            assert r.t_start <= r.t_scaled <= r.t_done
+        b = oracle.log_weights(slow.astype(np.int64))
+        assert oracle.perm_weight_exact(slow, perm_slow) == oracle.perm_weight_exact(slow, oracle.hungarian(b)[0])
+        s1 = stats(lib, h)
+        assert s1.live_launches == 1, s1.live_launches
+        assert s1.live_requests == 1 + len(fast)
+        # idle: every block leaves; the next request launches the kernel again
+        time.sleep(0.1)
+        st, t = submit(lib, h, fast[0])
+        assert wait(lib, h, t)[0] == 0
+        s2 = stats(lib, h)
+        assert s2.live_launches == 2 and s2.live_requests == 2 + len(fast)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert s2.live_device_bytes > 0 and 2 * s2.large_grid <= sms and s2.live_slots * s2.live_blocks <= sms
+    finally:
+        lib.sa_server_destroy(h)
+
+
+def test_large_request_after_the_queue_went_idle(lib):
+    """The request queue's launch takes every SM the large requests leave; once its
+    requests are done and its kernel has left, a large request gets its full grid back
+    (the SMs of an ended launch are counted free even when nothing else is in flight)."""
+    ps = [2.0 ** k for k in range(5)]
+    h, o = make_server(lib, 4 << 30, ps)
+    try:
+        small = [W.uniform(n, 1, 1000, 3400 + n, dtype=np.int16) for n in (50, 120, 300)]
+        for t in [submit(lib, h, m)[1] for m in small]:
+            assert wait(lib, h, t, timeout=60)[0] == 0
+        time.sleep(0.05)   # the queue's kernel leaves after 2 ms without requests
+        large = W.uniform(700, 1, 1000, 3410, dtype=np.int16)
+        st, t = submit(lib, h, large)
+        st, perm, r = wait(lib, h, t, timeout=60)
+        assert st == 0
+        b = oracle.log_weights(large.astype(np.int64))
+        assert oracle.perm_weight_exact(large, perm) == oracle.perm_weight_exact(large, oracle.hungarian(b)[0])
     finally:
         lib.sa_server_destroy(h)

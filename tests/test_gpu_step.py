@@ -158,8 +158,9 @@ def max_x_deviation(b, p, u1, v1, u2, v2, rows=512):
 
 
 def test_largest_supported_width(ctx):
-    """n = 12288 (six chunks of four columns per thread, the widest ring configuration):
-    X(p) entry by entry against the oracle and its FP64 sums by the oracle."""
+    """n = 12288 (six chunks of four columns per thread, the widest ring of two-row stages:
+    two stages, each consumed before the next is read): X(p) entry by entry against the
+    oracle and its FP64 sums by the oracle."""
     n = 12288
     w = W.uniform(n, 1, 1000, 85, dtype=np.int16)
     d = api.to_device(w)
@@ -175,11 +176,13 @@ def test_largest_supported_width(ctx):
 
 
 @pytest.mark.parametrize("n", [12290, 22000])
-def test_direct_rows_wide_instances(ctx, n):
-    """Rows wider than the ring (read from global memory with L2 prefetch), a ragged width
-    (eight chunks per thread) and n = 22000 (twelve, the widest), int16 weights in
-    [1, 32767], p = 1, 2, 4: X(p) entry by entry against the oracle and its FP64 sums by the
-    oracle (n = 20000, ten chunks, runs in the full-size tests)."""
+def test_wide_rows_one_row_stages(ctx, n):
+    """Rows of more than 48 KB run through a ring of one-row stages: a ragged width
+    n = 12290 (eight chunks per thread, three slots, partial row sums formed one stage
+    ahead) and n = 22000 (twelve chunks, the widest; two slots, each stage consumed before
+    the next is read), int16 weights in [1, 32767], p = 1, 2, 4: X(p) entry by entry against
+    the oracle and its FP64 sums by the oracle (n = 20000, ten chunks, runs in the
+    full-size tests)."""
     w = W.uniform(n, 1, 32767, 86, dtype=np.int16)
     d = api.to_device(w)
     ps = [1.0, 2.0, 4.0]
