@@ -57,13 +57,23 @@ def load_peaks():
 # capture was taken on: after any change to these files the figure is unknown (null).
 _TRAFFIC = {
     # step kernel: planted n=8192 int16, p=256 from a cold start, 200 sweeps + 1 evaluation of K
-    (3, 8192, 2): ((35.384280e9 + 0.372369e9) / 200, "ncu capture, planted n=8192 int16, p=256, 200 sweeps (one launch)",
+    (3, 8192, 2): ((37.085797e9 + 0.888429e9) / 200, "ncu capture, planted n=8192 int16, p=256, 200 sweeps (one launch)",
                    {"paper_1104_3830_gb300/csrc/sweep_step.cu":
-                    "76d10c7b1e71b17d886f9047d070f70e3a8f6f16dc559a3c6836a6f90d973936",
+                    "4f076eba500b3495da505af5705efdafabe0bbbf03e6cd1692e3ae97fa7e06fb",
                     "paper_1104_3830_gb300/csrc/common.cuh":
-                    "4b6aa6ba726fa5247da3513bd0bad787ec298c0fe61dc55d64ebfc82c49bd063",
+                    "081ba7d34dae961c3679ac9acf1c076fd6b30bb4428eb03eabf3ad582049a6cc",
                     "paper_1104_3830_gb300/csrc/log2pair.cuh":
                     "d0d997e23dba7b51d1c07b556aa6d5e60d23cf230a79b17de392b2f3074ae3d0"}),
+    # step kernel: uniform n=20000 int16, the whole p = 1..256 schedule (28 sweeps, 9 evaluations
+    # of K) of one scaling call, per sweep
+    (3, 20000, 2): ((69.191562e9 + 17.739943e9) / 28,
+                    "ncu capture, uniform n=20000 int16, p=1..256, the whole call (28 sweeps, 9 evaluations of K)",
+                    {"paper_1104_3830_gb300/csrc/sweep_step.cu":
+                     "4f076eba500b3495da505af5705efdafabe0bbbf03e6cd1692e3ae97fa7e06fb",
+                     "paper_1104_3830_gb300/csrc/common.cuh":
+                     "081ba7d34dae961c3679ac9acf1c076fd6b30bb4428eb03eabf3ad582049a6cc",
+                     "paper_1104_3830_gb300/csrc/log2pair.cuh":
+                     "d0d997e23dba7b51d1c07b556aa6d5e60d23cf230a79b17de392b2f3074ae3d0"}),
     # Newton solve kernel: planted n=8192 int16, the p = 1 step (19 operator applications)
     (4, 8192, 2): ((5.138667e9 + 0.108529e9) / 19,
                    "ncu capture, planted n=8192 int16, p = 1 step, 19 operator applications (one launch)",
@@ -492,7 +502,7 @@ def run_precision(args):
             ms = statistics.mean(times)
             paths[name] = {"sweeps": int(info["sweeps_total"]), "ms": ms,
                            "sweeps_per_s": info["sweeps_total"] / (ms / 1e3),
-                           "kernel": KERNEL_NAMES.get(info["kernel_used"], "?"),
+                           "kernel": KERNEL_NAMES.get(info["kernel_used"], "?"), "kernel_used": int(info["kernel_used"]),
                            "kernel_ms": info["kernel_ms"], "converged": int(info["converged"])}
     launches = L.lib().sa_kernel_launches() - launches0
     del d, flush
@@ -521,6 +531,9 @@ def run_precision(args):
     peak, peak_kind = load_peaks()
     m = paths["mixed"]
     achieved = m["sweeps"] * n * n * 2 / (m["ms"] / 1e3) / 1e9
+    # DRAM bytes per sweep of the whole call (evaluations of K included), when a capture of
+    # this kernel source exists
+    traffic, traffic_src = measured_traffic(m["kernel_used"], n, w.dtype.itemsize)
     line = {"metric": METRIC, "value": m["sweeps_per_s"], "unit": "sweeps/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": m["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (exp/sum), f64 potentials", "data": "synthetic",
@@ -531,7 +544,8 @@ def run_precision(args):
             "oracle": {"sweeps": int(swo.sum()), "status": int(sto), "seconds": oracle_s, "cores": oracle.num_threads(),
                        "how": "FP64 log-domain Sinkhorn of the oracle on the same matrix and schedule"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": m["kernel"], "peak_source": f"{peak_kind} hbm_gbs",
+                         "traffic": traffic, "traffic_source": traffic_src or "none for this kernel source or size",
+                         "kernel": m["kernel"], "peak_source": f"{peak_kind} hbm_gbs",
                          "note": "whole scaling call incl. the per-step evaluation of K, about 3 sweeps per step"},
             "e2e": None, "gpu_launches": int(launches), "clocks": clk.summary()}
     if not args.no_cpu_baseline:
