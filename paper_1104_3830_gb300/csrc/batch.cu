@@ -299,6 +299,23 @@ __device__ __forceinline__ void group_sync(int group) {
     }
 }
 
+// group barrier that also returns whether `pred` holds in every thread of the group (the
+// barrier's own reduction: no shared-memory round of partial results)
+template <int G>
+__device__ __forceinline__ bool group_sync_and(int group, bool pred) {
+    if (G == 1) return __all_sync(0xffffffffu, pred);
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)pred), "r"(group + 1), "r"(32 * G)
+        : "memory");
+    return r != 0;
+}
+
 template <typename WT, int G, int NMAX>
 __global__ void __launch_bounds__(256) batch_group_kernel(BatchArgs A) {
     constexpr int NT = 32 * G;                  // threads of a group
@@ -558,8 +575,9 @@ __global__ void __launch_bounds__(512) batch_regs_kernel(BatchArgs A) {
     float* rs = cs + P * SEG;
     float2* vp = (float2*)(rs + P * SEG);
     float* Cs = (float*)(vp + NMAX);
-    float* wres = Cs + NMAX;                  // [2][G] residuals, by sweep parity
+    float* wres = Cs + NMAX;                  // [G] per-warp flags of the evaluation of K
     int* s_q = (int*)(wres + 2 * G);
+    int* s_bad = s_q + 1;                     // a row or column sum left the FP32 range
     constexpr int STR = NMAX + 1;
     const unsigned FULL = 0xffffffffu;
     for (;;) {
@@ -641,6 +659,7 @@ __global__ void __launch_bounds__(512) batch_regs_kernel(BatchArgs A) {
                 cs[(q / L) * SEG + q % L] = cq;
                 rs[(q / L) * SEG + q % L] = 0.0f;   // rows beyond n keep 1/s = 0
             }
+            if (tg == 0) *s_bad = 0;
             group_sync<G>(group);   // c published; wres and the staging area are reused
             // ---- sweeps ----
             int sweeps = 0;
@@ -691,21 +710,15 @@ __global__ void __launch_bounds__(512) batch_regs_kernel(BatchArgs A) {
                     cq = __fdividef(cq, S);
                     if (part == 0) cs[(q / L) * SEG + q % L] = cq;
                 }
-                // the group's residual (a failure as +inf): non-negative floats order like
-                // their bit patterns, so one warp reduction of the bits gives the maximum
-                const unsigned rb = __reduce_max_sync(FULL, __float_as_uint(badr ? INFINITY : resid));
-                if (G > 1 && lane == 0) wres[par * G + wig] = __uint_as_float(rb);
-                group_sync<G>(group);
-                float rmax = __uint_as_float(rb);
-                if (G > 1) {
-                    rmax = 0.0f;
-#pragma unroll
-                    for (int x = 0; x < G; ++x) rmax = fmaxf(rmax, wres[par * G + x]);
-                }
+                // the group converged when every thread's residual is within tol (the
+                // barrier's AND); a non-finite sum anywhere is flagged in shared memory
+                // before the barrier and read after it
+                if (badr) *s_bad = 1;
+                const bool conv = group_sync_and<G>(group, !badr && resid <= (float)A.tol);
                 ++sweeps;
-                bad = !(rmax < INFINITY);
-                done = bad || (rmax <= (float)A.tol) || (sweeps >= A.max_sweeps);
-                if (done && !bad && !(rmax <= (float)A.tol)) capped = true;
+                bad = G == 1 ? __any_sync(FULL, badr != 0) : *(volatile int*)s_bad != 0;
+                done = bad || conv || (sweeps >= A.max_sweeps);
+                if (done && !bad && !conv) capped = true;
             }
             sweeps_all += sweeps;
             if (bad) break;

@@ -151,23 +151,36 @@ __device__ __forceinline__ void krows_instance(KrowsSmem<CH>& sm, const WT* wb, 
 #pragma unroll
             for (int x = 0; x < M; ++x) S[x] = 0.0f;
             int badr = 0;
-            for (int i = wid; i < n; i += NW) {
+            // the warp's next row is loaded while the current one is reduced (its rows follow
+            // one another, each waiting for the previous row's sum)
+            float4 nx[CH];
+            auto load_row = [&](int i) {
                 const float* kr = K + (size_t)i * ldk;
-                float kv[M];
-                float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
                 for (int kk = 0; kk < CH; ++kk) {
                     const int c4 = lane + 32 * kk;
-                    float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                    if (c4 < NC) q = __ldcg((const float4*)(kr + 4 * c4));
-                    kv[4 * kk] = q.x;
-                    kv[4 * kk + 1] = q.y;
-                    kv[4 * kk + 2] = q.z;
-                    kv[4 * kk + 3] = q.w;
-                    a0 = fmaf(q.x, c[4 * kk], a0);
-                    a1 = fmaf(q.y, c[4 * kk + 1], a1);
-                    a0 = fmaf(q.z, c[4 * kk + 2], a0);
-                    a1 = fmaf(q.w, c[4 * kk + 3], a1);
+                    nx[kk] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if (c4 < NC && i < n) nx[kk] = __ldcg((const float4*)(kr + 4 * c4));
+                }
+            };
+            load_row(wid);
+            for (int i = wid; i < n; i += NW) {
+                float kv[M];
+#pragma unroll
+                for (int kk = 0; kk < CH; ++kk) {
+                    kv[4 * kk] = nx[kk].x;
+                    kv[4 * kk + 1] = nx[kk].y;
+                    kv[4 * kk + 2] = nx[kk].z;
+                    kv[4 * kk + 3] = nx[kk].w;
+                }
+                load_row(i + NW);
+                float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+                for (int kk = 0; kk < CH; ++kk) {
+                    a0 = fmaf(kv[4 * kk], c[4 * kk], a0);
+                    a1 = fmaf(kv[4 * kk + 1], c[4 * kk + 1], a1);
+                    a0 = fmaf(kv[4 * kk + 2], c[4 * kk + 2], a0);
+                    a1 = fmaf(kv[4 * kk + 3], c[4 * kk + 3], a1);
                 }
                 const float sv = warp_sum(a0 + a1);
                 if (!(sv >= 0x1p-120f && sv <= 0x1p120f)) badr = 1;
