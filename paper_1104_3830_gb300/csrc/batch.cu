@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(256) batch_group_kernel(BatchArgs A) {
 template <int NMAX, int P>
 __host__ __device__ inline unsigned regs_slot_floats() {
     constexpr unsigned L = NMAX / P;
-    // staging K (NMAX x (NMAX + 1)), c and 1/s (P segments of L + 4), V pairs, C, residuals
+    // staging K (NMAX x (NMAX + 1)), c and 1/s (P segments of L + 4), V pairs, C, flags
     return ((NMAX * (NMAX + 1) + 3u) & ~3u) + 2u * P * (L + 4) + 2u * NMAX + NMAX + 64u;
 }
 
@@ -665,7 +665,6 @@ __global__ void __launch_bounds__(512) batch_regs_kernel(BatchArgs A) {
             int sweeps = 0;
             bool done = bad;
             while (!done) {
-                const int par = sweeps & 1;
                 // row pass: s_q = sum over the parts of K_q,part . c_part
                 const float* cseg = cs + part * SEG;
                 float a[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
