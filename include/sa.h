@@ -156,7 +156,9 @@ typedef enum {
                                  sa_solve_reduced_gpu from the scaling's duals; 0 (default):
                                  on the host with sa_solve_reduced_near */
     SA_OPT_STEP_SPARSE = 2,   /* 1: the STEP kernel may sweep only the entries >= 2^-70 of
-                                 their row when K is sparse enough; 0 (default): dense */
+                                 their row when K is sparse enough (where its ring has
+                                 two-row stages: n <= 6700 or 8900 < n <= 12288 on a GB300);
+                                 0 (default): dense */
     SA_OPT_MAX_GRID = 3,      /* cap on the blocks of the persistent kernels (0, the
                                  default: one or two per SM) */
     SA_OPT_FUSED_THREADS = 4, /* threads per block of the FUSED kernel for rows of 513 to

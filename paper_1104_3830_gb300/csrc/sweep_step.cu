@@ -43,12 +43,17 @@ namespace sa {
 namespace {
 
 constexpr int kStepNred = 4;      // row-sum publication buffers
-constexpr int kStepMaxRing = 16;  // ring slots at most; a slot holds one stage (two rows)
+constexpr int kStepMaxRps = 4;    // rows per ring stage at most
+constexpr int kStepMaxRing = 16;  // ring slots at most; a slot holds one stage
 // rows per ring stage of the dense ring mode.  A stage costs a fixed ~0.5 us (the
 // publication of the warps' partial row sums and the slot's release) plus ~0.4 us per row
 // at n = 8192, so two-row stages beat one-row stages (34.7 against 47.7 us per row pass)
-// although a one-row ring keeps twice the rows in flight.
+// although a one-row ring keeps twice the rows in flight.  Where at most three two-row
+// stages fit and two three-row stages do (rows of 27 to 35 KB), three-row stages are taken:
+// at n = 8192 45.5 against 48.0 us per sweep (row pass 33.7 against 37.1 us), although the
+// two-stage ring consumes each stage before forming the next one's partials.
 constexpr int kDenseRowsPerStage = 2;
+constexpr int kWideRowsPerStage = 3;
 
 struct StepArgs {
     const void* w;
@@ -170,8 +175,8 @@ struct KahanS {
     }
 };
 
-// SP: sparse epochs possible.  RPS: rows per ring stage (one for rows of more than 48 KB,
-// whose ring has two slots).
+// SP: sparse epochs possible.  RPS: rows per ring stage (three for rows of 27 to 35 KB, one
+// for rows of more than 48 KB; two or three slots then).
 template <int NT, int CH, bool SP, int RPS>
 __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     constexpr int NW = NT / 32;
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     constexpr int MAXR = kStepMaxRing;
     constexpr int FG = NT / 64;
     static_assert(NT % 64 == 0, "layout");
-    static_assert(RPS == 1 || RPS == 2, "rows per stage");
+    static_assert(RPS >= 1 && RPS <= kStepMaxRps, "rows per stage");
     static_assert(!SP || RPS == 2, "sparse records come in stages of two rows");
     extern __shared__ __align__(128) unsigned char smem[];
     // [region: dense ring | or sparse c, S and ring] [barriers] [scratch]
@@ -190,8 +195,8 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
     unsigned* rel_cnt = (unsigned*)(mrow + NRED);           // [MAXR] warp releases per slot
     unsigned* iss_cnt = rel_cnt + MAXR;                     // [MAXR] copies issued per slot
     // 8 (MAXR + NRED) + 8 MAXR bytes of barriers and counters end on a 16-byte boundary
-    float* red = (float*)(iss_cnt + MAXR);                  // [NRED][2][NW] (16-aligned)
-    double* crow = (double*)(red + NRED * 2 * NW);          // [max_rows] row references
+    float* red = (float*)(iss_cnt + MAXR);                  // [NRED][RPS][NW] (16-aligned)
+    double* crow = (double*)(red + NRED * kStepMaxRps * NW);   // [max_rows] row references
     double* redp = crow + A.max_rows;                       // [FG][64]
     double* redd = redp + FG * 64;                          // [NW]
     float* srow = (float*)(redd + NW);                      // [max_rows] row sums
@@ -610,10 +615,13 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 // mrow[g % NRED]; consume(g): wait for every warp's partials, accumulate the
                 // normalised rows into the column sums, release the slots.
                 // row r (0, 1) of the stage at ring index v
+                // row r of the stage in slot v % ring_n: dense rows at r row pitches; a sparse
+                // stage (two rows) holds the records of its first row, then its second's
                 auto row_of = [&](uint32_t v, int q0, int r) -> const unsigned char* {
                     const unsigned char* base = sbase + (size_t)(v % (uint32_t)ring_n) * slot_bytes;
                     if (r == 0) return base;
-                    return base + ((SP && sparse) ? rowlen[q0] * 8u : A.row_bytes);
+                    if (SP && sparse) return base + rowlen[q0] * 8u;
+                    return base + (size_t)r * A.row_bytes;
                 };
                 auto row_partial = [&](const unsigned char* rowp, int q) -> float {
                     float a0 = 0.0f, a1 = 0.0f;
@@ -640,35 +648,37 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 auto produce = [&](int g) {
                     const uint32_t v = its + g;
                     const int q0 = RPS * stage_of(v);
-                    const bool two = RPS == 2 && q0 + 1 < nrows;
+                    const int nr = min(RPS, nrows - q0);   // rows of the stage (the last may be short)
                     const uint32_t rn = (uint32_t)ring_n;
                     if (!mbar_wait(&mbar[v % rn], (v / rn) & 1u, A.err, A.wait_ns)) {
                         s_flag = 1;   // this thread's copy is not in: its warp never releases the slot
                     }
-                    const float sp0 = row_partial(row_of(v, q0, 0), q0);
-                    const float sp1 = two ? row_partial(row_of(v, q0, 1), q0 + 1) : 0.0f;
-                    const float w0 = warp_sum(sp0);
-                    const float w1 = RPS == 2 ? warp_sum(sp1) : 0.0f;
+                    float sp[RPS];
+#pragma unroll
+                    for (int r = 0; r < RPS; ++r) sp[r] = r < nr ? row_partial(row_of(v, q0, r), q0 + r) : 0.0f;
+#pragma unroll
+                    for (int r = 0; r < RPS; ++r) sp[r] = warp_sum(sp[r]);
                     if (lane == 0) {
                         const uint32_t gs = gbase + g;
-                        red[((gs % NRED) * 2) * NW + wid] = w0;
-                        if (RPS == 2) red[((gs % NRED) * 2 + 1) * NW + wid] = w1;
+#pragma unroll
+                        for (int r = 0; r < RPS; ++r) red[((gs % NRED) * RPS + r) * NW + wid] = sp[r];
                         mbar_arrive(&mrow[gs % NRED]);
                     }
                 };
                 auto consume = [&](int g) -> bool {
                     const uint32_t v = its + g;
                     const int q0 = RPS * stage_of(v);
-                    const bool two = RPS == 2 && q0 + 1 < nrows;
+                    const int nr = min(RPS, nrows - q0);
                     const uint32_t gs = gbase + g;
                     if (!mbar_wait(&mrow[gs % NRED], (gs / NRED) & 1u, A.err, A.wait_ns)) s_flag = 1;
                     // warp-uniform: a warp either releases the stage (every lane got its copy
                     // and every partial) or leaves the pass as a whole
                     if (__any_sync(0xffffffffu, *(volatile int*)&s_flag != 0)) return false;
-                    float ss[2] = {1.0f, 1.0f};
+                    float ss[RPS];
+                    bool ss_bad = false;
 #pragma unroll
                     for (int r = 0; r < RPS; ++r) {
-                        const float4* rv = (const float4*)(red + ((gs % NRED) * 2 + r) * NW);
+                        const float4* rv = (const float4*)(red + ((gs % NRED) * RPS + r) * NW);
                         float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
 #pragma unroll
                         for (int x = 0; x < NW / 4; ++x) {
@@ -679,19 +689,21 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                             a3 += q4.w;
                         }
                         ss[r] = (a0 + a1) + (a2 + a3);
+                        if (r < nr && !(ss[r] >= 0x1p-120f && ss[r] <= 0x1p120f)) ss_bad = true;
                     }
-                    if (!(ss[0] >= 0x1p-120f && ss[0] <= 0x1p120f) || (two && !(ss[1] >= 0x1p-120f && ss[1] <= 0x1p120f))) {
+                    if (ss_bad) {
                         if (tid == 0) atomicCAS(A.err, 0, kErrNonfinite);
                         s_flag = 1;
                         return false;
                     }
                     if (tid == 0) {
-                        srow[q0] = ss[0];
-                        if (two) srow[q0 + 1] = ss[1];
+#pragma unroll
+                        for (int r = 0; r < RPS; ++r)
+                            if (r < nr) srow[q0 + r] = ss[r];
                     }
 #pragma unroll
                     for (int r = 0; r < RPS; ++r) {
-                        if (r == 1 && !two) break;
+                        if (r >= nr) break;
                         const float inv = rcp_approx(ss[r]);
                         const unsigned char* rowp = row_of(v, q0, r);
                         if (SP && sparse) {
@@ -719,9 +731,11 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs A) {
                 };
                 // With three or more ring stages the partial row sums of stage g + 1 are
                 // formed while the other warps' partials of stage g are still arriving.  A
-                // two-stage ring (rows too wide for more) cannot look ahead: the slot of g + 1
-                // is refilled only when g + 1 - 2 is released, so each stage is consumed first
-                // and its copy for g + 2 is in flight while the next stage is read.
+                // two-stage ring cannot look ahead: the slot of g + 1 is refilled only when
+                // g + 1 - 2 is released, so each stage is consumed first and its copy for
+                // g + 2 is in flight while the next stage is read.  (Forming g + 1's partials
+                // first whenever its copy had already landed measured slower: 46.7 against
+                // 45.5 us per sweep at n = 8192 with three-row stages.)
                 if ((SP && sparse) || ring_n > 2) {
                     if (nst > 0) produce(0);
                     for (int g = 0; g < nst; ++g) {
@@ -884,7 +898,7 @@ size_t step_smem_bytes(int nt, size_t region_bytes, int max_rows) {
     const int nw = nt / 32;
     const int fg = nt / 64;
     return region_bytes + 8 * (size_t)(kStepMaxRing + kStepNred) + 8 * (size_t)kStepMaxRing +
-           4 * (size_t)(kStepNred * 2 * nw) +
+           4 * (size_t)(kStepNred * kStepMaxRps * nw) +
            8 * (size_t)(max_rows + fg * 64 + nw) + 4 * (size_t)max_rows + 8 * (size_t)max_rows + 4096 + 1024;
 }
 
@@ -910,13 +924,30 @@ StepCfg pick_step(const sa_ctx* ctx, int n) {
     else return c;
     const unsigned row_bytes = (unsigned)align_up((size_t)n * 4, 16);
     const int max_rows = step_max_rows(ctx, n);
-    // ring slots in rows: two-row stages up to 48 KB rows, else one-row stages (rows of 48
-    // to 96 KB: two or three of them fit).  The ring doubles as scratch for V (8 ceil(n/4)*4
-    // bytes = two rows) during the per-step evaluation of K.
-    const int rmax = c.rps == 1 ? 3 : 8, rmin = c.rps == 1 ? 2 : 4;
-    for (int ring = rmax; ring >= rmin; --ring) {
-        if (step_smem_bytes(c.nt, (size_t)ring * row_bytes, max_rows) <= ctx->smem_optin) {
-            c.ring = ring;
+    auto fits = [&](int ring) {
+        return step_smem_bytes(c.nt, (size_t)ring * row_bytes, max_rows) <= ctx->smem_optin;
+    };
+    // ring slots in rows, a whole number of stages, at least two: one-row stages for rows of
+    // 48 to 96 KB (two or three fit); else two-row stages, up to four, unless at most three
+    // of them fit and two three-row stages do.  The ring doubles as scratch for V
+    // (8 ceil(n/4)*4 bytes = two rows) during the per-step evaluation of K.
+    if (c.rps == 1) {
+        for (int st = 3; st >= 2; --st)
+            if (fits(st)) {
+                c.ring = st;
+                return c;
+            }
+    } else {
+        int st2 = 0;
+        for (int st = 4; st >= 2 && st2 == 0; --st)
+            if (fits(st * kDenseRowsPerStage)) st2 = st;
+        if (st2 <= 3 && (c.ch == 4 || c.ch == 6) && fits(2 * kWideRowsPerStage)) {
+            c.rps = kWideRowsPerStage;
+            c.ring = 2 * kWideRowsPerStage;
+            return c;
+        }
+        if (st2 >= 2) {
+            c.ring = st2 * kDenseRowsPerStage;
             return c;
         }
     }
@@ -1091,7 +1122,9 @@ sa_status scale_step(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, do
     else if (cfg.nt == 256) rc = launch_step<256, 1>(ctx, args, smem, &G);
     else if (cfg.ch == 1) rc = launch_step<512, 1>(ctx, args, smem, &G);
     else if (cfg.ch == 2) rc = launch_step<512, 2>(ctx, args, smem, &G);
+    else if (cfg.ch == 4 && cfg.rps == kWideRowsPerStage) rc = launch_step<512, 4, kWideRowsPerStage>(ctx, args, smem, &G);
     else if (cfg.ch == 4) rc = launch_step<512, 4>(ctx, args, smem, &G);
+    else if (cfg.ch == 6 && cfg.rps == kWideRowsPerStage) rc = launch_step<512, 6, kWideRowsPerStage>(ctx, args, smem, &G);
     else if (cfg.ch == 6) rc = launch_step<512, 6>(ctx, args, smem, &G);
     else if (cfg.ch == 8) rc = launch_step<512, 8, 1>(ctx, args, smem, &G);
     else if (cfg.ch == 10) rc = launch_step<512, 10, 1>(ctx, args, smem, &G);

@@ -175,6 +175,25 @@ def test_largest_supported_width(ctx):
     assert fp64_sum_err(b, ps[-1], u, v) < STEP_SUM_BOUND
 
 
+@pytest.mark.parametrize("n", [7001, 8500])
+def test_three_row_stages(ctx, n):
+    """Rows of 27 to 35 KB run through a ring of two three-row stages: a ragged width
+    n = 7001 (four chunks per thread) and n = 8500 (six chunks), int16 weights in [1, 1000],
+    p = 1, 2: X(p) entry by entry against the oracle and its FP64 sums by the oracle (the
+    planted n = 8192 workload runs the same ring in the full-size tests)."""
+    w = W.uniform(n, 1, 1000, 88 + n, dtype=np.int16)
+    d = api.to_device(w)
+    ps = [1.0, 2.0]
+    u, v, info = api.sa_scale(ctx, d, ps, 1e-6, 2000, kernel="step")
+    assert info["status"] == 0 and info["kernel_used"] == 3, info
+    uu, vv = u.cpu().numpy(), v.cpu().numpy()
+    b = oracle.log_weights(w.astype(np.int64))
+    uo, vo, _, _, st = oracle.sinkhorn(b, ps, 1e-6, 2000)
+    assert st == 0
+    assert max_x_deviation(b, ps[-1], uu, vv, uo, vo, rows=512) < 8e-6
+    assert fp64_sum_err(b, ps[-1], uu, vv) < STEP_SUM_BOUND
+
+
 @pytest.mark.parametrize("n", [12290, 22000])
 def test_wide_rows_one_row_stages(ctx, n):
     """Rows of more than 48 KB run through a ring of one-row stages: a ragged width
