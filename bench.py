@@ -66,10 +66,10 @@ _TRAFFIC = {
                     "d0d997e23dba7b51d1c07b556aa6d5e60d23cf230a79b17de392b2f3074ae3d0"}),
     # step kernel: uniform n=20000 int16, the whole p = 1..256 schedule (28 sweeps, 9 evaluations
     # of K) of one scaling call, per sweep
-    (3, 20000, 2): ((69.191562e9 + 17.739943e9) / 28,
+    (3, 20000, 2): ((69.185471e9 + 17.739302e9) / 28,
                     "ncu capture, uniform n=20000 int16, p=1..256, the whole call (28 sweeps, 9 evaluations of K)",
                     {"paper_1104_3830_gb300/csrc/sweep_step.cu":
-                     "4f076eba500b3495da505af5705efdafabe0bbbf03e6cd1692e3ae97fa7e06fb",
+                     "fc6690f60f6448b776fb7bcfe39b4e109130c29330eb55b98c7f21ff7129c31f",
                      "paper_1104_3830_gb300/csrc/common.cuh":
                      "081ba7d34dae961c3679ac9acf1c076fd6b30bb4428eb03eabf3ad582049a6cc",
                      "paper_1104_3830_gb300/csrc/log2pair.cuh":
