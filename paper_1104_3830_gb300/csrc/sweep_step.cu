@@ -140,13 +140,17 @@ __device__ __forceinline__ void fence_proxy_async_all() {
     asm volatile("fence.proxy.async;" ::: "memory");
 }
 
+// Grid barrier: thread 0 arrives with a release reduction (the block's writes, ordered
+// before it by the block barrier, become visible with the arrival) and polls the counter
+// with acquire loads.  The error word is read while polling, not after a completed wait:
+// a block that fails sets it and leaves before its next arrival, so the others see it
+// while they wait at that barrier (within 32 polls) and leave in turn.
 __device__ __forceinline__ bool step_grid_sync(unsigned* ctr, unsigned target, int* err, int* s_ok,
                                                uint64_t wait_ns) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
-        atomicAdd(ctr, 1u);
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(1u) : "memory");
         if (ld_acquire(ctr) < target) {
             const uint64_t t0 = globaltimer_ns();
             unsigned spins = 0;
@@ -158,7 +162,6 @@ __device__ __forceinline__ bool step_grid_sync(unsigned* ctr, unsigned target, i
                 __nanosleep(32);
             }
         }
-        if (*(volatile int*)err != 0) ok = 0;
         *s_ok = ok;
     }
     __syncthreads();
