@@ -57,19 +57,19 @@ def load_peaks():
 # capture was taken on: after any change to these files the figure is unknown (null).
 _TRAFFIC = {
     # step kernel: planted n=8192 int16, p=256 from a cold start, 200 sweeps + 1 evaluation of K
-    (3, 8192, 2): ((37.424049e9 + 0.924273e9) / 200, "ncu capture, planted n=8192 int16, p=256, 200 sweeps (one launch)",
+    (3, 8192, 2): ((37.355624e9 + 0.927293e9) / 200, "ncu capture, planted n=8192 int16, p=256, 200 sweeps (one launch)",
                    {"paper_1104_3830_gb300/csrc/sweep_step.cu":
-                    "fc6690f60f6448b776fb7bcfe39b4e109130c29330eb55b98c7f21ff7129c31f",
+                    "2714eb0a87182dc9e9501bed35d548eb3c7986a9c9daa6e21a14acfc754e8af6",
                     "paper_1104_3830_gb300/csrc/common.cuh":
                     "081ba7d34dae961c3679ac9acf1c076fd6b30bb4428eb03eabf3ad582049a6cc",
                     "paper_1104_3830_gb300/csrc/log2pair.cuh":
                     "d0d997e23dba7b51d1c07b556aa6d5e60d23cf230a79b17de392b2f3074ae3d0"}),
     # step kernel: uniform n=20000 int16, the whole p = 1..256 schedule (28 sweeps, 9 evaluations
     # of K) of one scaling call, per sweep
-    (3, 20000, 2): ((69.185471e9 + 17.739302e9) / 28,
+    (3, 20000, 2): ((69.183675e9 + 17.738929e9) / 28,
                     "ncu capture, uniform n=20000 int16, p=1..256, the whole call (28 sweeps, 9 evaluations of K)",
                     {"paper_1104_3830_gb300/csrc/sweep_step.cu":
-                     "fc6690f60f6448b776fb7bcfe39b4e109130c29330eb55b98c7f21ff7129c31f",
+                     "2714eb0a87182dc9e9501bed35d548eb3c7986a9c9daa6e21a14acfc754e8af6",
                      "paper_1104_3830_gb300/csrc/common.cuh":
                      "081ba7d34dae961c3679ac9acf1c076fd6b30bb4428eb03eabf3ad582049a6cc",
                      "paper_1104_3830_gb300/csrc/log2pair.cuh":

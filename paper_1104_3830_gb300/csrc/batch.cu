@@ -776,7 +776,7 @@ sa_status launch_group(sa_ctx* ctx, cudaStream_t bs, const BatchArgs& args, int 
                   NMAX, smem + fa.sharedSizeBytes, ctx->smem_optin);
         return SA_E_UNSUPPORTED;
     }
-    SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SA_CUDA(allow_dynamic_smem(kern, ctx->smem_optin));
     int per_sm = 0;
     SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * G * per_block, smem));
     if (per_sm < 1) {
@@ -811,7 +811,7 @@ sa_status launch_regs(sa_ctx* ctx, cudaStream_t bs, const BatchArgs& args, int p
                   per_block, G, NMAX, threads, smem + fa.sharedSizeBytes);
         return SA_E_UNSUPPORTED;
     }
-    SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SA_CUDA(allow_dynamic_smem(kern, ctx->smem_optin));
     int per_sm = 0;
     SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) {
@@ -887,7 +887,7 @@ sa_status launch_block_path(sa_ctx* ctx, cudaStream_t bs, BatchArgs args, int ma
     size_t smem = std::min<size_t>(ctx->smem_optin, 110 * 1024);   // two blocks per SM
     args.smem_table = smem > fixed ? smem - fixed : 0;
     auto go = [&](auto kern) -> sa_status {
-        SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SA_CUDA(allow_dynamic_smem(kern, ctx->smem_optin));
         int per_sm = 0;
         SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
         const int grid = std::max(1, std::min(args.k, ctx->num_sms * std::max(per_sm, 1)));

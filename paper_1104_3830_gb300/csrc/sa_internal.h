@@ -96,6 +96,18 @@ struct sa_ctx {
 namespace sa {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Sets a kernel's dynamic shared-memory limit to the most it can take next to its static
+// shared memory (optin: the device's per-block opt-in maximum).  Setting the size of each
+// call instead would race between host threads that launch the same kernel with different
+// sizes (one thread's smaller limit failing the other's occupancy query or launch).
+template <typename Kern>
+inline cudaError_t allow_dynamic_smem(Kern kern, size_t optin) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(optin - fa.sharedSizeBytes));
+}
 inline int wbytes(sa_wtype t) { return t == SA_I16 ? 2 : 4; }
 
 // Bump allocator over a reserved workspace.

@@ -22,6 +22,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -174,6 +175,10 @@ std::vector<Request*> admit(sa_server* s, bool small_only, int max_take, std::un
 }
 
 void finish(sa_server* s, Request* r, sa_status st) {
+    // a failed request leaves a line on stderr with the worker's last error message
+    if (st != SA_OK && st != SA_E_NOT_CONVERGED)
+        fprintf(stderr, "sa_server: request %llu (n=%d) failed with status %d: %s\n", (unsigned long long)r->ticket, r->n,
+                (int)st, sa_last_error());
     std::lock_guard<std::mutex> g(s->mu);
     r->status = st;
     r->t_done = s->now();

@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(FusedArgs A) {
 template <typename WT, int NT, int CH, int RING, int R>
 sa_status launch_fused(sa_ctx* ctx, const FusedArgs& args, size_t smem, int* grid_out) {
     auto kern = fused_kernel<WT, NT, CH, RING, R>;
-    SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SA_CUDA(allow_dynamic_smem(kern, ctx->smem_optin));
     int per_sm = 0;
     SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
     if (per_sm < 1) {

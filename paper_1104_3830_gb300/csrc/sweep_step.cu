@@ -967,7 +967,7 @@ sa_status launch_step(sa_ctx* ctx, const StepArgs& args, size_t smem, int* grid_
         kern = args.sparse_ok ? step_kernel<NT, CH, true, 2> : step_kernel<NT, CH, false, 2>;
     else
         kern = step_kernel<NT, CH, false, RPS>;
-    SA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SA_CUDA(allow_dynamic_smem(kern, ctx->smem_optin));
     int per_sm = 0;
     SA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
     if (per_sm < 1) {

@@ -132,6 +132,22 @@ def test_auto_picks_step_for_mixed(ctx):
     assert info["kernel_used"] in (1, 2)
 
 
+def test_zero_column_is_nonfinite(ctx):
+    """A column without support is found by the column finalisation of some block; every
+    block then leaves (at the next grid barrier at the latest) and the call returns
+    SA_E_NONFINITE on the three-row stage ring (n = 8192) as on the smallest one."""
+    for n in (256, 8192):
+        w = W.uniform(n, 1, 1000, 82 + n, dtype=np.int16)
+        w[:, 5] = 0
+        d = api.to_device(w)
+        with pytest.raises(api.SaError) as e:
+            api.sa_scale(ctx, d, [1.0, 2.0], 1e-6, 50, kernel="step")
+        assert e.value.status == -6, n
+    w2 = W.uniform(256, 1, 1000, 85, dtype=np.int16)
+    _, _, info = api.sa_scale(ctx, api.to_device(w2), [1.0, 2.0], 1e-6, kernel="step")
+    assert info["status"] == 0
+
+
 def test_zero_row_is_nonfinite(ctx):
     w = W.uniform(256, 1, 1000, 81, dtype=np.int16)
     w[17, :] = 0
