@@ -449,6 +449,7 @@ sa_status sa_scale(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, doub
         set_error("newton kernel needs SA_PREC_MIXED, a 16-byte aligned base and ld*sizeof(w) %% 16 == 0");
         return SA_E_UNSUPPORTED;
     }
+    NvtxRange range("sa_scale n=%d kernel=%d p_steps=%d", n, (int)kind, o->n_p);
     // library units: log2.  A warm start is kept so that a failure leaves the caller's
     // potentials as they were given.
     if (o->resume_from > 0) {
@@ -579,6 +580,7 @@ sa_status sa_assign(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, dou
     if ((rc = check_opts(o))) return rc;
     DeviceGuard g(ctx->device);
     const int n = a->n;
+    NvtxRange range("sa_assign n=%d", n);
     double* d_uv = nullptr;
     SA_CUDA(cudaMallocAsync((void**)&d_uv, 2 * sizeof(double) * n, ctx->stream));
     double* d_u = d_uv;
@@ -608,11 +610,14 @@ sa_status sa_assign(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, dou
     // prune + solve, re-pruning at t/16 while B holds no permutation
     for (;;) {
         double a0 = now_ms();
+        nvtxRangePushA("prune");
         rc = prune_device(ctx, a, p, d_u, d_v, t, 1, &B, have_first ? nullptr : &log_ub);
+        nvtxRangePop();
         double a1 = now_ms();
         res->ms_prune += a1 - a0;
         if (rc) { cudaFreeAsync(d_uv, ctx->stream); return rc; }
         if (!have_first) res->nnz_first = B.nnz;
+        NvtxRange solve_range("solve B nnz=%lld", (long long)B.nnz);
         if (ctx->solve_gpu && B.nnz >= kAuctionMinNnz) {
             std::vector<double> pmax(n);
             for (int j = 0; j < n; ++j) pmax[j] = -price[j];
@@ -642,6 +647,7 @@ sa_status sa_assign(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, dou
     res->gamma = std::exp(log_ub - first_sum);
     // LP-duality repair: add violating entries of A until none is left
     for (int iter = 0;; ++iter) {
+        NvtxRange cert_range("certify %d", iter);
         double c0 = now_ms();
         int64_t nv = 0;
         sa_csr add{};
@@ -702,6 +708,7 @@ sa_status sa_algorithm1(sa_ctx* ctx, const sa_matrix* a, const sa_alg1_opts* o, 
     double p = o->p0, p_prev_raw = 0.0;
     sa_status out = SA_E_NOT_CONVERGED;
     for (int r = 0; r < o->max_rounds; ++r, p += o->dp) {
+        NvtxRange round_range("algorithm 1 round %d (p=%g)", r, p);
         const double p_raw = p * m;
         double sched[2] = {p_prev_raw, p_raw};
         sa_scale_opts so{};

@@ -940,6 +940,7 @@ extern "C" sa_status sa_batch_scale(sa_ctx* ctx, int32_t k, const void* const* d
             return SA_E_INVALID;
         }
     cudaSetDevice(ctx->device);
+    NvtxRange range("sa_batch_scale k=%d", k);
     cudaStream_t st = ctx->stream;
     std::vector<int32_t> hn(k);
     std::vector<int64_t> hld(k);

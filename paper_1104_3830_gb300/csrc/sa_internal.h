@@ -1,7 +1,10 @@
 // sa_internal.h -- host-side internals of libsa shared by the translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+#include <stdarg.h>
 #include <stdint.h>
+#include <stdio.h>
 
 #include <atomic>
 #include <string>
@@ -24,6 +27,22 @@ constexpr double kLog2e = 1.44269504088896340736;
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;  // 2 s per device wait
 
 void set_error(const char* fmt, ...);
+
+// An NVTX range over a scope (host side: API calls, p steps of host-driven loops, server
+// request phases).  Without a tool attached the NVTX calls return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char* fmt, ...) {
+        char buf[96];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        nvtxRangePushA(buf);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Process-wide count of kernels this library has launched (sa_kernel_launches).
 extern std::atomic<long long> g_kernel_launches;

@@ -329,6 +329,7 @@ void small_worker(sa_server* s) {
             }
         }
         if (fin) {
+            sa::NvtxRange range("server: finish request %llu n=%d", (unsigned long long)fin->ticket, fin->n);
             sa_status rq = fin->live_rc;
             if (rq == SA_OK) rq = fin->live_status >= 0 ? SA_OK : SA_E_NONFINITE;
             fin->sweeps = fin->live_sweeps;
@@ -348,6 +349,7 @@ void small_worker(sa_server* s) {
         }
         // upload the group's matrices and make room for their potentials; one
         // synchronisation, then each request that made it is published
+        sa::NvtxRange range("server: admit %zu small requests", adm.size());
         std::vector<sa_status> rcs(adm.size(), SA_OK);
         for (size_t q = 0; q < adm.size(); ++q) {
             Request* r = adm[q];
@@ -457,6 +459,7 @@ void live_dispatcher(sa_server* s) {
         const bool start = oldest_unclaimed >= 0 && free_slot >= 0 && grid >= std::min(L.grid, kMinLiveGrid) &&
                            (nrun == 0 || (!large_pending && s->now() - oldest_unclaimed > 2e-4));
         if (start) {
+            nvtxMarkA("server: request queue launch");
             sa::LiveArgs a = L.args;
             a.kscr = L.kbase + (size_t)free_slot * L.grid * sa::live_slot_floats();
             sa_status rc = sa::live_launch(a, grid, L.stream[free_slot]);
@@ -617,6 +620,7 @@ void large_worker(sa_server* s) {
                 rc = SA_E_INVALID;
                 sa::set_error("server stopped");
             } else {
+                sa::NvtxRange range("server: assign request %llu n=%d grid=%d", (unsigned long long)r->ticket, r->n, grid);
                 ctx->max_grid = grid;
                 sa_matrix a{dw, r->wtype, r->n, ld};
                 r->perm.assign(r->n, -1);

@@ -213,6 +213,7 @@ sa_status run_plain(sa_ctx* ctx, const sa_matrix* a, const sa_scale_opts* o, dou
     double last_res = INFINITY;
     for (int k = k0; k < o->n_p; ++k) {
         const double p = o->p[k];
+        NvtxRange range("p step %d (p=%g)", k, p);
         if (k > 0 && !o->warm_keep_v) {
             double f = p / o->p[k - 1];
             scale_vec_kernel<<<(n + 255) / 256, 256, 0, st>>>(U, n, f);
